@@ -1,0 +1,253 @@
+/*
+ * adagio.h -- C ABI of the GB300-native ADAGIO library.
+ *
+ * ADAGIO (Blasiok & Tsourakakis, arXiv 1609.05388) embeds a point cloud
+ * T = {x_1..x_n} in R^d linearly into R^m by
+ *     f(w) = (P w, S (w - P^T P w))                              (Algorithm 1)
+ * where P (s x d, orthonormal rows) spans the top-s principal subspace of the
+ * zero-centred data (Sec. 2, "PCA") and S (k x d) has iid entries
+ * +-1/sqrt(k) (Algorithm 1; Lemma 2), m = s + k.  For a target dimension m
+ * the library uses s = floor(m/2), k = ceil(m/2) (Sec. 4.1) unless told
+ * otherwise.  The map is stored as the m x d matrix A = [P ; S (I - P^T P)],
+ * so that Y = X A^T.
+ *
+ * Quality is certified exhaustively: for every unordered pair i < j the
+ * pair distortion  | ||y_i - y_j|| / ||x_i - x_j|| - 1 |  (Eq. 2) is formed,
+ * and the certificate reports its maximum (Eq. 3, the embedding's distortion),
+ * mean, a histogram and the number of pairs above eps.
+ *
+ * Conventions for every entry point:
+ *  - Matrices are float32, row-major, one point per row, with an explicit
+ *    leading dimension (elements between consecutive rows, >= the row length).
+ *  - Array arguments may be DEVICE pointers (on the context's device) or HOST
+ *    pointers (pageable or pinned).  Host inputs are copied to the device and
+ *    host outputs copied back inside the call; this is the end-to-end path.
+ *    Arrays are owned by the caller and never retained after the call.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  Work is
+ *    enqueued on it.  Entry points that return a host-side result (a
+ *    certificate, a chosen dimension) synchronise that stream before
+ *    returning; the others return as soon as the work is enqueued, unless a
+ *    host output array forces a synchronising copy.
+ *  - A context owns a device workspace and must not be used by two calls at
+ *    the same time (calls on one context are serialised by the caller).
+ *  - Every function returns ADAGIO_OK (0) or a negative status; no exception
+ *    crosses the ABI and the library never exits or traps.  The message of
+ *    the last failure on a context is returned by adagio_last_error().
+ */
+#ifndef ADAGIO_H
+#define ADAGIO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ status */
+#define ADAGIO_OK                  0
+#define ADAGIO_E_INVALID_ARG      -1  /* a size, pointer or option is out of range   */
+#define ADAGIO_E_NONFINITE        -2  /* an input holds NaN or Inf                   */
+#define ADAGIO_E_CUDA             -3  /* a CUDA runtime call failed                  */
+#define ADAGIO_E_WORKSPACE        -4  /* the workspace limit would be exceeded       */
+#define ADAGIO_E_QUEUE_OVERFLOW   -5  /* recompute queue full even after a retry     */
+#define ADAGIO_E_TIMEOUT          -6  /* a bounded device-side wait gave up          */
+#define ADAGIO_E_NOT_CERTIFIABLE  -7  /* eps not reached at the largest allowed m    */
+#define ADAGIO_E_UNSUPPORTED      -8  /* the device is not sm_103 or a mode is absent */
+
+#define ADAGIO_HIST_BINS 64
+
+/* Arithmetic of the all-pairs Gram tiles (the exact recompute of flagged
+ * pairs is the same in every mode). */
+#define ADAGIO_PREC_FP32     0  /* plain FP32 SIMT Gram tiles                       */
+#define ADAGIO_PREC_FP16X3   1  /* tensor cores: 2-term FP16 split, 3 products,     */
+                                /* FP32 accumulate (power-of-two scaled)            */
+#define ADAGIO_PREC_BF16X3   2  /* tensor cores: 2-term BF16 split, 3 products      */
+
+#define ADAGIO_JL_RADEMACHER 0  /* entries +-1/sqrt(k) (Algorithm 1)                */
+#define ADAGIO_JL_GAUSSIAN   1  /* entries N(0, 1/k) (Box-Muller)                   */
+
+typedef struct adagio_ctx adagio_ctx;
+
+/*
+ * Certificate of an embedding (Eq. 2 and Eq. 3 over all n(n-1)/2 pairs).
+ *  pairs        n(n-1)/2
+ *  degenerate   pairs with x_i == x_j (Eq. 2 undefined); excluded from all
+ *               statistics below
+ *  violations   pairs with distortion > eps (distortion == eps is allowed)
+ *  overflow     pairs outside [hist_lo, hist_hi)
+ *  recomputed   pairs whose fast tensor/SIMT value was too close to a bin
+ *               edge, to eps, or too ill-conditioned, and were recomputed
+ *               exactly from coordinate differences
+ *  hist[b]      pairs with hist_lo + b*w <= distortion < hist_lo + (b+1)*w,
+ *               w = (hist_hi - hist_lo) / 64
+ *  max          largest distortion, at pair (argmax_i, argmax_j), i < j
+ *  mean         mean distortion over the non-degenerate pairs
+ *  max_err_bound   bound on |max - exact max| implied by the per-pair error
+ *                  bounds (<= 1e-5 by construction)
+ *  mean_err_bound  mean of the per-pair error bounds
+ *  Histogram and violation counts are exact except possibly for pairs whose
+ *  exact distortion lies within 1e-6 of a bin edge or of eps.
+ */
+typedef struct {
+    uint64_t pairs, degenerate, violations, overflow, recomputed;
+    uint64_t hist[ADAGIO_HIST_BINS];
+    double max, mean, max_err_bound, mean_err_bound;
+    int64_t argmax_i, argmax_j;
+    double hist_lo, hist_hi, eps;
+} adagio_cert;
+
+/*
+ * Options of adagio_fit.  Fill with adagio_default_fit_opts() first.
+ *  eps         > 0: search the smallest certified target dimension m (the
+ *              exhaustive certificate's maximum distortion <= eps) by
+ *              galloping (m = 16, 32, 64, ... capped at m_cap) and bisection;
+ *              <= 0: fit at the fixed dimension `m`
+ *  m           target dimension when eps <= 0
+ *  s           number of principal rows; -1 = floor(m/2) (Sec. 4.1)
+ *  seed        seed of the JL matrix and of the randomized PCA start block
+ *  jl_dist     ADAGIO_JL_RADEMACHER (default) or ADAGIO_JL_GAUSSIAN
+ *  precision   arithmetic of the certificate tiles (ADAGIO_PREC_*)
+ *  use_predictor  1: start from the dimension predictor's guess (needs a
+ *              trained predictor on the context), verify it with the
+ *              exhaustive certificate, and fall back to the search
+ *  hist_lo/hi  histogram range; hi <= lo selects [0, 2 eps) (or [0, 1))
+ *  max_iter, tol   subspace iteration stops when every Ritz residual
+ *              ||C v - theta v|| <= tol * theta_1 for the kept vectors
+ *  oversample  extra block columns of the subspace iteration (default 32)
+ */
+typedef struct {
+    double eps;
+    int m;
+    int s;
+    uint64_t seed;
+    int jl_dist;
+    int precision;
+    int use_predictor;
+    double hist_lo, hist_hi;
+    int max_iter;
+    double tol;
+    int oversample;
+} adagio_fit_opts;
+
+void adagio_default_fit_opts(adagio_fit_opts *opts);
+
+/* ----------------------------------------------------------------- context */
+/* Creates a context on CUDA device `device`.  workspace_limit = 0 means no
+ * limit; otherwise a call that would need more device workspace fails with
+ * ADAGIO_E_WORKSPACE.  Fails with ADAGIO_E_UNSUPPORTED on a device that is
+ * not compute capability 10.3.  *out is NULL on failure. */
+int adagio_ctx_create(int device, size_t workspace_limit, adagio_ctx **out);
+int adagio_ctx_destroy(adagio_ctx *ctx);
+/* Message of the last failure on ctx ("" if none).  The pointer stays valid
+ * until the next call on ctx.  NULL ctx gives the message of the last failed
+ * adagio_ctx_create on this thread. */
+const char *adagio_last_error(const adagio_ctx *ctx);
+/* Bytes of device workspace currently held by ctx. */
+size_t adagio_workspace_bytes(const adagio_ctx *ctx);
+
+/* ------------------------------------------------------------- certificate */
+/*
+ * Exhaustive distortion certificate of the map x_i -> y_i (Eq. 2, Eq. 3).
+ *  X  n x d (leading dimension ldx), Y  n x m (leading dimension ldy).
+ *  eps in (0, 1): violation threshold.  hist_hi <= hist_lo selects [0, 2 eps).
+ *  precision  ADAGIO_PREC_*.
+ * Never materialises the n x n matrix.  Synchronises `stream`.
+ * Errors: INVALID_ARG (n < 2, d < 1, m < 1, bad eps/range/pointers),
+ * NONFINITE, WORKSPACE, QUEUE_OVERFLOW, CUDA.
+ */
+int adagio_distortion(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
+                      const float *Y, int m, int64_t ldy, double eps, double hist_lo,
+                      double hist_hi, int precision, adagio_cert *out, void *stream);
+
+/* ------------------------------------------------------------------- embed */
+/*
+ * Y = X A^T: row i of Y is f(x_i) = A x_i (Algorithm 1's output for every w).
+ *  A  m x d (lda), X  n x d (ldx), Y  n x m (ldy), written in full.
+ * Errors: INVALID_ARG, CUDA, WORKSPACE (host arrays need staging).
+ */
+int adagio_embed(adagio_ctx *ctx, const float *A, int m, int d, int64_t lda,
+                 const float *X, int64_t n, int64_t ldx, float *Y, int64_t ldy,
+                 void *stream);
+
+/* --------------------------------------------------------------- fit steps */
+/*
+ * JL matrix S (k x d, lds >= d): entry (i, j) is +-1/sqrt(k) by the top bit of
+ * output number c = i*2^32 + 2j of the SplitMix64 stream seeded with `seed`
+ * (Steele, Lea & Flood 2014); Gaussian: Box-Muller from outputs c and c + 1.
+ * Row i does not depend on k except for the scale (Algorithm 1; Lemma 2).
+ */
+int adagio_jl_matrix(adagio_ctx *ctx, uint64_t seed, int k, int d, int jl_dist,
+                     float *S, int64_t lds, void *stream);
+
+/*
+ * Top-s principal directions of X (Sec. 2 "PCA"; randomized PCA, Sec. 4.5):
+ * randomized block subspace iteration on the covariance C = Xc^T Xc of the
+ * centred data, shifted CholeskyQR2 orthonormalisation and Rayleigh-Ritz.
+ *  P      s x d (ldp) orthonormal rows by decreasing eigenvalue; the entry of
+ *         largest magnitude of each row is positive
+ *  theta  s eigenvalue estimates of C (host or device, may be NULL)
+ *  opts   seed, max_iter, tol, oversample are used (NULL = defaults)
+ * Synchronises `stream`.  Errors: INVALID_ARG (s < 1 or s > d), NONFINITE,
+ * WORKSPACE, CUDA.
+ */
+int adagio_pca(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx, int s,
+               const adagio_fit_opts *opts, float *P, int64_t ldp, double *theta,
+               void *stream);
+
+/*
+ * A = [P ; S (I - P^T P)] (m = s + k rows, d columns, lda >= d): the matrix
+ * of Algorithm 1's map w -> (P w, S (w - P^T P w)).  s or k may be 0.
+ */
+int adagio_assemble(adagio_ctx *ctx, const float *P, int s, int64_t ldp, const float *S,
+                    int k, int64_t lds, int d, float *A, int64_t lda, void *stream);
+
+/* --------------------------------------------------------------------- fit */
+/*
+ * Fits the ADAGIO map of X.  With opts->eps > 0 the smallest certified target
+ * dimension found by the search is used (the paper's Table 3 question: how
+ * many dimensions reach distortion eps); otherwise opts->m.
+ *  A       output, m_cap x d (row-major, leading dimension d); the first
+ *          *m_out rows hold the map
+ *  m_cap   largest m allowed (<= d when eps > 0)
+ *  m_out, s_out   chosen m and its number of principal rows
+ *  cert    certificate of the returned map (may be NULL when eps <= 0)
+ * Synchronises `stream`.  Errors: INVALID_ARG, NONFINITE, WORKSPACE, CUDA,
+ * NOT_CERTIFIABLE (eps not reached at m_cap: A, m_out and cert still hold
+ * the map at m_cap and its certificate).
+ */
+int adagio_fit(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
+               const adagio_fit_opts *opts, float *A, int m_cap, int *m_out, int *s_out,
+               adagio_cert *cert, void *stream);
+
+/* ------------------------------------------------------------- diagnostics */
+/*
+ * Timing of the most recent certificate on ctx, taken with CUDA events on the
+ * caller's stream around each stage when timing is enabled
+ * (adagio_set_timing(ctx, 1); off by default, it adds one event pair per
+ * stage).  All times in milliseconds; -1 when not measured.
+ *  prep_ms       K0 (centring, split planes) of X and Y
+ *  tile_ms       K8, the all-pairs tile kernel
+ *  recompute_ms  K9 + K10 (exact recompute of queued pairs, finaliser)
+ *  queued        pairs sent to the exact recompute
+ *  grid          CTAs of the tile kernel; tiles = tile pairs it walked
+ */
+typedef struct {
+    double prep_ms, tile_ms, recompute_ms;
+    uint64_t queued;
+    int grid;
+    int64_t tiles;
+} adagio_cert_stats;
+
+int adagio_set_timing(adagio_ctx *ctx, int enable);
+int adagio_last_cert_stats(const adagio_ctx *ctx, adagio_cert_stats *out);
+
+/* Number of kernels this library has launched in this process (all contexts,
+ * all devices); a difference of two readings counts the launches between. */
+uint64_t adagio_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADAGIO_H */

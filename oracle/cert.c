@@ -42,13 +42,14 @@ typedef struct {
     int64_t argmax_i, argmax_j;
     double sum;            /* Neumaier sum of distortions                        */
     double sum_c;          /* its compensation term                              */
+    uint64_t near_edge;    /* pairs within edge_tol of a bin edge or of eps      */
 } oracle_cert_t;
 
 typedef struct {
     const double *X, *Y;
     int64_t ldx, ldy, n, row_begin, row_end;
     int d, m, nbins, tid, nthreads;
-    double eps, lo, hi;
+    double eps, lo, hi, edge_tol;
     oracle_cert_t res;
 } job_t;
 
@@ -71,7 +72,7 @@ static double sqdist(const double *a, const double *b, int len) {
 }
 
 static void record(oracle_cert_t *r, int64_t i, int64_t j, double dx2, double dy2,
-                   double eps, double lo, double hi, int nbins) {
+                   double eps, double lo, double hi, int nbins, double edge_tol) {
     r->pairs++;
     if (dx2 == 0.0) {
         r->degenerate++;
@@ -85,6 +86,15 @@ static void record(oracle_cert_t *r, int64_t i, int64_t j, double dx2, double dy
     }
     neumaier_add(&r->sum, &r->sum_c, delta);
     if (delta > eps) r->violations++;
+    if (edge_tol > 0.0) {
+        /* bookkeeping for comparisons: distance to the nearest edge lo + b*w */
+        double w = (hi - lo) / (double)nbins;
+        double t = (delta - lo) / w;
+        double tn = floor(t + 0.5);
+        int near = fabs(delta - eps) < edge_tol;
+        if (tn >= 0.0 && tn <= (double)nbins && fabs(delta - (lo + tn * w)) < edge_tol) near = 1;
+        if (near) r->near_edge++;
+    }
     if (delta < lo || delta >= hi) {
         r->overflow++;
     } else {
@@ -107,7 +117,7 @@ static void *worker(void *arg) {
         for (int64_t j = i + 1; j < jb->n; ++j) {
             double dx2 = sqdist(xi, jb->X + j * jb->ldx, jb->d);
             double dy2 = sqdist(yi, jb->Y + j * jb->ldy, jb->m);
-            record(r, i, j, dx2, dy2, jb->eps, jb->lo, jb->hi, jb->nbins);
+            record(r, i, j, dx2, dy2, jb->eps, jb->lo, jb->hi, jb->nbins, jb->edge_tol);
         }
     }
     return NULL;
@@ -121,7 +131,7 @@ static void *worker(void *arg) {
 int oracle_certificate(const double *X, int64_t ldx, const double *Y, int64_t ldy,
                        int64_t n, int d, int m, double eps, double lo, double hi,
                        int nbins, int64_t row_begin, int64_t row_end, int nthreads,
-                       oracle_cert_t *out) {
+                       double edge_tol, oracle_cert_t *out) {
     if (!X || !Y || !out || n < 0 || d < 1 || m < 1 || nbins < 1 ||
         nbins > ORACLE_MAX_BINS || !(hi > lo) || row_begin < 0 || row_end > n ||
         row_begin > row_end || ldx < d || ldy < m)
@@ -139,7 +149,7 @@ int oracle_certificate(const double *X, int64_t ldx, const double *Y, int64_t ld
         jb->X = X; jb->Y = Y; jb->ldx = ldx; jb->ldy = ldy; jb->n = n;
         jb->row_begin = row_begin; jb->row_end = row_end;
         jb->d = d; jb->m = m; jb->nbins = nbins; jb->tid = t; jb->nthreads = nthreads;
-        jb->eps = eps; jb->lo = lo; jb->hi = hi;
+        jb->eps = eps; jb->lo = lo; jb->hi = hi; jb->edge_tol = edge_tol;
     }
     for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, worker, &jobs[t]);
     worker(&jobs[0]);
@@ -153,6 +163,7 @@ int oracle_certificate(const double *X, int64_t ldx, const double *Y, int64_t ld
         out->degenerate += r->degenerate;
         out->violations += r->violations;
         out->overflow += r->overflow;
+        out->near_edge += r->near_edge;
         for (int b = 0; b < nbins; ++b) out->hist[b] += r->hist[b];
         neumaier_add(&out->sum, &out->sum_c, r->sum);
         neumaier_add(&out->sum, &out->sum_c, r->sum_c);

@@ -31,6 +31,7 @@ class _Cert(ctypes.Structure):
         ("argmax_j", ctypes.c_int64),
         ("sum", ctypes.c_double),
         ("sum_c", ctypes.c_double),
+        ("near_edge", ctypes.c_uint64),
     ]
 
 
@@ -48,6 +49,7 @@ class OracleCert:
     eps: float
     lo: float
     hi: float
+    near_edge: int = 0
     extra: dict = field(default_factory=dict)
 
     @property
@@ -83,7 +85,7 @@ def _load():
             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
             ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
             ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int64,
-            ctypes.c_int64, ctypes.c_int, ctypes.POINTER(_Cert)]
+            ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_Cert)]
         lib.oracle_pair_sqdist.restype = ctypes.c_int
         lib.oracle_pair_sqdist.argtypes = [
             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
@@ -99,13 +101,15 @@ def default_threads() -> int:
 
 def certificate(X: np.ndarray, Y: np.ndarray, eps: float, lo: float = 0.0,
                 hi: float | None = None, nbins: int = 64, rows=None,
-                threads: int | None = None) -> OracleCert:
+                threads: int | None = None, edge_tol: float = 1e-6) -> OracleCert:
     """FP64 all-pairs certificate of the map row i of X -> row i of Y.
 
     Inputs are widened to float64 (exact for float32 data).
 
     ``hi`` defaults to 2*eps (64 uniform bins on [0, 2 eps)).  ``rows=(a, b)``
-    restricts to pairs (i, j) with a <= i < b, i < j.
+    restricts to pairs (i, j) with a <= i < b, i < j.  ``near_edge`` counts the
+    pairs whose distortion lies within ``edge_tol`` of a bin edge or of eps (the
+    pairs a faithful implementation may bin either way).
     """
     X = np.ascontiguousarray(X, dtype=np.float64)
     Y = np.ascontiguousarray(Y, dtype=np.float64)
@@ -119,13 +123,13 @@ def certificate(X: np.ndarray, Y: np.ndarray, eps: float, lo: float = 0.0,
     res = _Cert()
     rc = _load().oracle_certificate(
         X.ctypes.data, d, Y.ctypes.data, m, n, d, m, float(eps), float(lo),
-        float(hi), nbins, a, b, threads or default_threads(), ctypes.byref(res))
+        float(hi), nbins, a, b, threads or default_threads(), float(edge_tol), ctypes.byref(res))
     if rc != 0:
         raise ValueError("oracle_certificate: bad arguments")
     return OracleCert(int(res.pairs), int(res.degenerate), int(res.violations),
                       int(res.overflow), np.array(res.hist[:nbins], dtype=np.int64),
                       float(res.max), int(res.argmax_i), int(res.argmax_j),
-                      float(res.sum), float(eps), float(lo), float(hi))
+                      float(res.sum), float(eps), float(lo), float(hi), int(res.near_edge))
 
 
 def pair_sqdist(X: np.ndarray, Y: np.ndarray, I, J):

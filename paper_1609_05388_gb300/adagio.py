@@ -1,0 +1,334 @@
+"""Thin Python binding of the C ABI in include/adagio.h (argument marshalling only).
+
+Arrays may be CUDA ``torch.Tensor``s (device path: the work is enqueued on the
+current torch stream), or host arrays (numpy or CPU tensors: the library copies
+them to the device and back inside the call).  Every computation runs in
+``libadagio.so``; if the library is missing this module raises on import.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libadagio.so")
+
+OK = 0
+E_INVALID_ARG = -1
+E_NONFINITE = -2
+E_CUDA = -3
+E_WORKSPACE = -4
+E_QUEUE_OVERFLOW = -5
+E_TIMEOUT = -6
+E_NOT_CERTIFIABLE = -7
+E_UNSUPPORTED = -8
+
+PREC_FP32 = 0
+PREC_FP16X3 = 1
+PREC_BF16X3 = 2
+JL_RADEMACHER = 0
+JL_GAUSSIAN = 1
+HIST_BINS = 64
+
+STATUS_NAMES = {0: "OK", -1: "INVALID_ARG", -2: "NONFINITE", -3: "CUDA", -4: "WORKSPACE",
+                -5: "QUEUE_OVERFLOW", -6: "TIMEOUT", -7: "NOT_CERTIFIABLE", -8: "UNSUPPORTED"}
+
+
+class CertStruct(ctypes.Structure):
+    _fields_ = [
+        ("pairs", ctypes.c_uint64), ("degenerate", ctypes.c_uint64),
+        ("violations", ctypes.c_uint64), ("overflow", ctypes.c_uint64),
+        ("recomputed", ctypes.c_uint64), ("hist", ctypes.c_uint64 * HIST_BINS),
+        ("max", ctypes.c_double), ("mean", ctypes.c_double),
+        ("max_err_bound", ctypes.c_double), ("mean_err_bound", ctypes.c_double),
+        ("argmax_i", ctypes.c_int64), ("argmax_j", ctypes.c_int64),
+        ("hist_lo", ctypes.c_double), ("hist_hi", ctypes.c_double), ("eps", ctypes.c_double),
+    ]
+
+
+class FitOptsStruct(ctypes.Structure):
+    _fields_ = [
+        ("eps", ctypes.c_double), ("m", ctypes.c_int), ("s", ctypes.c_int),
+        ("seed", ctypes.c_uint64), ("jl_dist", ctypes.c_int), ("precision", ctypes.c_int),
+        ("use_predictor", ctypes.c_int), ("hist_lo", ctypes.c_double),
+        ("hist_hi", ctypes.c_double), ("max_iter", ctypes.c_int), ("tol", ctypes.c_double),
+        ("oversample", ctypes.c_int),
+    ]
+
+
+class CertStatsStruct(ctypes.Structure):
+    _fields_ = [("prep_ms", ctypes.c_double), ("tile_ms", ctypes.c_double),
+                ("recompute_ms", ctypes.c_double), ("queued", ctypes.c_uint64),
+                ("grid", ctypes.c_int), ("tiles", ctypes.c_int64)]
+
+
+class AdagioError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"adagio error {code} ({STATUS_NAMES.get(code, '?')}): {msg}")
+        self.code = code
+
+
+@dataclass
+class Certificate:
+    pairs: int
+    degenerate: int
+    violations: int
+    overflow: int
+    recomputed: int
+    hist: np.ndarray
+    max: float
+    mean: float
+    max_err_bound: float
+    mean_err_bound: float
+    argmax_i: int
+    argmax_j: int
+    hist_lo: float
+    hist_hi: float
+    eps: float
+
+    @classmethod
+    def from_struct(cls, c: CertStruct) -> "Certificate":
+        return cls(int(c.pairs), int(c.degenerate), int(c.violations), int(c.overflow),
+                   int(c.recomputed), np.array(c.hist[:], dtype=np.int64), float(c.max),
+                   float(c.mean), float(c.max_err_bound), float(c.mean_err_bound),
+                   int(c.argmax_i), int(c.argmax_j), float(c.hist_lo), float(c.hist_hi),
+                   float(c.eps))
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with paper_1609_05388_gb300.build.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    sig = {
+        "adagio_ctx_create": (i32, [i32, ctypes.c_size_t, ctypes.POINTER(vp)]),
+        "adagio_ctx_destroy": (i32, [vp]),
+        "adagio_last_error": (ctypes.c_char_p, [vp]),
+        "adagio_workspace_bytes": (ctypes.c_size_t, [vp]),
+        "adagio_default_fit_opts": (None, [ctypes.POINTER(FitOptsStruct)]),
+        "adagio_distortion": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, f64, f64, f64, i32,
+                                    ctypes.POINTER(CertStruct), vp]),
+        "adagio_embed": (i32, [vp, vp, i32, i32, i64, vp, i64, i64, vp, i64, vp]),
+        "adagio_jl_matrix": (i32, [vp, ctypes.c_uint64, i32, i32, i32, vp, i64, vp]),
+        "adagio_pca": (i32, [vp, vp, i64, i32, i64, i32, ctypes.POINTER(FitOptsStruct), vp, i64,
+                             vp, vp]),
+        "adagio_assemble": (i32, [vp, vp, i32, i64, vp, i32, i64, i32, vp, i64, vp]),
+        "adagio_fit": (i32, [vp, vp, i64, i32, i64, ctypes.POINTER(FitOptsStruct), vp, i32,
+                             ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(CertStruct),
+                             vp]),
+        "adagio_set_timing": (i32, [vp, i32]),
+        "adagio_last_cert_stats": (i32, [vp, ctypes.POINTER(CertStatsStruct)]),
+        "adagio_launch_count": (ctypes.c_uint64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+LIB = _load()
+
+
+def exported_symbols() -> list[str]:
+    return [n for n in ("adagio_ctx_create", "adagio_ctx_destroy", "adagio_last_error",
+                        "adagio_workspace_bytes", "adagio_default_fit_opts", "adagio_distortion",
+                        "adagio_embed", "adagio_jl_matrix", "adagio_pca", "adagio_assemble",
+                        "adagio_fit", "adagio_set_timing", "adagio_last_cert_stats",
+                        "adagio_launch_count") if hasattr(LIB, n)]
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(LIB.adagio_launch_count())
+
+
+# ------------------------------------------------------------------ marshalling
+class _Arr:
+    """A 2-D float32 row-major array handed to the library (pointer + leading dim)."""
+
+    def __init__(self, a, writable: bool = False):
+        self.keep = a
+        if _is_torch(a):
+            import torch
+            if a.dtype != torch.float32:
+                raise TypeError("float32 tensors only")
+            if a.dim() == 1:
+                a = a.view(1, -1)
+            if a.stride(1) != 1:
+                raise ValueError("rows must be contiguous")
+            if not a.is_cuda and not a.is_contiguous():
+                raise ValueError("host tensors must be contiguous")
+            self.keep = a
+            self.ptr = a.data_ptr()
+            self.rows, self.cols = a.shape
+            self.ld = a.stride(0) if a.shape[0] > 1 else a.shape[1]
+            self.cuda = a.is_cuda
+        else:
+            arr = np.asarray(a)
+            if arr.dtype != np.float32 or not arr.flags.c_contiguous:
+                if writable:
+                    raise TypeError("output arrays must be C-contiguous float32")
+                arr = np.ascontiguousarray(arr, dtype=np.float32)
+            if arr.ndim == 1:
+                arr = arr.reshape(1, -1)
+            self.keep = arr
+            self.ptr = arr.ctypes.data
+            self.rows, self.cols = arr.shape
+            self.ld = arr.shape[1]
+            self.cuda = False
+
+
+def _is_torch(a) -> bool:
+    try:
+        import torch
+    except ImportError:
+        return False
+    return isinstance(a, torch.Tensor)
+
+
+def _stream(*arrs) -> int:
+    if any(getattr(a, "cuda", False) for a in arrs):
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return 0
+
+
+class Context:
+    """One library context on one CUDA device (owns the device workspace)."""
+
+    def __init__(self, device: int = 0, workspace_limit: int = 0):
+        h = ctypes.c_void_p()
+        rc = LIB.adagio_ctx_create(device, workspace_limit, ctypes.byref(h))
+        if rc != OK:
+            raise AdagioError(rc, LIB.adagio_last_error(None).decode())
+        self.h = h
+        self.device = device
+
+    def close(self):
+        if getattr(self, "h", None):
+            LIB.adagio_ctx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _check(self, rc: int, allow=()):
+        if rc != OK and rc not in allow:
+            raise AdagioError(rc, LIB.adagio_last_error(self.h).decode())
+        return rc
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(LIB.adagio_workspace_bytes(self.h))
+
+    def set_timing(self, enable: bool = True):
+        self._check(LIB.adagio_set_timing(self.h, 1 if enable else 0))
+
+    def last_cert_stats(self) -> dict:
+        st = CertStatsStruct()
+        self._check(LIB.adagio_last_cert_stats(self.h, ctypes.byref(st)))
+        return {"prep_ms": st.prep_ms, "tile_ms": st.tile_ms, "recompute_ms": st.recompute_ms,
+                "queued": int(st.queued), "grid": st.grid, "tiles": int(st.tiles)}
+
+    # -------------------------------------------------------------- certificate
+    def distortion(self, X, Y, eps: float, hist_lo: float = 0.0, hist_hi: float = 0.0,
+                   precision: int = PREC_FP16X3) -> Certificate:
+        x, y = _Arr(X), _Arr(Y)
+        if x.rows != y.rows:
+            raise ValueError("X and Y must have the same number of rows")
+        c = CertStruct()
+        self._check(LIB.adagio_distortion(self.h, x.ptr, x.rows, x.cols, x.ld, y.ptr, y.cols, y.ld,
+                                          eps, hist_lo, hist_hi, precision, ctypes.byref(c),
+                                          _stream(x, y)))
+        return Certificate.from_struct(c)
+
+    # -------------------------------------------------------------------- embed
+    def embed(self, A, X, Y=None):
+        a, x = _Arr(A), _Arr(X)
+        if Y is None:
+            if x.cuda:
+                import torch
+                Y = torch.empty((x.rows, a.rows), dtype=torch.float32, device=x.keep.device)
+            else:
+                Y = np.empty((x.rows, a.rows), dtype=np.float32)
+        y = _Arr(Y, writable=True)
+        self._check(LIB.adagio_embed(self.h, a.ptr, a.rows, a.cols, a.ld, x.ptr, x.rows, x.ld,
+                                     y.ptr, y.ld, _stream(a, x, y)))
+        return Y
+
+    # ---------------------------------------------------------------- fit steps
+    def jl_matrix(self, seed: int, k: int, d: int, dist: int = JL_RADEMACHER, out=None):
+        if out is None:
+            out = np.empty((k, d), dtype=np.float32)
+        o = _Arr(out, writable=True)
+        self._check(LIB.adagio_jl_matrix(self.h, seed, k, d, dist, o.ptr, o.ld, _stream(o)))
+        return out
+
+    def pca(self, X, s: int, opts: FitOptsStruct | None = None, P=None):
+        x = _Arr(X)
+        if P is None:
+            P = np.empty((s, x.cols), dtype=np.float32)
+        p = _Arr(P, writable=True)
+        theta = np.empty(s, dtype=np.float64)
+        self._check(LIB.adagio_pca(self.h, x.ptr, x.rows, x.cols, x.ld, s,
+                                   ctypes.byref(opts) if opts is not None else None, p.ptr, p.ld,
+                                   theta.ctypes.data, _stream(x, p)))
+        return P, theta
+
+    def assemble(self, P, S, A=None):
+        p = _Arr(P) if P is not None and np.size(P) else None
+        s_ = _Arr(S) if S is not None and np.size(S) else None
+        d = (p or s_).cols
+        s, k = (p.rows if p else 0), (s_.rows if s_ else 0)
+        if A is None:
+            A = np.empty((s + k, d), dtype=np.float32)
+        a = _Arr(A, writable=True)
+        self._check(LIB.adagio_assemble(self.h, p.ptr if p else None, s, p.ld if p else d,
+                                        s_.ptr if s_ else None, k, s_.ld if s_ else d, d, a.ptr,
+                                        a.ld, _stream(a, *(v for v in (p, s_) if v))))
+        return A
+
+    # ---------------------------------------------------------------------- fit
+    @staticmethod
+    def default_opts(**kw) -> FitOptsStruct:
+        o = FitOptsStruct()
+        LIB.adagio_default_fit_opts(ctypes.byref(o))
+        for k, v in kw.items():
+            setattr(o, k, v)
+        return o
+
+    def fit(self, X, eps: float = 0.1, m: int = 0, m_cap: int | None = None, A=None,
+            opts: FitOptsStruct | None = None, **kw):
+        """Returns (A[:m], m, s, certificate, status)."""
+        x = _Arr(X)
+        o = opts if opts is not None else self.default_opts(eps=eps, m=m, **kw)
+        if opts is None and eps <= 0:
+            o.eps = 0.0
+        if m_cap is None:
+            m_cap = x.cols if o.eps > 0 else o.m
+        if A is None:
+            if x.cuda:
+                import torch
+                A = torch.empty((m_cap, x.cols), dtype=torch.float32, device=x.keep.device)
+            else:
+                A = np.empty((m_cap, x.cols), dtype=np.float32)
+        a = _Arr(A, writable=True)
+        mo, so = ctypes.c_int(0), ctypes.c_int(0)
+        c = CertStruct()
+        rc = self._check(LIB.adagio_fit(self.h, x.ptr, x.rows, x.cols, x.ld, ctypes.byref(o), a.ptr,
+                                        m_cap, ctypes.byref(mo), ctypes.byref(so), ctypes.byref(c),
+                                        _stream(x, a)), allow=(E_NOT_CERTIFIABLE,))
+        return A[: mo.value], mo.value, so.value, Certificate.from_struct(c), rc

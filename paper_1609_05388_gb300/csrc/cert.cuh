@@ -1,0 +1,67 @@
+// Certificate pipeline: launch descriptors shared by the tile kernels, the
+// exact recompute and the finaliser.
+#pragma once
+
+#include "internal.cuh"
+#include "cert_common.cuh"
+#include "prep.cuh"
+
+namespace adagio {
+
+struct CertLaunch {
+    const PrepMat *x = nullptr;
+    const PrepMat *y = nullptr;
+    CertConst cc{};
+    CertPartial *partials = nullptr;  // [grid]
+    int grid = 0;
+    int2 *queue = nullptr;
+    unsigned long long *qcount = nullptr;
+    unsigned long long qcap = 0;
+    int *stop_flag = nullptr;         // early exit (search probes) or null
+    int *status = nullptr;            // device status word (timeouts)
+};
+
+// Device-side result of the finaliser (host copies it back).
+struct CertDevResult {
+    unsigned long long hist[kBins];
+    unsigned long long fast_pairs, queued, recomputed, degenerate, violations, overflow;
+    double sum, bound_sum;
+    float max, max_bound;
+    int argmax_i, argmax_j;
+    unsigned flags;
+    int status;
+    int stopped;  // the early-exit flag fired: statistics are partial
+};
+
+void launch_cert_simt(const CertLaunch &L, cudaStream_t st);
+int cert_simt_threads();
+// tcgen05 tile kernel; returns false when the shape is not supported
+bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st);
+int cert_tc_grid(adagio_ctx *ctx);
+
+// Exact recompute of the queued pairs from the original (uncentred) inputs.
+void launch_recompute(const float *X, int64_t ldx, int d, const float *Y, int64_t ldy, int m,
+                      const int2 *queue, const unsigned long long *qcount,
+                      unsigned long long qcap, CertConst cc, CertPartial *partials, int grid,
+                      cudaStream_t st);
+
+void launch_finalize(const CertPartial *fast, int nfast, const CertPartial *rec, int nrec,
+                     const unsigned long long *qcount, const unsigned *flags, const int *status,
+                     const int *stop_flag, CertDevResult *out, cudaStream_t st);
+
+// Full certificate of (X, Y) given device pointers.  Fills `out`; returns the
+// status (ADAGIO_OK, ADAGIO_E_NONFINITE, ...).  stop_early: the tile kernels
+// stop at the first certain violation (a search probe only needs max > eps),
+// in which case the statistics are partial and only out->max > eps is
+// meaningful.  Synchronises `st`.
+struct CertOptions {
+    double eps = 0.1, lo = 0.0, hi = 0.2;
+    int precision = ADAGIO_PREC_FP16X3;
+    bool stop_early = false;
+};
+int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_t ldy, int64_t n,
+            int d, int m, const CertOptions &opt, adagio_cert *out, cudaStream_t st,
+            bool *stopped = nullptr);
+size_t certify_bytes(adagio_ctx *ctx, int64_t n, int d, int m, int precision);
+
+}  // namespace adagio

@@ -1,0 +1,175 @@
+// K8 (plain FP32 path): all-pairs distortion tiles on CUDA cores.
+//
+// Each CTA walks 128 x 128 tiles (I, J), I <= J, of the upper triangle of the
+// pair matrix (Eq. 3 is a max over unordered pairs) in a persistent,
+// round-robin loop.  For every tile it forms the two Gram tiles
+// Gy = Yc[I] Yc[J]^T and Gx = Xc[I] Xc[J]^T in FP32 (128x128x8 smem stages,
+// an 8 x 8 register block per thread), then classifies each pair with the
+// shared epilogue (cert_common.cuh).  The n x n matrix is never stored.
+#include "internal.cuh"
+#include "cert_common.cuh"
+#include "cert.cuh"
+
+namespace adagio {
+
+namespace {
+
+constexpr int BM = 128, BK = 8, NT = 256, PADS = 4;
+
+struct SimtArgs {
+    const float *Xc;
+    const float *Yc;
+    int ldx, ldy;      // = Kp32 of each side (multiple of 8)
+    int Kx, Ky;        // padded contraction lengths
+    const RowStat *rsx, *rsy;
+    int n, T;
+    long long ntp;     // number of tile pairs
+    CertConst cc;
+    CertPartial *partials;
+    int2 *queue;
+    unsigned long long *qcount, qcap;
+    int *stop_flag;    // non-null: early exit on a certain violation
+};
+
+// acc[a][b] += rows(I) . rows(J) over K, for the thread's 8 x 8 block.
+__device__ __forceinline__ void gram_tile(const float *__restrict__ M, int ld, int K, int rowI,
+                                          int rowJ, float (*As)[BK][BM + PADS],
+                                          float (*Bs)[BK][BM + PADS], float acc[8][8]) {
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+    const int lr = tid >> 1, lk = (tid & 1) * 4;
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+    const float *pa = M + (int64_t)(rowI + lr) * ld + lk;
+    const float *pb = M + (int64_t)(rowJ + lr) * ld + lk;
+    float4 ra = *reinterpret_cast<const float4 *>(pa);
+    float4 rb = *reinterpret_cast<const float4 *>(pb);
+    int buf = 0;
+    for (int k0 = 0; k0 < K; k0 += BK) {
+        As[buf][lk + 0][lr] = ra.x; As[buf][lk + 1][lr] = ra.y;
+        As[buf][lk + 2][lr] = ra.z; As[buf][lk + 3][lr] = ra.w;
+        Bs[buf][lk + 0][lr] = rb.x; Bs[buf][lk + 1][lr] = rb.y;
+        Bs[buf][lk + 2][lr] = rb.z; Bs[buf][lk + 3][lr] = rb.w;
+        __syncthreads();
+        if (k0 + BK < K) {
+            ra = *reinterpret_cast<const float4 *>(pa + k0 + BK);
+            rb = *reinterpret_cast<const float4 *>(pb + k0 + BK);
+        }
+#pragma unroll
+        for (int kk = 0; kk < BK; ++kk) {
+            float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
+            float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
+            float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
+            float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+            float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+        }
+        buf ^= 1;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(NT, 1) cert_simt_kernel(SimtArgs p) {
+    __shared__ __align__(16) float As[2][BK][BM + PADS];
+    __shared__ __align__(16) float Bs[2][BK][BM + PADS];
+    __shared__ RowStat sIx[BM], sIy[BM], sJx[BM], sJy[BM];
+    extern __shared__ unsigned s_hist[];  // [kBins][NT]
+
+    const int tid = threadIdx.x;
+    const int ty = tid >> 4, tx = tid & 15;
+    for (int b = 0; b < kBins; ++b) s_hist[b * NT + tid] = 0;
+
+    unsigned long long npairs = 0, nviol = 0, nover = 0, nqueued = 0;
+    double sum = 0.0, bsum = 0.0;
+    float mx = -1.0f, mxb_all = 0.0f;
+    int ai = 0x7fffffff, aj = 0x7fffffff;
+    float gx[8][8], gy[8][8];
+
+    __shared__ int s_stop;
+    for (long long t = blockIdx.x; t < p.ntp; t += gridDim.x) {
+        // block-uniform early-exit decision; also orders the previous tile's
+        // epilogue reads of the row statistics before they are overwritten
+        __syncthreads();
+        if (tid == 0) s_stop = p.stop_flag ? *(volatile int *)p.stop_flag : 0;
+        __syncthreads();
+        if (s_stop) break;
+        int I, J;
+        tri_index(t, p.T, I, J);
+        const int rowI = I * BM, rowJ = J * BM;
+        if (tid < BM) {
+            sIx[tid] = p.rsx[rowI + tid];
+            sIy[tid] = p.rsy[rowI + tid];
+            sJx[tid] = p.rsx[rowJ + tid];
+            sJy[tid] = p.rsy[rowJ + tid];
+        }
+        gram_tile(p.Yc, p.ldy, p.Ky, rowI, rowJ, As, Bs, gy);
+        gram_tile(p.Xc, p.ldx, p.Kx, rowI, rowJ, As, Bs, gx);
+
+        float tsum = 0.0f, tbsum = 0.0f;
+        bool stop = false;
+#pragma unroll
+        for (int a = 0; a < 8; ++a) {
+            const int li = ty * 4 + (a & 3) + (a >> 2) * 64;
+            const int i = rowI + li;
+            const RowStat xi = sIx[li], yi = sIy[li];
+#pragma unroll
+            for (int b = 0; b < 8; ++b) {
+                const int lj = tx * 4 + (b & 3) + (b >> 2) * 64;
+                const int j = rowJ + lj;
+                FastPair fp;
+                int cls = PAIR_SKIP;
+                if (i < j && j < p.n) cls = classify_pair(gx[a][b], gy[a][b], xi, sJx[lj], yi, sJy[lj], p.cc, fp);
+                queue_push(cls == PAIR_QUEUE, i, j, p.queue, p.qcount, p.qcap);
+                if (cls == PAIR_OK) {
+                    ++npairs;
+                    if (fp.bin >= 0) s_hist[fp.bin * NT + tid] += 1u; else ++nover;
+                    nviol += fp.violation;
+                    tsum += fp.delta;
+                    tbsum += fp.bound;
+                    mxb_all = fmaxf(mxb_all, fp.bound);
+                    if (better_max(fp.delta, i, j, mx, ai, aj)) { mx = fp.delta; ai = i; aj = j; }
+                    stop |= fp.delta > p.cc.eps + fp.bound;
+                } else if (cls == PAIR_QUEUE) {
+                    ++nqueued;
+                }
+            }
+        }
+        sum += (double)tsum;
+        bsum += (double)tbsum;
+        if (p.stop_flag && stop) atomicExch(p.stop_flag, 1);
+    }
+    write_partial<NT>(p.partials + blockIdx.x, s_hist, npairs, nviol, nover, nqueued, 0ull, sum,
+                      bsum, mx, mxb_all, ai, aj);
+}
+
+}  // namespace
+
+void launch_cert_simt(const CertLaunch &L, cudaStream_t st) {
+    SimtArgs p;
+    p.Xc = L.x->c32; p.Yc = L.y->c32;
+    p.ldx = L.x->Kp32; p.ldy = L.y->Kp32;
+    p.Kx = L.x->Kp32; p.Ky = L.y->Kp32;
+    p.rsx = L.x->rs; p.rsy = L.y->rs;
+    p.n = (int)L.x->n;
+    p.T = (int)(L.x->n_pad / BM);
+    p.ntp = (long long)p.T * (p.T + 1) / 2;
+    p.cc = L.cc;
+    p.partials = L.partials;
+    p.queue = L.queue; p.qcount = L.qcount; p.qcap = L.qcap;
+    p.stop_flag = L.stop_flag;
+    const size_t smem = (size_t)kBins * NT * sizeof(unsigned);
+    ADAGIO_CUDA(cudaFuncSetAttribute(cert_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+    cert_simt_kernel<<<L.grid, NT, smem, st>>>(p);
+    ADAGIO_CHECK_LAUNCH();
+}
+
+int cert_simt_threads() { return NT; }
+
+}  // namespace adagio

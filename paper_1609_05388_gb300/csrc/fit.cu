@@ -1,0 +1,231 @@
+// Fit of the ADAGIO map (Algorithm 1 with the Sec. 4.1 split) and the
+// certified search for the smallest target dimension (the question Table 3
+// answers: how many dimensions reach distortion eps).
+//
+// Search: probe r = 16, 32, 64, ... (the last probe is m_cap) until the
+// exhaustive certificate's maximum is <= eps, then bisect between the last
+// failing and the first passing probe with mid = floor((lo + hi) / 2).  Each
+// probe builds A_r = [P_s ; S_k (I - P_s^T P_s)] with s = floor(r/2),
+// k = ceil(r/2) (P_s is a prefix of the incrementally computed principal
+// rows; S_k is a prefix of the counter-generated JL rows, rescaled), embeds
+// Y = X A_r^T and certifies it.  A failing probe stops at the first certain
+// violation.  Passing probes are complete certificates.
+#include "internal.cuh"
+#include "cert.cuh"
+#include "fit.cuh"
+#include "jl.cuh"
+#include "linalg.cuh"
+#include "pca.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+namespace adagio {
+
+void assemble(const float *P, int s, int64_t ldp, const float *S, int k, int64_t lds, int d,
+              float *A, int64_t lda, float *T, cudaStream_t st) {
+    if (s > 0) copy_rows(P, ldp, A, lda, s, d, st);
+    if (k == 0) return;
+    float *AS = A + (int64_t)s * lda;
+    copy_rows(S, lds, AS, lda, k, d, st);
+    if (s == 0) return;
+    // T = S P^T (k x s);  A_S = S - T P
+    gemm<float, float, float, float>(k, s, d, 1.0f, MatView<float>{S, lds, 1},
+                                     MatView<float>{P, 1, ldp}, 0.0f, T, s, st);
+    gemm<float, float, float, float>(k, d, s, -1.0f, MatView<float>{T, s, 1},
+                                     MatView<float>{P, ldp, 1}, 1.0f, AS, lda, st);
+}
+
+size_t fit_bytes(adagio_ctx *ctx, int64_t n, int d, int s_cap, int k_cap, int m_cap, int precision,
+                 int oversample) {
+    size_t b = pca_bytes(n, d, s_cap, oversample);
+    b += align_up((size_t)std::max(k_cap, 1) * d * sizeof(float), 256);          // S
+    b += 2 * align_up((size_t)std::max(m_cap, 1) * d * sizeof(float), 256);      // A probe, A best
+    b += align_up((size_t)std::max(k_cap, 1) * std::max(s_cap, 1) * sizeof(float), 256);  // T
+    b += align_up((size_t)n * std::max(m_cap, 1) * sizeof(float), 256);          // Y
+    b += certify_bytes(ctx, n, d, std::max(m_cap, 1), precision);
+    return b + 65536;
+}
+
+namespace {
+
+struct Prober {
+    adagio_ctx *ctx;
+    const float *X;
+    int64_t ldx, n;
+    int d;
+    const adagio_fit_opts *o;
+    PCA *pca;
+    float *S, *A, *Abest, *T, *Y;
+    CertOptions copt;
+    int fixed_s;  // >= 0: every probe uses this many principal rows
+    struct Rec {
+        int r;
+        bool ok;
+        double max;
+    };
+    std::vector<Rec> probes;
+    int best_r = -1, best_s = 0;
+    adagio_cert best_cert{};
+    int last_r = -1, last_s = 0;
+    adagio_cert last_cert{};
+
+    int split_s(int r) const { return fixed_s >= 0 ? std::min(fixed_s, r) : r / 2; }
+
+    // builds A_r into A (m = r rows, ld d)
+    void build(int r, cudaStream_t st) {
+        const int s = split_s(r), k = r - s;
+        if (s > 0) pca->extend(s, st);
+        if (k > 0) jl_matrix(o->seed, k, d, o->jl_dist, S, d, st);
+        assemble(pca->P, s, d, S, k, d, d, A, d, T, st);
+    }
+
+    bool probe(int r, bool stop_early, cudaStream_t st) {
+        build(r, st);
+        embed_gemm(X, ldx, n, d, A, d, r, Y, r, st);
+        adagio_cert c;
+        CertOptions co = copt;
+        co.stop_early = stop_early;
+        bool stopped = false;
+        certify(ctx, X, ldx, Y, r, n, d, r, co, &c, st, &stopped);
+        const bool ok = !stopped && c.max <= copt.eps;
+        probes.push_back({r, ok, c.max});
+        last_r = r;
+        last_s = split_s(r);
+        last_cert = c;
+        if (ok && (best_r < 0 || r < best_r)) {
+            best_r = r;
+            best_s = split_s(r);
+            best_cert = c;
+            ADAGIO_CUDA(cudaMemcpyAsync(Abest, A, sizeof(float) * (size_t)r * d,
+                                        cudaMemcpyDeviceToDevice, st));
+        }
+        return ok;
+    }
+};
+
+}  // namespace
+
+int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
+               const adagio_fit_opts *o, float *A_out, int m_cap, int *m_out, int *s_out,
+               adagio_cert *cert, cudaStream_t st, FitTrace *trace) {
+    const bool search = o->eps > 0.0;
+    int cap, s_cap, k_cap;
+    if (search) {
+        cap = std::min(m_cap, d);
+        if (o->s >= 0) {
+            s_cap = std::min(o->s, cap);
+            k_cap = cap;
+        } else {
+            s_cap = cap / 2;
+            k_cap = cap - cap / 2;
+        }
+    } else {
+        cap = o->m;
+        s_cap = o->s >= 0 ? o->s : o->m / 2;
+        k_cap = o->m - s_cap;
+    }
+    const size_t mark = ctx->ws.off;
+    PCA pca;
+    pca.init(ctx, X, n, d, ldx, s_cap, o->seed, o->max_iter, o->tol, o->oversample, st);
+    Prober pr{};
+    pr.ctx = ctx;
+    pr.X = X;
+    pr.ldx = ldx;
+    pr.n = n;
+    pr.d = d;
+    pr.o = o;
+    pr.pca = &pca;
+    pr.S = ws_array<float>(ctx, (size_t)std::max(k_cap, 1) * d);
+    pr.A = ws_array<float>(ctx, (size_t)std::max(cap, 1) * d);
+    pr.Abest = ws_array<float>(ctx, (size_t)std::max(cap, 1) * d);
+    pr.T = ws_array<float>(ctx, (size_t)std::max(k_cap, 1) * std::max(s_cap, 1));
+    pr.Y = ws_array<float>(ctx, (size_t)n * std::max(cap, 1));
+    const double eps = search ? o->eps : 0.1;
+    pr.copt.eps = eps;
+    pr.copt.precision = o->precision;
+    if (o->hist_hi > o->hist_lo) {
+        pr.copt.lo = o->hist_lo;
+        pr.copt.hi = o->hist_hi;
+    } else {
+        pr.copt.lo = 0.0;
+        pr.copt.hi = search ? 2.0 * eps : 1.0;
+    }
+    pr.fixed_s = o->s;
+
+    int status = ADAGIO_OK;
+    int r_final, s_final;
+    if (!search) {
+        pr.build(cap, st);
+        if (cert) {
+            embed_gemm(X, ldx, n, d, pr.A, d, cap, pr.Y, cap, st);
+            certify(ctx, X, ldx, pr.Y, cap, n, d, cap, pr.copt, cert, st);
+        }
+        ADAGIO_CUDA(cudaMemcpyAsync(A_out, pr.A, sizeof(float) * (size_t)cap * d,
+                                    cudaMemcpyDeviceToDevice, st));
+        r_final = cap;
+        s_final = pr.split_s(cap);
+    } else {
+        const int start = (trace && trace->start_r > 0) ? std::min(trace->start_r, cap) : 0;
+        int last_fail = 0, first_ok = -1;
+        if (start > 0) {
+            // a predicted dimension is verified first; on failure the search
+            // continues above it
+            if (pr.probe(start, true, st)) first_ok = start; else last_fail = start;
+        }
+        if (first_ok < 0) {
+            std::vector<int> seq;
+            for (int r = 16; r < cap; r *= 2)
+                if (r > last_fail) seq.push_back(r);
+            seq.push_back(cap);
+            for (int r : seq) {
+                if (pr.probe(r, true, st)) {
+                    first_ok = r;
+                    break;
+                }
+                last_fail = r;
+            }
+        }
+        const bool accept_prediction = trace && trace->verify_only && first_ok == start && start > 0;
+        if (first_ok >= 0 && !accept_prediction) {
+            int lo = last_fail, hi = first_ok;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) / 2;
+                if (pr.probe(mid, true, st)) hi = mid; else lo = mid;
+            }
+        }
+        if (pr.best_r > 0) {
+            r_final = pr.best_r;
+            s_final = pr.best_s;
+            if (cert) *cert = pr.best_cert;
+            ADAGIO_CUDA(cudaMemcpyAsync(A_out, pr.Abest, sizeof(float) * (size_t)r_final * d,
+                                        cudaMemcpyDeviceToDevice, st));
+        } else {
+            // not certifiable at the cap: return the map at the cap and its full certificate
+            pr.build(cap, st);
+            embed_gemm(X, ldx, n, d, pr.A, d, cap, pr.Y, cap, st);
+            adagio_cert c;
+            certify(ctx, X, ldx, pr.Y, cap, n, d, cap, pr.copt, &c, st);
+            if (cert) *cert = c;
+            ADAGIO_CUDA(cudaMemcpyAsync(A_out, pr.A, sizeof(float) * (size_t)cap * d,
+                                        cudaMemcpyDeviceToDevice, st));
+            r_final = cap;
+            s_final = pr.split_s(cap);
+            status = ADAGIO_E_NOT_CERTIFIABLE;
+        }
+    }
+    if (m_out) *m_out = r_final;
+    if (s_out) *s_out = s_final;
+    if (trace) {
+        trace->probes.clear();
+        for (const auto &p : pr.probes) trace->probes.push_back({p.r, p.ok ? 1 : 0, p.max});
+        trace->pca_iterations = pca.iterations;
+        trace->s_computed = pca.s_done;
+    }
+    ADAGIO_CUDA(cudaStreamSynchronize(st));
+    ctx->ws.off = mark;
+    return status;
+}
+
+}  // namespace adagio

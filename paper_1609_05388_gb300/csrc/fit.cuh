@@ -1,0 +1,48 @@
+#pragma once
+
+#include <vector>
+
+#include "internal.cuh"
+
+namespace adagio {
+
+struct FitProbe {
+    int r;
+    int ok;
+    double max;
+};
+
+// Optional trace of a fit: the probes of the search, the PCA effort, and a
+// predicted starting dimension (verified first; the search continues above
+// it on failure).
+struct FitTrace {
+    int start_r = 0;
+    bool verify_only = false;  // with start_r: accept start_r if it passes
+    std::vector<FitProbe> probes;
+    int pca_iterations = 0;
+    int s_computed = 0;
+};
+
+// A = [P ; S (I - P^T P)] (Algorithm 1); T is k x s scratch.
+void assemble(const float *P, int s, int64_t ldp, const float *S, int k, int64_t lds, int d,
+              float *A, int64_t lda, float *T, cudaStream_t st);
+
+size_t fit_bytes(adagio_ctx *ctx, int64_t n, int d, int s_cap, int k_cap, int m_cap, int precision,
+                 int oversample);
+
+// Fit on device data; A_out (device) gets m x d rows with leading dimension d.
+int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
+               const adagio_fit_opts *o, float *A_out, int m_cap, int *m_out, int *s_out,
+               adagio_cert *cert, cudaStream_t st, FitTrace *trace);
+
+// Public-argument fit (checks, staging) with an optional trace.
+int fit_entry(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
+              const adagio_fit_opts *opts, float *A, int m_cap, int *m_out, int *s_out,
+              adagio_cert *cert, void *stream, FitTrace *trace);
+
+// Fit that starts from the dimension predictor's guess (mlp.cu).
+int fit_predicted(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
+                  const adagio_fit_opts *opts, float *A, int m_cap, int *m_out, int *s_out,
+                  adagio_cert *cert, void *stream);
+
+}  // namespace adagio

@@ -1,0 +1,126 @@
+// Internal runtime of the ADAGIO library: context, workspace arena, status
+// handling and the launch helpers shared by every translation unit.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "adagio.h"
+
+namespace adagio {
+
+constexpr int kBins = ADAGIO_HIST_BINS;
+
+// Thrown only inside the library; every C entry point catches it and turns it
+// into a status code, so nothing crosses the ABI.
+struct Error {
+    int code;
+    std::string msg;
+};
+
+[[noreturn]] void fail(int code, const char *fmt, ...);
+
+#define ADAGIO_CUDA(call)                                                          \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            ::adagio::fail(ADAGIO_E_CUDA, "%s failed: %s (%s:%d)", #call,          \
+                           cudaGetErrorString(e_), __FILE__, __LINE__);            \
+    } while (0)
+
+// Every kernel launch is followed by this check; it also counts launches.
+void count_launch();
+#define ADAGIO_CHECK_LAUNCH()                 \
+    do {                                      \
+        ::adagio::count_launch();             \
+        ADAGIO_CUDA(cudaGetLastError());      \
+    } while (0)
+
+#define ADAGIO_REQUIRE(cond, ...)                                                  \
+    do {                                                                           \
+        if (!(cond)) ::adagio::fail(ADAGIO_E_INVALID_ARG, __VA_ARGS__);            \
+    } while (0)
+
+// Device workspace: one growable buffer, carved per call by a bump pointer.
+// Growth frees the old buffer after synchronising the device, so a call must
+// reserve its whole need before launching anything that uses it.
+struct Workspace {
+    char *base = nullptr;
+    size_t cap = 0;
+    size_t off = 0;
+    size_t limit = 0;  // 0 = unlimited
+};
+
+struct Predictor;  // dimension predictor (mlp.cu)
+
+}  // namespace adagio
+
+struct adagio_ctx {
+    int device = 0;
+    int num_sms = 0;
+    adagio::Workspace ws;
+    std::string last_error;
+    // pinned host staging for small device->host results
+    void *host_stage = nullptr;
+    size_t host_stage_bytes = 0;
+    // device-side scalars reused by kernels (flags, counters)
+    adagio::Predictor *predictor = nullptr;
+    // statistics of the most recent certificate (for diagnostics)
+    adagio_cert_stats last_stats{-1.0, -1.0, -1.0, 0, 0, 0};
+    int collect_timing = 0;
+};
+
+namespace adagio {
+
+// RAII device selection for the duration of an entry point.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        cudaGetDevice(&prev);
+        if (prev != dev) ADAGIO_CUDA(cudaSetDevice(dev));
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+// Workspace management -------------------------------------------------------
+void ws_reset(adagio_ctx *ctx);
+void ws_reserve(adagio_ctx *ctx, size_t bytes);           // capacity >= bytes
+void *ws_alloc(adagio_ctx *ctx, size_t bytes, size_t align = 256);
+template <typename T>
+T *ws_array(adagio_ctx *ctx, size_t count) {
+    return reinterpret_cast<T *>(ws_alloc(ctx, count * sizeof(T)));
+}
+void *host_stage(adagio_ctx *ctx, size_t bytes);
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+// Pointer kinds ----------------------------------------------------------------
+bool is_device_ptr(const void *p, int device);
+
+// Input staging: returns a device pointer to a row-major n x cols matrix with
+// leading dimension *ld_out.  Host input is copied into the workspace.
+const float *stage_input(adagio_ctx *ctx, const float *p, int64_t rows, int cols, int64_t ld,
+                         int64_t *ld_out, cudaStream_t st);
+
+// Error-bound constants of the pair distortion for one Gram arithmetic (see
+// cert_common.cuh).
+struct BoundModel {
+    float c4;    // statistical product-error coefficient (times ||a||_4 ||b||_4)
+    float cacc;  // accumulation coefficient (times ||a||_2 ||b||_2)
+};
+BoundModel bound_model(int precision, int K);
+
+// Releases the dimension predictor held by a context (mlp.cu).
+void free_predictor(adagio_ctx *ctx);
+
+}  // namespace adagio

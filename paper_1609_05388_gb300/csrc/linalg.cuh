@@ -1,0 +1,60 @@
+// Dense linear-algebra building blocks of the fit (randomized PCA, Algorithm
+// 1's assembly, the embedding).  All matrices live in device memory.
+#pragma once
+
+#include "internal.cuh"
+
+namespace adagio {
+
+// Strided matrix view: element (i, k) at p[i * rs + k * cs].
+template <typename T>
+struct MatView {
+    const T *p;
+    int64_t rs, cs;
+};
+
+// C[M x N] = alpha * A[M x K] * B[K x N] + beta * C, accumulating in TACC.
+// Strides are arbitrary; C is row-major with leading dimension ldc.
+template <typename TA, typename TB, typename TC, typename TACC>
+void gemm(int M, int N, int K, TACC alpha, MatView<TA> A, MatView<TB> B, TACC beta, TC *C,
+          int64_t ldc, cudaStream_t st);
+
+// C[M x N] (FP32) = A^T B for tall A (K x M) and B (K x N) row-major with K
+// rows (the covariance Xc^T Xc), split over K into FP32 partials that are
+// summed in FP64.  `partials` must hold chunks(K) * M * N floats.
+void gemm_tn_splitk(int M, int N, int64_t K, const float *A, int64_t lda, const float *B,
+                    int64_t ldb, float *C, int64_t ldc, float *partials, cudaStream_t st);
+int64_t splitk_chunks(int64_t K);
+
+// Y[n x m] = X[n x d] A[m x d]^T, both row-major (the embedding, Algorithm 1).
+void embed_gemm(const float *X, int64_t ldx, int64_t n, int d, const float *A, int64_t lda, int m,
+                float *Y, int64_t ldy, cudaStream_t st);
+
+// Cholesky factorisation in place of an SPD b x b FP64 matrix (upper factor R,
+// G = R^T R), one CTA.  Pivots below `floor_rel * max diagonal` are raised
+// to it (shifted CholeskyQR guard).
+void cholesky_upper(double *G, int b, double floor_rel, cudaStream_t st);
+
+// V (b x d rows, FP32, leading dimension ldv) <- R^{-T} V, i.e. row i of the
+// result is (v_i - sum_{k<i} R_ki r_k) / R_ii; FP64 arithmetic.
+void trsm_rows(const double *R, int b, float *V, int64_t ldv, int d, cudaStream_t st);
+
+// Symmetric eigen-decomposition of a b x b matrix (b <= kJacobiMax) by
+// parallel cyclic Jacobi in one CTA: H (FP64 in) -> theta (descending, FP64
+// out) and U (b x b FP32 row-major, column c = eigenvector of theta[c]).
+constexpr int kJacobiMax = 160;
+void jacobi_eig(const double *H, int b, double *theta, float *U, int max_sweeps, cudaStream_t st);
+
+// Per-row residual norms ||W_i - theta_i V_i|| for i < s (FP32 out).
+void ritz_residuals(const float *W, const float *V, int64_t ld, int d, const double *theta, int s,
+                    float *res, cudaStream_t st);
+
+// Flip the sign of each row of P (s x d) so its largest-magnitude entry
+// (lowest index on ties) is positive.
+void canonical_signs(float *P, int s, int d, int64_t ldp, cudaStream_t st);
+
+// Copies of strided matrices.
+void copy_rows(const float *src, int64_t lds, float *dst, int64_t ldd, int rows, int cols,
+               cudaStream_t st);
+
+}  // namespace adagio

@@ -1,0 +1,157 @@
+// Randomized PCA (Sec. 2 "PCA"; the randomized variant of Sec. 4.5, after
+// Martinsson et al.): top principal directions of the centred data, computed
+// by block subspace iteration on the covariance C = Xc^T Xc.
+//
+//   C        : split-K FP32 Gram of the centred rows, partials summed in FP64
+//   start    : +-1 block V (b x d, rows are vectors) from the counter RNG
+//   iterate  : W = V C; H = V W^T (FP64); H = U diag(theta) U^T (Jacobi);
+//              V <- U^T V, W <- U^T W (Rayleigh-Ritz); stop when every kept
+//              Ritz residual ||W_i - theta_i V_i|| <= tol * theta_1;
+//              otherwise V <- orth(W) (shifted CholeskyQR2, FP64 Gram and
+//              Cholesky)
+//   blocks   : directions are found in blocks of at most kJacobiMax - p;
+//              later blocks iterate in the orthogonal complement of the
+//              earlier ones (deflation), so the rows of P stay sorted by
+//              eigenvalue and any prefix P[:s] is the top-s subspace.
+#include "internal.cuh"
+#include "linalg.cuh"
+#include "jl.cuh"
+#include "pca.cuh"
+#include "prep.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+
+namespace adagio {
+
+size_t pca_bytes(int64_t n, int d, int s_cap, int oversample) {
+    const int b = std::min(kJacobiMax, d);
+    size_t bytes = prep_bytes(n, d, true, false);
+    bytes += align_up((size_t)d * d * sizeof(float), 256);                          // C
+    bytes += align_up((size_t)splitk_chunks(n) * d * d * sizeof(float), 256);       // partials
+    bytes += 3 * align_up((size_t)b * d * sizeof(float), 256);                      // V, W, T
+    bytes += align_up((size_t)std::max(s_cap, 1) * d * sizeof(float), 256);         // P
+    bytes += align_up((size_t)std::max(s_cap, 1) * b * sizeof(float), 256);         // proj coeffs
+    bytes += 2 * align_up((size_t)b * b * sizeof(double), 256);                     // G, H
+    bytes += align_up((size_t)b * b * sizeof(float), 256);                          // U
+    bytes += align_up((size_t)(b + std::max(s_cap, 1)) * sizeof(double), 256);     // theta
+    bytes += align_up((size_t)b * sizeof(float), 256);                              // residuals
+    (void)oversample;
+    return bytes + 8192;
+}
+
+void PCA::init(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int64_t ldx, int s_cap_,
+               uint64_t seed_, int max_iter_, double tol_, int oversample_, cudaStream_t st) {
+    ctx = ctx_;
+    n = n_;
+    d = d_;
+    s_cap = std::max(0, std::min(s_cap_, d_));
+    seed = seed_;
+    max_iter = std::max(1, max_iter_);
+    tol = tol_ > 0 ? tol_ : 1e-6;
+    p = std::max(1, std::min(oversample_, kJacobiMax / 2));
+    s_done = 0;
+    iterations = 0;
+    theta1 = 0.0;
+    flags = ws_array<unsigned>(ctx, 1);
+    ADAGIO_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
+    // centred FP32 copy (K0) and the covariance C = Xc^T Xc
+    PrepMat pm;
+    prep_matrix(ctx, X, n, d, ldx, ADAGIO_PREC_FP32, true, false, pm, flags, st);
+    C = ws_array<float>(ctx, (size_t)d * d);
+    float *partials = ws_array<float>(ctx, (size_t)splitk_chunks(n) * d * d);
+    gemm_tn_splitk(d, d, n, pm.c32, pm.Kp32, pm.c32, pm.Kp32, C, d, partials, st);
+    const int bmax = std::min(kJacobiMax, d);
+    V = ws_array<float>(ctx, (size_t)bmax * d);
+    W = ws_array<float>(ctx, (size_t)bmax * d);
+    T = ws_array<float>(ctx, (size_t)bmax * d);
+    P = ws_array<float>(ctx, (size_t)std::max(s_cap, 1) * d);
+    coef = ws_array<float>(ctx, (size_t)std::max(s_cap, 1) * bmax);
+    G = ws_array<double>(ctx, (size_t)bmax * bmax);
+    H = ws_array<double>(ctx, (size_t)bmax * bmax);
+    U = ws_array<float>(ctx, (size_t)bmax * bmax);
+    theta_blk = ws_array<double>(ctx, bmax);
+    theta = ws_array<double>(ctx, std::max(s_cap, 1));
+    res = ws_array<float>(ctx, bmax);
+    unsigned hflag = 0;
+    ADAGIO_CUDA(cudaMemcpyAsync(&hflag, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    ADAGIO_CUDA(cudaStreamSynchronize(st));
+    if (hflag & 1u) fail(ADAGIO_E_NONFINITE, "input holds NaN or Inf");
+}
+
+// rows of M (r x d) <- M - (M P^T) P over the s_done finished directions
+void PCA::deflate(float *M, int r, cudaStream_t st) {
+    if (s_done == 0 || r == 0) return;
+    gemm<float, float, float, float>(r, s_done, d, 1.0f, MatView<float>{M, d, 1},
+                                     MatView<float>{P, 1, d}, 0.0f, coef, s_done, st);
+    gemm<float, float, float, float>(r, d, s_done, -1.0f, MatView<float>{coef, s_done, 1},
+                                     MatView<float>{P, d, 1}, 1.0f, M, d, st);
+}
+
+void PCA::orth(float *M, int b, cudaStream_t st) {
+    for (int pass = 0; pass < 2; ++pass) {
+        gemm<float, float, double, double>(b, b, d, 1.0, MatView<float>{M, d, 1},
+                                           MatView<float>{M, 1, d}, 0.0, G, b, st);
+        cholesky_upper(G, b, pass == 0 ? 1e-12 : 1e-15, st);
+        trsm_rows(G, b, M, d, d, st);
+    }
+}
+
+void PCA::extend(int s_needed, cudaStream_t st) {
+    s_needed = std::min(s_needed, s_cap);
+    while (s_done < s_needed) {
+        const int remaining = d - s_done;
+        const int s_blk = std::min({s_cap - s_done, kJacobiMax - p, remaining});
+        const int b = std::min(s_blk + p, remaining);
+        rademacher_block(seed + (uint64_t)s_done * 0x9E3779B9ull, b, d, V, d, st);
+        deflate(V, b, st);
+        orth(V, b, st);
+        float *hres = nullptr;
+        double *hth = nullptr;
+        for (int it = 0; it < max_iter; ++it) {
+            ++iterations;
+            // W = V C (C symmetric)
+            gemm<float, float, float, float>(b, d, d, 1.0f, MatView<float>{V, d, 1},
+                                             MatView<float>{C, d, 1}, 0.0f, W, d, st);
+            deflate(W, b, st);
+            // Rayleigh-Ritz: H = V W^T, H = U diag(theta) U^T
+            gemm<float, float, double, double>(b, b, d, 1.0, MatView<float>{V, d, 1},
+                                               MatView<float>{W, 1, d}, 0.0, H, b, st);
+            jacobi_eig(H, b, theta_blk, U, 30, st);
+            // V <- U^T V, W <- U^T W
+            gemm<float, float, float, float>(b, d, b, 1.0f, MatView<float>{U, 1, b},
+                                             MatView<float>{V, d, 1}, 0.0f, T, d, st);
+            std::swap(V, T);
+            gemm<float, float, float, float>(b, d, b, 1.0f, MatView<float>{U, 1, b},
+                                             MatView<float>{W, d, 1}, 0.0f, T, d, st);
+            std::swap(W, T);
+            ritz_residuals(W, V, d, d, theta_blk, s_blk, res, st);
+            char *hs = reinterpret_cast<char *>(host_stage(ctx, (size_t)b * 8 + (size_t)b * 4 + 64));
+            hth = reinterpret_cast<double *>(hs);
+            hres = reinterpret_cast<float *>(hs + (size_t)b * 8);
+            ADAGIO_CUDA(cudaMemcpyAsync(hth, theta_blk, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
+            ADAGIO_CUDA(cudaMemcpyAsync(hres, res, sizeof(float) * s_blk, cudaMemcpyDeviceToHost, st));
+            ADAGIO_CUDA(cudaStreamSynchronize(st));
+            if (s_done == 0) theta1 = std::max(hth[0], 0.0);
+            float worst = 0.0f;
+            for (int i = 0; i < s_blk; ++i) worst = std::max(worst, hres[i]);
+            if (!(worst > tol * theta1) || b == remaining || it == max_iter - 1) break;
+            // next iterate: V <- orth(W)
+            std::swap(V, W);
+            orth(V, b, st);
+        }
+        // accept the first s_blk Ritz vectors; re-orthonormalise against the
+        // earlier blocks and among themselves
+        float *dst = P + (size_t)s_done * d;
+        copy_rows(V, d, dst, d, s_blk, d, st);
+        deflate(dst, s_blk, st);
+        orth(dst, s_blk, st);
+        canonical_signs(dst, s_blk, d, d, st);
+        ADAGIO_CUDA(cudaMemcpyAsync(theta + s_done, theta_blk, sizeof(double) * s_blk,
+                                    cudaMemcpyDeviceToDevice, st));
+        s_done += s_blk;
+    }
+}
+
+}  // namespace adagio

@@ -1,0 +1,35 @@
+#pragma once
+
+#include "internal.cuh"
+
+namespace adagio {
+
+// Incremental randomized PCA of one data set (see pca.cu).  All buffers come
+// from the context workspace; reserve pca_bytes() first.
+struct PCA {
+    adagio_ctx *ctx = nullptr;
+    int64_t n = 0;
+    int d = 0, s_cap = 0, p = 32, max_iter = 100;
+    uint64_t seed = 0;
+    double tol = 1e-6, theta1 = 0.0;
+    int s_done = 0, iterations = 0;
+    float *C = nullptr;        // d x d covariance
+    float *P = nullptr;        // s_cap x d principal rows (first s_done valid)
+    double *theta = nullptr;   // eigenvalue estimates of those rows
+    float *V = nullptr, *W = nullptr, *T = nullptr, *U = nullptr, *coef = nullptr, *res = nullptr;
+    double *G = nullptr, *H = nullptr, *theta_blk = nullptr;
+    unsigned *flags = nullptr;
+
+    void init(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx, int s_cap,
+              uint64_t seed, int max_iter, double tol, int oversample, cudaStream_t st);
+    // make sure the first s_needed rows of P are computed (synchronises)
+    void extend(int s_needed, cudaStream_t st);
+
+   private:
+    void deflate(float *M, int r, cudaStream_t st);
+    void orth(float *M, int b, cudaStream_t st);
+};
+
+size_t pca_bytes(int64_t n, int d, int s_cap, int oversample);
+
+}  // namespace adagio
