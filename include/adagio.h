@@ -242,6 +242,21 @@ typedef struct {
 int adagio_set_timing(adagio_ctx *ctx, int enable);
 int adagio_last_cert_stats(const adagio_ctx *ctx, adagio_cert_stats *out);
 
+/*
+ * Error-model check of the certificate's fast path.  Runs the certificate of
+ * (X, Y) like adagio_distortion and, for the first `tiles` 128 x 128 tile
+ * pairs the tile kernel visits, writes per pair (local row a, local column b)
+ * four floats at out[((t * 128 + a) * 128 + b) * 4]: the fast squared
+ * distances dx2 = ||xc_a||^2 + ||xc_b||^2 - 2 xc_a.xc_b and dy2 (likewise)
+ * and their error bounds ex, ey; tile_ij[2t], tile_ij[2t+1] receive the tile
+ * coordinates (I, J), so the pair is (128 I + a, 128 J + b).  Entries of
+ * pairs outside i < j < n are written but meaningless.  Arrays are host or
+ * device; `out` holds tiles * 65536 floats.  Synchronises `stream`.
+ */
+int adagio_debug_tile_bounds(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
+                             const float *Y, int m, int64_t ldy, int precision, int64_t tiles,
+                             float *out, int *tile_ij, void *stream);
+
 /* Number of kernels this library has launched in this process (all contexts,
  * all devices); a difference of two readings counts the launches between. */
 uint64_t adagio_launch_count(void);

@@ -122,6 +122,8 @@ def _load() -> ctypes.CDLL:
         "adagio_set_timing": (i32, [vp, i32]),
         "adagio_last_cert_stats": (i32, [vp, ctypes.POINTER(CertStatsStruct)]),
         "adagio_launch_count": (ctypes.c_uint64, []),
+        "adagio_debug_tile_bounds": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, i32, i64, vp, vp,
+                                           vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -138,7 +140,7 @@ def exported_symbols() -> list[str]:
                         "adagio_workspace_bytes", "adagio_default_fit_opts", "adagio_distortion",
                         "adagio_embed", "adagio_jl_matrix", "adagio_pca", "adagio_assemble",
                         "adagio_fit", "adagio_set_timing", "adagio_last_cert_stats",
-                        "adagio_launch_count") if hasattr(LIB, n)]
+                        "adagio_launch_count", "adagio_debug_tile_bounds") if hasattr(LIB, n)]
 
 
 def launch_count() -> int:
@@ -254,6 +256,16 @@ class Context:
                                           eps, hist_lo, hist_hi, precision, ctypes.byref(c),
                                           _stream(x, y)))
         return Certificate.from_struct(c)
+
+    def debug_tile_bounds(self, X, Y, tiles: int, precision: int = PREC_FP16X3):
+        """(dump[tiles,128,128,4] = (dx2, dy2, ex, ey), tile_ij[tiles,2]) of the fast path."""
+        x, y = _Arr(X), _Arr(Y)
+        out = np.empty((tiles, 128, 128, 4), dtype=np.float32)
+        ij = np.empty((tiles, 2), dtype=np.int32)
+        self._check(LIB.adagio_debug_tile_bounds(self.h, x.ptr, x.rows, x.cols, x.ld, y.ptr, y.cols,
+                                                 y.ld, precision, tiles, out.ctypes.data,
+                                                 ij.ctypes.data, _stream(x, y)))
+        return out, ij
 
     # -------------------------------------------------------------------- embed
     def embed(self, A, X, Y=None):

@@ -84,6 +84,45 @@ int adagio_distortion(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t
     API_END(ctx)
 }
 
+int adagio_debug_tile_bounds(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
+                             const float *Y, int m, int64_t ldy, int precision, int64_t tiles,
+                             float *out, int *tile_ij, void *stream) {
+    API_BEGIN(ctx)
+    ADAGIO_REQUIRE(X && Y && out && tile_ij, "null pointer argument");
+    ADAGIO_REQUIRE(n >= 2 && n < (1ll << 31) - 256 && d >= 1 && m >= 1 && ldx >= d && ldy >= m,
+                   "bad sizes");
+    check_precision(precision);
+    const int T = (int)((n + 127) / 128);
+    const long long ntp = (long long)T * (T + 1) / 2;
+    ADAGIO_REQUIRE(tiles >= 1 && tiles <= ntp, "tiles must lie in [1, %lld]", ntp);
+    cudaStream_t st = (cudaStream_t)stream;
+    const bool out_dev = is_device_ptr(out, ctx->device);
+    const size_t dump_bytes = (size_t)tiles * 128 * 128 * 4 * sizeof(float);
+    size_t need = staging_bytes(ctx, X, n, d) + staging_bytes(ctx, Y, n, m) +
+                  certify_bytes(ctx, n, d, m, precision) + (out_dev ? 0 : align_up(dump_bytes, 256));
+    ws_reserve(ctx, need);
+    int64_t lx, ly;
+    const float *dX = stage_input(ctx, X, n, d, ldx, &lx, st);
+    const float *dY = stage_input(ctx, Y, n, m, ldy, &ly, st);
+    float *dump = out_dev ? out : reinterpret_cast<float *>(ws_alloc(ctx, dump_bytes));
+    CertOptions co;
+    co.eps = 0.5;
+    co.lo = 0.0;
+    co.hi = 1.0;
+    co.precision = precision;
+    co.dump = dump;
+    co.dump_tiles = tiles;
+    adagio_cert c;
+    const int rc = certify(ctx, dX, lx, dY, ly, n, d, m, co, &c, st);
+    if (!out_dev) {
+        ADAGIO_CUDA(cudaMemcpyAsync(out, dump, dump_bytes, cudaMemcpyDeviceToHost, st));
+        ADAGIO_CUDA(cudaStreamSynchronize(st));
+    }
+    for (long long t = 0; t < tiles; ++t) tile_coords(precision, T, t, &tile_ij[2 * t], &tile_ij[2 * t + 1]);
+    return rc;
+    API_END(ctx)
+}
+
 int adagio_embed(adagio_ctx *ctx, const float *A, int m, int d, int64_t lda, const float *X,
                  int64_t n, int64_t ldx, float *Y, int64_t ldy, void *stream) {
     API_BEGIN(ctx)

@@ -9,12 +9,34 @@
 
 namespace adagio {
 
+// Initial capacity of the recompute queue: 1/1024 of the pairs (at least
+// 2^20 entries); it grows to the observed need when a run overflows it.
 static unsigned long long queue_capacity(unsigned long long pairs) {
-    unsigned long long q = pairs / 64;
-    if (q < (1ull << 16)) q = 1ull << 16;
-    if (q > (1ull << 28)) q = 1ull << 28;
+    unsigned long long q = pairs / 1024;
+    if (q < (1ull << 20)) q = 1ull << 20;
     if (q > pairs) q = pairs;
     return q;
+}
+
+static void ensure_queue(adagio_ctx *ctx, unsigned long long cap) {
+    if (ctx->qbuf_cap >= cap) return;
+    if (ctx->qbuf_fixed)
+        fail(ADAGIO_E_QUEUE_OVERFLOW, "recompute queue needs %llu entries, fixed capacity is %llu", cap,
+             ctx->qbuf_cap);
+    if (ctx->qbuf) {
+        ADAGIO_CUDA(cudaDeviceSynchronize());  // a previous certificate may still read it
+        ADAGIO_CUDA(cudaFree(ctx->qbuf));
+        ctx->qbuf = nullptr;
+        ctx->qbuf_cap = 0;
+    }
+    cudaError_t e = cudaMalloc(&ctx->qbuf, cap * sizeof(int2));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->qbuf = nullptr;
+        fail(ADAGIO_E_WORKSPACE, "cudaMalloc of a %llu-entry recompute queue failed: %s", cap,
+             cudaGetErrorString(e));
+    }
+    ctx->qbuf_cap = cap;
 }
 
 static int tile_grid(adagio_ctx *ctx, int precision) {
@@ -29,7 +51,7 @@ size_t certify_bytes(adagio_ctx *ctx, int64_t n, int d, int m, int precision) {
     const unsigned long long pairs = (unsigned long long)n * (n - 1) / 2;
     size_t b = prep_bytes(n, d, !tc, tc) + prep_bytes(n, m, !tc, tc);
     b += align_up(sizeof(CertPartial) * (tile_grid(ctx, precision) + recompute_grid(ctx)), 256);
-    b += align_up(sizeof(int2) * queue_capacity(pairs) * 8, 256);  // room for one retry
+    (void)pairs;
     b += 4096 + sizeof(CertDevResult);
     return b;
 }
@@ -39,7 +61,7 @@ int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_
             bool *stopped) {
     const bool tc = opt.precision != ADAGIO_PREC_FP32;
     const unsigned long long pairs = (unsigned long long)n * (unsigned long long)(n - 1) / 2;
-    unsigned long long qcap = queue_capacity(pairs);
+    if (!ctx->qbuf_fixed) ensure_queue(ctx, queue_capacity(pairs));
     const size_t mark = ctx->ws.off;
 
     for (int attempt = 0; attempt < 2; ++attempt) {
@@ -63,6 +85,7 @@ int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_
         prep_matrix(ctx, Y, n, m, ldy, opt.precision, !tc, tc, py, flags, st);
 
         CertLaunch L;
+        L.ctx = ctx;
         L.x = &px;
         L.y = &py;
         L.cc.lo = (float)opt.lo;
@@ -76,11 +99,14 @@ int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_
         L.partials = ws_array<CertPartial>(ctx, L.grid);
         const int rgrid = recompute_grid(ctx);
         CertPartial *rparts = ws_array<CertPartial>(ctx, rgrid);
-        L.queue = ws_array<int2>(ctx, qcap);
+        const unsigned long long qcap = ctx->qbuf_cap;
+        L.queue = ctx->qbuf;
         L.qcount = qcount;
         L.qcap = qcap;
         L.stop_flag = opt.stop_early ? stop : nullptr;
         L.status = status;
+        L.dump = opt.dump;
+        L.dump_tiles = opt.dump_tiles;
         CertDevResult *dres = ws_array<CertDevResult>(ctx, 1);
 
         if (ctx->collect_timing) ADAGIO_CUDA(cudaEventRecord(ev[1], st));
@@ -121,9 +147,8 @@ int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_
         if (h->status != 0)
             fail(ADAGIO_E_TIMEOUT, "certificate kernel gave up a bounded wait (status %d)", h->status);
         if (*hq > qcap) {
-            if (attempt == 0 && qcap < pairs) {
-                // certify_bytes() reserved room for an 8x larger queue
-                qcap = std::min<unsigned long long>(pairs, qcap * 8);
+            if (attempt == 0 && !ctx->qbuf_fixed) {
+                ensure_queue(ctx, std::min<unsigned long long>(pairs, *hq + *hq / 8 + 1024));
                 continue;
             }
             fail(ADAGIO_E_QUEUE_OVERFLOW, "recompute queue overflow (%llu pairs > capacity %llu)",
@@ -163,6 +188,19 @@ int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_
         return ADAGIO_OK;
     }
     return ADAGIO_E_QUEUE_OVERFLOW;
+}
+
+void tile_coords(int precision, int T, long long t, int *I, int *J) {
+    if (precision == ADAGIO_PREC_FP32) {
+        // row-major upper triangle (the SIMT kernel's order)
+        int i = 0;
+        long long off = 0;
+        while (i < T && off + (T - i) <= t) off += T - i++;
+        *I = i;
+        *J = i + (int)(t - off);
+    } else {
+        tc_tile_coords(T, t, I, J);
+    }
 }
 
 }  // namespace adagio

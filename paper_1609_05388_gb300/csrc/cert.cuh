@@ -9,6 +9,7 @@
 namespace adagio {
 
 struct CertLaunch {
+    adagio_ctx *ctx = nullptr;
     const PrepMat *x = nullptr;
     const PrepMat *y = nullptr;
     CertConst cc{};
@@ -19,6 +20,8 @@ struct CertLaunch {
     unsigned long long qcap = 0;
     int *stop_flag = nullptr;         // early exit (search probes) or null
     int *status = nullptr;            // device status word (timeouts)
+    void *dump = nullptr;             // optional per-pair (dx2, dy2, ex, ey) dump
+    long long dump_tiles = 0;         // tile pairs to dump (schedule order)
 };
 
 // Device-side result of the finaliser (host copies it back).
@@ -38,6 +41,7 @@ int cert_simt_threads();
 // tcgen05 tile kernel; returns false when the shape is not supported
 bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st);
 int cert_tc_grid(adagio_ctx *ctx);
+void tc_tile_coords(int T, long long t, int *I, int *J);
 
 // Exact recompute of the queued pairs from the original (uncentred) inputs.
 void launch_recompute(const float *X, int64_t ldx, int d, const float *Y, int64_t ldy, int m,
@@ -58,7 +62,13 @@ struct CertOptions {
     double eps = 0.1, lo = 0.0, hi = 0.2;
     int precision = ADAGIO_PREC_FP16X3;
     bool stop_early = false;
+    void *dump = nullptr;       // per-pair fast values of the first dump_tiles tile pairs
+    long long dump_tiles = 0;
 };
+
+// Tile coordinates of the t-th tile pair the tile kernel of `precision`
+// visits (host side, for diagnostics).
+void tile_coords(int precision, int T, long long t, int *I, int *J);
 int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_t ldy, int64_t n,
             int d, int m, const CertOptions &opt, adagio_cert *out, cudaStream_t st,
             bool *stopped = nullptr);

@@ -216,6 +216,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(bar_tempty + 8 * b, 128);
         }
         mbar_init(bar_done, 1);
+        for (int q = 0; q < kStages + 3; ++q) s_cmd[q] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -238,6 +239,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         // ------------------------------------------------------ TMA producer
+        // lane 0 waits and issues; the outcome of every wait is broadcast so
+        // the warp never diverges on a timeout
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
@@ -247,20 +250,33 @@ __global__ void __launch_bounds__(kThreads, 1)
         long long t = blockIdx.x;
         while (ok) {
             bool stop = t >= p.ntp;
-            if (!stop && p.stop_flag) stop = *(volatile int *)p.stop_flag != 0;
+            if (!stop && p.stop_flag) {
+                int f = 0;
+                if (lane == 0) f = *(volatile int *)p.stop_flag;
+                stop = __shfl_sync(0xffffffffu, f, 0) != 0;
+            }
             if (stop) {
-                ok = mbar_wait(bar_empty + 8 * stage, phase ^ 1, p.status, 1);
-                if (ok && lane == 0) {
-                    s_cmd[stage] = -1;
-                    mbar_arrive(bar_full + 8 * stage);
+                int w = 0;
+                if (lane == 0) {
+                    w = mbar_wait(bar_empty + 8 * stage, phase ^ 1, p.status, 1);
+                    if (w) {
+                        s_cmd[stage] = -1;
+                        mbar_arrive(bar_full + 8 * stage);
+                    }
                 }
+                // the empty wait proved the stage's last copy was consumed, and
+                // the stop arrive moved its full barrier one phase on: nothing
+                // of this stage is left to drain
+                issued[stage] = false;
                 __syncwarp();
                 break;
             }
             const uint32_t packed = p.sched[t];
             const int I = (int)(packed >> 16), J = (int)(packed & 0xFFFF);
-            for (int ks = 0; ks < ksteps && ok; ++ks) {
-                ok = mbar_wait(bar_empty + 8 * stage, phase ^ 1, p.status, 1);
+            for (int ks = 0; ks < ksteps; ++ks) {
+                int w = 0;
+                if (lane == 0) w = mbar_wait(bar_empty + 8 * stage, phase ^ 1, p.status, 1);
+                ok = __shfl_sync(0xffffffffu, w, 0) != 0;
                 if (!ok) break;
                 if (lane == 0) {
                     if (ks == 0) s_cmd[stage] = (int)t;
@@ -287,36 +303,43 @@ __global__ void __launch_bounds__(kThreads, 1)
             t += gridDim.x;
         }
         // drain: every issued copy must have landed before the CTA can exit
-        for (int s = 0; s < kStages; ++s)
-            if (issued[s]) mbar_wait(bar_full + 8 * s, issued_parity[s], p.status, 1);
+        if (lane == 0)
+            for (int s = 0; s < kStages; ++s)
+                if (issued[s]) mbar_wait(bar_full + 8 * s, issued_parity[s], p.status, 1);
+        __syncwarp();
     } else if (warp == 1) {
         // ------------------------------------------------------- MMA issuer
         int stage = 0;
         uint32_t phase = 0;
         int buf = 0;
         uint32_t bphase = 0;
-        bool ok = true;
         bool any = false;
-        while (ok) {
-            ok = mbar_wait(bar_full + 8 * stage, phase, p.status, 2);
-            if (!ok) break;
-            const int t = s_cmd[stage];
+        while (true) {
+            int w = 0, t = -1;
+            if (lane == 0) {
+                w = mbar_wait(bar_full + 8 * stage, phase, p.status, 2);
+                if (w) t = s_cmd[stage];
+            }
+            if (!__shfl_sync(0xffffffffu, w, 0)) break;
+            t = __shfl_sync(0xffffffffu, t, 0);
             if (t < 0) {
-                // forward the stop to the epilogue once its buffer is free
-                ok = mbar_wait(bar_tempty + 8 * buf, bphase ^ 1, p.status, 2);
-                if (ok && lane == 0) {
+                // forward the stop to the epilogue once its buffer is free; a
+                // plain arrive releases the store of the stop word
+                if (lane == 0 && mbar_wait(bar_tempty + 8 * buf, bphase ^ 1, p.status, 2)) {
                     s_cmd[kStages + buf] = -1;
                     mbar_arrive(bar_tfull + 8 * buf);
                 }
                 __syncwarp();
                 break;
             }
-            ok = mbar_wait(bar_tempty + 8 * buf, bphase ^ 1, p.status, 2);
-            if (!ok) break;
+            if (lane == 0) w = mbar_wait(bar_tempty + 8 * buf, bphase ^ 1, p.status, 2);
+            if (!__shfl_sync(0xffffffffu, w, 0)) break;
             tc_fence_after();
+            bool ok = true;
             for (int ks = 0; ks < ksteps; ++ks) {
                 if (ks > 0) {
-                    ok = mbar_wait(bar_full + 8 * stage, phase, p.status, 2);
+                    if (lane == 0) w = mbar_wait(bar_full + 8 * stage, phase, p.status, 2);
+                    ok = __shfl_sync(0xffffffffu, w, 0) != 0;
                     if (!ok) break;
                     tc_fence_after();
                 }
@@ -345,25 +368,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             if (!ok) break;
-            if (lane == 0) {
-                s_cmd[kStages + buf] = t;
-                tc_commit(bar_tfull + 8 * buf);
-            }
+            if (lane == 0) tc_commit(bar_tfull + 8 * buf);
             __syncwarp();
             buf ^= 1;
             if (buf == 0) bphase ^= 1;
         }
         // all issued MMAs must be complete before TMEM is released
-        if (lane == 0 && any) tc_commit(bar_done);
+        any = __shfl_sync(0xffffffffu, any ? 1 : 0, 0) != 0;
+        if (lane == 0 && any) {
+            tc_commit(bar_done);
+            mbar_wait(bar_done, 0, p.status, 2);
+        }
         __syncwarp();
-        if (any) mbar_wait(bar_done, 0, p.status, 2);
     } else {
         // --------------------------------------------------------- epilogue
         const int et = threadIdx.x - 64;   // 0..127
         const int quarter = warp & 3;      // TMEM lanes this warp may access
         const int r = quarter * 32 + lane; // row of the tile owned by this thread
-        const float c_inf = 0.0f;
-        (void)c_inf;
         int buf = 0;
         uint32_t bphase = 0;
         unsigned long long npairs = 0, nviol = 0, nover = 0, nqueued = 0;
@@ -373,13 +394,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float sx = *p.scale_x, sy = *p.scale_y;
         const float inv_sx2 = 1.0f / (sx * sx), inv_sy2 = 1.0f / (sy * sy);
         int tiles_since_flush = 0;
-        bool ok = true;
+        int *s_state = s_cmd + kStages + 2;   // epilogue-wide decision word
+        long long t = blockIdx.x;             // same static sequence the producer walks
         while (true) {
-            ok = mbar_wait(bar_tfull + 8 * buf, bphase, p.status, 3);
-            if (!ok) break;
+            // one thread waits; the decision reaches all 128 through the barrier
+            if (et == 0) {
+                const bool w = mbar_wait(bar_tfull + 8 * buf, bphase, p.status, 3);
+                *s_state = !w ? 2 : (s_cmd[kStages + buf] < 0 ? 1 : 0);
+            }
+            epi_bar();
+            if (*s_state != 0) break;
             tc_fence_after();
-            const int t = s_cmd[kStages + buf];
-            if (t < 0) break;
             const uint32_t packed = p.sched[t];
             const int I = (int)(packed >> 16), J = (int)(packed & 0xFFFF);
             s_jx[et] = p.rsx[J * kTile + et];
@@ -432,6 +457,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             tc_fence_before();
             mbar_arrive(bar_tempty + 8 * buf);
+            t += gridDim.x;
             sum += (double)tsum;
             bsum += (double)tbsum;
             if (p.stop_flag && stop) atomicExch(p.stop_flag, 1);
@@ -597,6 +623,13 @@ static const uint32_t *schedule_for(adagio_ctx *ctx, int T) {
 }
 
 int cert_tc_grid(adagio_ctx *ctx) { return ctx->num_sms; }
+
+void tc_tile_coords(int T, long long t, int *I, int *J) {
+    const std::vector<uint32_t> s = band_schedule(T);
+    const uint32_t v = s.at((size_t)t);
+    *I = (int)(v >> 16);
+    *J = (int)(v & 0xFFFF);
+}
 
 bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     const PrepMat &x = *L.x, &y = *L.y;

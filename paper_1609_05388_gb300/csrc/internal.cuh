@@ -70,7 +70,11 @@ struct adagio_ctx {
     // pinned host staging for small device->host results
     void *host_stage = nullptr;
     size_t host_stage_bytes = 0;
-    // device-side scalars reused by kernels (flags, counters)
+    // recompute queue of the certificate: context-owned, grown on demand
+    // (qbuf_fixed: an external buffer that must not be replaced)
+    int2 *qbuf = nullptr;
+    unsigned long long qbuf_cap = 0;
+    bool qbuf_fixed = false;
     adagio::Predictor *predictor = nullptr;
     // statistics of the most recent certificate (for diagnostics)
     adagio_cert_stats last_stats{-1.0, -1.0, -1.0, 0, 0, 0};

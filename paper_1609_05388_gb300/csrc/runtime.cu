@@ -159,6 +159,7 @@ int adagio_ctx_destroy(adagio_ctx *ctx) {
         cudaDeviceSynchronize();
         free_predictor(ctx);
         if (ctx->ws.base) cudaFree(ctx->ws.base);
+        if (ctx->qbuf && !ctx->qbuf_fixed) cudaFree(ctx->qbuf);
         if (ctx->host_stage) cudaFreeHost(ctx->host_stage);
         if (prev >= 0) cudaSetDevice(prev);
     }

@@ -4,7 +4,7 @@ import numpy as np
 from oracle.certificate import pair_distortion
 
 # Arithmetic of the certificate tiles exercised by the parity tests.
-PRECISIONS = (0,)
+PRECISIONS = (0, 1, 2)   # FP32 SIMT, FP16x3 and BF16x3 tensor cores
 
 
 def assert_cert_parity(g, o, X, Y, max_tol=1e-5, mean_tol=1e-6):
