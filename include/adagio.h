@@ -160,6 +160,28 @@ int adagio_distortion(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t
                       const float *Y, int m, int64_t ldy, double eps, double hist_lo,
                       double hist_hi, int precision, adagio_cert *out, void *stream);
 
+/*
+ * Allocation-free certificate (the paper has no counterpart; this is a
+ * deployment variant of adagio_distortion).  For callers that cannot let a
+ * library allocate device memory during a call -- a service whose device
+ * memory all belongs to its own pool, or a loop that cannot afford the
+ * device-wide synchronisation of cudaMalloc/cudaFree -- it computes the same
+ * certificate as adagio_distortion with precision ADAGIO_PREC_FP32, using
+ * only a fixed 8 MiB scratch array that the library keeps in static device
+ * memory (held by every GPU that loads the library until the process exits).
+ *  Limits: n <= 1024, d <= 512, m <= 256; larger inputs fail with
+ *          ADAGIO_E_INVALID_ARG.  X and Y must be device pointers; out is host.
+ *  The first call on a device looks up the scratch array's device address;
+ *  make that first call before capturing any stream on the device.
+ *  All calls share the scratch array (it keeps the last call's contents and
+ *  each call clears what must start at zero); overlapping calls would race, so
+ *  calls are serialised by a host lock and the stream is synchronised before
+ *  returning.  No cudaMalloc, cudaFree or allocating library call is made.
+ */
+int adagio_distortion_noalloc(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
+                              const float *Y, int m, int64_t ldy, double eps, double hist_lo,
+                              double hist_hi, adagio_cert *out, void *stream);
+
 /* ------------------------------------------------------------------- embed */
 /*
  * Y = X A^T: row i of Y is f(x_i) = A x_i (Algorithm 1's output for every w).

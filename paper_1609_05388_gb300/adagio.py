@@ -124,6 +124,8 @@ def _load() -> ctypes.CDLL:
         "adagio_launch_count": (ctypes.c_uint64, []),
         "adagio_debug_tile_bounds": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, i32, i64, vp, vp,
                                            vp]),
+        "adagio_distortion_noalloc": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, f64, f64, f64,
+                                            ctypes.POINTER(CertStruct), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -140,7 +142,8 @@ def exported_symbols() -> list[str]:
                         "adagio_workspace_bytes", "adagio_default_fit_opts", "adagio_distortion",
                         "adagio_embed", "adagio_jl_matrix", "adagio_pca", "adagio_assemble",
                         "adagio_fit", "adagio_set_timing", "adagio_last_cert_stats",
-                        "adagio_launch_count", "adagio_debug_tile_bounds") if hasattr(LIB, n)]
+                        "adagio_launch_count", "adagio_debug_tile_bounds",
+                        "adagio_distortion_noalloc") if hasattr(LIB, n)]
 
 
 def launch_count() -> int:
@@ -266,6 +269,18 @@ class Context:
                                                  y.ld, precision, tiles, out.ctypes.data,
                                                  ij.ctypes.data, _stream(x, y)))
         return out, ij
+
+    def distortion_noalloc(self, X, Y, eps: float, hist_lo: float = 0.0,
+                           hist_hi: float = 0.0) -> Certificate:
+        """The certificate computed without any device allocation (small inputs, device arrays)."""
+        x, y = _Arr(X), _Arr(Y)
+        if x.rows != y.rows:
+            raise ValueError("X and Y must have the same number of rows")
+        c = CertStruct()
+        self._check(LIB.adagio_distortion_noalloc(self.h, x.ptr, x.rows, x.cols, x.ld, y.ptr,
+                                                  y.cols, y.ld, eps, hist_lo, hist_hi,
+                                                  ctypes.byref(c), _stream(x, y)))
+        return Certificate.from_struct(c)
 
     # -------------------------------------------------------------------- embed
     def embed(self, A, X, Y=None):
