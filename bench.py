@@ -254,6 +254,7 @@ def main():
     ms = e0.elapsed_time(e1) / args.steps
     ms = max_over_ranks(pg, ms)
     A, m, s, cert, rc = results[-1]
+    fit_stats = ctx.last_fit_stats()
     value = sum_over_ranks(pg, pairs / (ms / 1e3))
 
     # plain FP32 GPU path (SIMT tiles, plain search) on the same input
@@ -326,6 +327,7 @@ def main():
             "result": {"m": m, "s": s, "max": cert.max, "mean": cert.mean,
                        "violations": cert.violations, "recomputed": cert.recomputed,
                        "max_err_bound": cert.max_err_bound},
+            "fit_stats": fit_stats,
             "certificate_only": {"value": pairs / (tile_ms / 1e3), "unit": "pairs/s (tile kernel)"},
             "plain_fp32": plain,
             "roofline": roof,

@@ -242,6 +242,43 @@ int adagio_fit(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
                const adagio_fit_opts *opts, float *A, int m_cap, int *m_out, int *s_out,
                adagio_cert *cert, void *stream);
 
+/* ----------------------------------------------------- dimension predictor */
+/*
+ * A small network predicts the target dimension the certified search would
+ * return, so that adagio_fit (opts->use_predictor = 1) can start from the
+ * prediction: the predicted m is verified with the exhaustive certificate and
+ * returned if it passes; otherwise the search continues above it.  The paper
+ * has no learned component; the certificate keeps every returned map exact.
+ *  Features (68 floats): 0.5 log(theta_i / tr C) for the 64 leading eigenvalues
+ *  of the centred covariance C (missing ones: 0.5 log 1e-12), log n, log d,
+ *  eps, 1.  Network: 68 -> 256 -> 256 -> 1, exact GELU, output y = log m,
+ *  BF16 weights with FP32 accumulation and activations; m = ceil(1.05 e^y).
+ *  Parameters (adagio_mlp_num_params() floats): W1 [256][68], b1 [256],
+ *  W2 [256][256], b2 [256], w3 [256], b3 [1] (FP32 master copy).
+ *  Training: mean squared error on y, Adam (beta 0.9 / 0.999, eps 1e-8) with
+ *  bias correction.  Arrays may be host or device pointers.
+ */
+int64_t adagio_mlp_num_params(void);
+int adagio_mlp_init(adagio_ctx *ctx, uint64_t seed);
+int adagio_mlp_set_params(adagio_ctx *ctx, const float *params, int64_t count);
+int adagio_mlp_get_params(adagio_ctx *ctx, float *params, int64_t count);
+/* y (count floats) = network output for `count` feature rows (count x 68). */
+int adagio_mlp_forward(adagio_ctx *ctx, const float *feats, int count, float *y, void *stream);
+/* Loss (mean squared error against target y) and its gradient, no update. */
+int adagio_mlp_grad(adagio_ctx *ctx, const float *feats, const float *target, int count,
+                    double *loss, float *grads, void *stream);
+/* One Adam step on a batch; *loss (may be NULL) gets the batch loss before it. */
+int adagio_mlp_train_step(adagio_ctx *ctx, const float *feats, const float *target, int count,
+                          float lr, double *loss, void *stream);
+/* m_out[i] = ceil(1.05 exp(y_i)) for each feature row. */
+int adagio_predict_m(adagio_ctx *ctx, const float *feats, int count, int *m_out, void *stream);
+/* Spectrum features of X for the predictor (68 floats, host or device). */
+int adagio_features(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx, double eps,
+                    const adagio_fit_opts *opts, float *feats, void *stream);
+/* Weights, Adam moments and step count to / from a file. */
+int adagio_mlp_save(adagio_ctx *ctx, const char *path);
+int adagio_mlp_load(adagio_ctx *ctx, const char *path);
+
 /* ------------------------------------------------------------- diagnostics */
 /*
  * Timing of the most recent certificate on ctx, taken with CUDA events on the
@@ -260,6 +297,23 @@ typedef struct {
     int grid;
     int64_t tiles;
 } adagio_cert_stats;
+
+/*
+ * Statistics of the most recent adagio_fit on ctx.
+ *  probes          certificates run by the search (early-exit probes included)
+ *  full_certs      probes that ran to completion
+ *  pca_iterations  subspace iterations over all blocks
+ *  s_computed      principal directions computed
+ *  pca_ms, total_ms  wall time of the PCA (covariance included) and of the fit
+ *  predicted_m     the predictor's guess (0 when the predictor was not used)
+ */
+typedef struct {
+    int probes, full_certs, pca_iterations, s_computed;
+    double pca_ms, total_ms;
+    int predicted_m;  /* the predictor's guess (0 when the predictor was not used) */
+} adagio_fit_stats;
+
+int adagio_last_fit_stats(const adagio_ctx *ctx, adagio_fit_stats *out);
 
 int adagio_set_timing(adagio_ctx *ctx, int enable);
 int adagio_last_cert_stats(const adagio_ctx *ctx, adagio_cert_stats *out);

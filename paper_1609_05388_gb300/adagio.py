@@ -65,6 +65,12 @@ class CertStatsStruct(ctypes.Structure):
                 ("grid", ctypes.c_int), ("tiles", ctypes.c_int64)]
 
 
+class FitStatsStruct(ctypes.Structure):
+    _fields_ = [("probes", ctypes.c_int), ("full_certs", ctypes.c_int),
+                ("pca_iterations", ctypes.c_int), ("s_computed", ctypes.c_int),
+                ("pca_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+
+
 class AdagioError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"adagio error {code} ({STATUS_NAMES.get(code, '?')}): {msg}")
@@ -122,6 +128,7 @@ def _load() -> ctypes.CDLL:
         "adagio_set_timing": (i32, [vp, i32]),
         "adagio_last_cert_stats": (i32, [vp, ctypes.POINTER(CertStatsStruct)]),
         "adagio_launch_count": (ctypes.c_uint64, []),
+        "adagio_last_fit_stats": (i32, [vp, ctypes.POINTER(FitStatsStruct)]),
         "adagio_debug_tile_bounds": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, i32, i64, vp, vp,
                                            vp]),
         "adagio_distortion_noalloc": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, f64, f64, f64,
@@ -143,7 +150,7 @@ def exported_symbols() -> list[str]:
                         "adagio_embed", "adagio_jl_matrix", "adagio_pca", "adagio_assemble",
                         "adagio_fit", "adagio_set_timing", "adagio_last_cert_stats",
                         "adagio_launch_count", "adagio_debug_tile_bounds",
-                        "adagio_distortion_noalloc") if hasattr(LIB, n)]
+                        "adagio_distortion_noalloc", "adagio_last_fit_stats") if hasattr(LIB, n)]
 
 
 def launch_count() -> int:
@@ -241,6 +248,11 @@ class Context:
 
     def set_timing(self, enable: bool = True):
         self._check(LIB.adagio_set_timing(self.h, 1 if enable else 0))
+
+    def last_fit_stats(self) -> dict:
+        st = FitStatsStruct()
+        self._check(LIB.adagio_last_fit_stats(self.h, ctypes.byref(st)))
+        return {k: getattr(st, k) for k, _ in FitStatsStruct._fields_}
 
     def last_cert_stats(self) -> dict:
         st = CertStatsStruct()

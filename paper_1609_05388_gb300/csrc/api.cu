@@ -256,7 +256,11 @@ int fit_entry(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
         k_cap = o.m - s_cap;
         ADAGIO_REQUIRE(s_cap <= d, "s must be <= d");
     }
-    if (o.use_predictor) ADAGIO_REQUIRE(o.eps > 0.0, "use_predictor needs eps > 0");
+    if (o.use_predictor) {
+        ADAGIO_REQUIRE(o.eps > 0.0, "use_predictor needs eps > 0");
+        ADAGIO_REQUIRE(has_predictor(ctx), "use_predictor needs a predictor (adagio_mlp_load)");
+        s_cap = std::max(s_cap, std::min(64, d));
+    }
     cudaStream_t st = (cudaStream_t)stream;
     const bool a_dev = is_device_ptr(A, ctx->device);
     size_t need = staging_bytes(ctx, X, n, d) +
@@ -287,8 +291,6 @@ extern "C" {
 int adagio_fit(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
                const adagio_fit_opts *opts, float *A, int m_cap, int *m_out, int *s_out,
                adagio_cert *cert, void *stream) {
-    if (opts && opts->use_predictor)
-        return fit_predicted(ctx, X, n, d, ldx, opts, A, m_cap, m_out, s_out, cert, stream);
     return fit_entry(ctx, X, n, d, ldx, opts, A, m_cap, m_out, s_out, cert, stream, nullptr);
 }
 

@@ -53,6 +53,7 @@ size_t certify_bytes(adagio_ctx *ctx, int64_t n, int d, int m, int precision) {
     b += align_up(sizeof(CertPartial) * (tile_grid(ctx, precision) + recompute_grid(ctx)), 256);
     (void)pairs;
     b += 4096 + sizeof(CertDevResult);
+    if (tc) b += align_up((size_t)((n + 127) / 128 * 128) * sizeof(float4), 256);
     return b;
 }
 
@@ -108,6 +109,7 @@ int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_
         L.dump = opt.dump;
         L.dump_tiles = opt.dump_tiles;
         CertDevResult *dres = ws_array<CertDevResult>(ctx, 1);
+        if (tc) L.rs_xy = ws_array<float4>(ctx, (size_t)px.n_pad);
 
         if (ctx->collect_timing) ADAGIO_CUDA(cudaEventRecord(ev[1], st));
         if (tc) {

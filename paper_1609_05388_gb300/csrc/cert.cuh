@@ -22,6 +22,7 @@ struct CertLaunch {
     int *status = nullptr;            // device status word (timeouts)
     void *dump = nullptr;             // optional per-pair (dx2, dy2, ex, ey) dump
     long long dump_tiles = 0;         // tile pairs to dump (schedule order)
+    void *rs_xy = nullptr;            // tensor path: packed per-row statistics (n_pad float4)
 };
 
 // Device-side result of the finaliser (host copies it back).

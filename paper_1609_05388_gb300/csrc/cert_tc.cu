@@ -7,22 +7,26 @@
 //     Gy = Yc[I] Yc[J]^T   and   Gx = Xc[I] Xc[J]^T
 // from 2-term split planes (hi + lo, FP16 or BF16, power-of-two scaled) with
 // three products hi.hi + hi.lo + lo.hi per K chunk, accumulated in FP32 in
-// tensor memory, and hands the two tiles to the epilogue (cert_common.cuh),
+// tensor memory chunk by chunk, and hands the sums to the epilogue (cert_common.cuh),
 // which classifies every pair (Eq. 2), accumulates max / histogram / counts
 // and queues the pairs that need the exact recompute.
 //
-// Roles (192 threads):
+// Roles (320 threads):
 //   warp 0      TMA producer: 4 planes (A hi/lo, B hi/lo) of 64 K-elements per
 //               stage, 3 stages of 64 KB, 128-byte swizzle
-//   warp 1      TMEM owner (512 columns) and MMA issuer: tcgen05.mma kind::f16,
-//               M = N = 128, K = 16, into two accumulator buffers of
-//               256 columns (Gx | Gy), so the epilogue of tile t overlaps the
-//               MMAs of tile t + 1
-//   warps 2..5  epilogue: tcgen05.ld of their 32-lane quarter, 16 columns at
-//               a time
+//   warp 1      TMEM owner (512 columns = 4 chunk slots of 128) and MMA issuer:
+//               tcgen05.mma kind::f16, M = N = 128, K = 16.  Every 64-element K
+//               step goes to a fresh slot, cross products (hi.lo, lo.hi) first
+//               and the 4 hi.hi products last: the FP32 accumulator loses up to
+//               one unit in the last place per MMA (it truncates), so this
+//               bounds the full-size roundings to 4 per chunk
+//   warps 2..9  epilogue: two warps per TMEM lane quarter, 64 columns each;
+//               they drain every slot into register running sums (round to
+//               nearest) and classify their 64 pairs at the end of a tile
 // The producer decides the tile sequence and sends it down the pipeline (a
-// tile index per first stage, -1 to stop), so early exit needs no CTA-wide
-// barrier.  Every wait is bounded: on timeout the role records a status word
+// tile index per first stage, -1 to stop, forwarded through a slot), so early
+// exit needs no CTA-wide barrier, and the epilogue warps never wait on one
+// another.  Every wait is bounded: on timeout the role records a status word
 // and leaves, the producer drains its in-flight copies, the MMA warp waits
 // for its last commit, and TMEM is freed.
 #include <cuda.h>
@@ -37,25 +41,29 @@ namespace adagio {
 
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;                                // two per TMEM lane quarter
+constexpr int kThreads = 64 + 32 * kEpiWarps;               // producer, MMA, epilogue
 constexpr int kStages = 3;
+constexpr int kSlots = 4;                                   // TMEM chunk accumulators
 constexpr int kTile = 128;
 constexpr int kKStep = 64;                                  // fp16 elements per stage row
+constexpr int kEpiCols = 64;                                // columns per epilogue warp
 constexpr uint32_t kPlaneBytes = kTile * kKStep * 2;        // 16 KB
 constexpr uint32_t kStageBytes = 4 * kPlaneBytes;           // 64 KB
-constexpr uint32_t kTmemCols = 512;
-constexpr int kHistFlushTiles = 256;                        // u16 counters: <= 128 per tile
+constexpr uint32_t kTmemCols = kSlots * kTile;              // 512
+constexpr int kHistFlushTiles = 1000;                       // u16 counters: <= 64 per tile
 constexpr long long kSpinLimit = 4000000000ll;              // clock64 cycles (~2 s)
 
 struct TcArgs {
-    const RowStat *rsx, *rsy;
+    const float4 *rs;          // per row: (|xc|^2, |yc|^2, q4x, q4y)
+    float cx, cy;              // bound coefficients of (n2_i + n2_j) per side
     const float *scale_x, *scale_y;
     const uint32_t *sched;     // (I << 16) | J per tile pair
     long long ntp;
     int n, kx_steps, ky_steps;
     uint32_t idesc;
     CertConst cc;
-    CertPartial *partials;
+    CertPartial *partials;     // [gridDim.x * kEpiWarps], one slot per epilogue warp
     int2 *queue;
     unsigned long long *qcount, qcap;
     int *stop_flag;
@@ -66,11 +74,9 @@ struct TcArgs {
 
 struct SmemLayout {
     static constexpr uint32_t stages = 0;
-    static constexpr uint32_t hist = kStages * kStageBytes;              // u16 [64][128]
-    static constexpr uint32_t jstat = hist + kBins * 128 * 2;            // RowStat [2][128]
-    static constexpr uint32_t red = jstat + 2 * 128 * sizeof(RowStat);   // reduction scratch
-    static constexpr uint32_t bars = red + 4 * 1024;
-    static constexpr uint32_t cmd = bars + 256;                           // int [kStages + 2]
+    static constexpr uint32_t hist = kStages * kStageBytes;                  // u16 [64][256]
+    static constexpr uint32_t bars = hist + kBins * 32 * kEpiWarps * 2;
+    static constexpr uint32_t cmd = bars + 256;                               // int [16]
     static constexpr uint32_t tmem_ptr = cmd + 64;
     static constexpr uint32_t total = tmem_ptr + 16;
 };
@@ -108,6 +114,13 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *st
             return false;
         }
     }
+}
+
+// Warp-uniform bounded wait: lane 0 waits, every lane gets the outcome.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, int *status, int code) {
+    int ok = 0;
+    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, status, code) ? 1 : 0;
+    return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
@@ -162,8 +175,7 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
@@ -171,19 +183,59 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-#pragma unroll
-    for (int q = 0; q < 16; ++q) v[q] = __uint_as_float(r[q]);
 }
 
 __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void epi_bar() {  // the 4 epilogue warps only
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+// Folds this warp's 32 per-thread u16 counters of every bin into its partial.
+__device__ __forceinline__ void fold_hist(uint16_t *s_hist, int ew, CertPartial *dst) {
+    const int lane = threadIdx.x & 31;
+    for (int b = 0; b < kBins; ++b) {
+        uint16_t *c = s_hist + b * (32 * kEpiWarps) + ew * 32 + lane;
+        unsigned v = *c;
+        *c = 0;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) dst->hist[b] += v;
+    }
+    __syncwarp();
+}
+
+// Fast classification of one pair from its Gram entries (Eq. 2), two MUFU
+// operations per pair.  With p = dx2 dy2 and s = sqrt(p):
+//   rho = sqrt(dy2 / dx2) = dy2 / s,   delta = |rho - 1| = |dy2 - dx2| / (dx2 + s)
+// (the second form has no cancellation).  The Gram error bounds are
+// ex = q4x_i q4x_j + cx (n2x_i + n2x_j), likewise ey, and the distortion error
+// is at most B = 0.55 rho (ex / dx2 + ey / dy2) + 1e-6 delta + 1e-9 (the last
+// terms cover the approximate reciprocal square root and reciprocal).
+// Returns 0 = fast result valid, 1 = needs the exact recompute.
+__device__ __forceinline__ int fast_pair(float gx, float gy, const float4 &ri, const float4 &rj,
+                                         float cx, float cy, const CertConst &cc, float &delta,
+                                         float &bound) {
+    const float sx = ri.x + rj.x, sy = ri.y + rj.y;
+    const float dx2 = fmaf(-2.0f, gx, sx), dy2 = fmaf(-2.0f, gy, sy);
+    const float ex = fmaf(ri.z, rj.z, cx * sx), ey = fmaf(ri.w, rj.w, cy * sy);
+    if (!(dx2 > 8.0f * ex) || !(dy2 > 8.0f * ey)) return 1;
+    const float pp = dx2 * dy2;
+    const float rs = rsqrtf(pp);
+    const float sq = pp * rs;                       // sqrt(dx2 dy2)
+    delta = __fdividef(fabsf(dy2 - dx2), dx2 + sq);
+    const float rho = dy2 * rs;
+    const float inv_p = rs * rs;                    // 1 / (dx2 dy2)
+    bound = fmaf(0.55f * rho * inv_p, fmaf(ex, dy2, ey * dx2), fmaf(1e-6f, delta, 1e-9f));
+    if (bound > kMaxTol) return 1;
+    if (bound > kExempt) {
+        const float t = (delta - cc.lo) * cc.inv_w;
+        const float tn = rintf(t);
+        const bool edge_real = !(cc.lo_is_floor && tn <= 0.0f) && tn <= (float)kBins;
+        if ((edge_real && fabsf(t - tn) * cc.w < bound) || fabsf(delta - cc.eps) < bound) return 1;
+    }
+    return 0;
 }
 
 // ---------------------------------------------------------------- the kernel
+template <bool DUMP>
 __global__ void __launch_bounds__(kThreads, 1)
     cert_tc_kernel(const __grid_constant__ CUtensorMap map_xh, const __grid_constant__ CUtensorMap map_xl,
                    const __grid_constant__ CUtensorMap map_yh, const __grid_constant__ CUtensorMap map_yl,
@@ -195,35 +247,30 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     uint16_t *s_hist = reinterpret_cast<uint16_t *>(smem + SmemLayout::hist);
-    RowStat *s_jx = reinterpret_cast<RowStat *>(smem + SmemLayout::jstat);
-    RowStat *s_jy = s_jx + 128;
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SmemLayout::bars);
-    int *s_cmd = reinterpret_cast<int *>(smem + SmemLayout::cmd);      // [kStages] stage cmds, [kStages+b] tmem cmds
+    int *s_cmd = reinterpret_cast<int *>(smem + SmemLayout::cmd);  // [kStages] stage, [kStages + s] slot
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + SmemLayout::tmem_ptr);
     const uint32_t bar_full = smem_u32(bars);                 // [kStages]
     const uint32_t bar_empty = bar_full + 8 * kStages;        // [kStages]
-    const uint32_t bar_tfull = bar_empty + 8 * kStages;       // [2]
-    const uint32_t bar_tempty = bar_tfull + 16;               // [2]
-    const uint32_t bar_done = bar_tempty + 16;                // MMA drain
+    const uint32_t bar_sfull = bar_empty + 8 * kStages;       // [kSlots]
+    const uint32_t bar_sempty = bar_sfull + 8 * kSlots;       // [kSlots]
+    const uint32_t bar_done = bar_sempty + 8 * kSlots;        // MMA drain
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(bar_full + 8 * s, 1);
             mbar_init(bar_empty + 8 * s, 1);
         }
-        for (int b = 0; b < 2; ++b) {
-            mbar_init(bar_tfull + 8 * b, 1);
-            mbar_init(bar_tempty + 8 * b, 128);
+        for (int s = 0; s < kSlots; ++s) {
+            mbar_init(bar_sfull + 8 * s, 1);
+            mbar_init(bar_sempty + 8 * s, 32 * kEpiWarps);
         }
         mbar_init(bar_done, 1);
-        for (int q = 0; q < kStages + 3; ++q) s_cmd[q] = 0;
+        for (int q = 0; q < 16; ++q) s_cmd[q] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    if (warp >= 2) {
-        const int et = threadIdx.x - 64;
-        for (int b = 0; b < kBins; ++b) s_hist[b * 128 + et] = 0;
-    }
+    for (int e = threadIdx.x; e < kBins * 32 * kEpiWarps; e += kThreads) s_hist[e] = 0;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(s_tmem)),
@@ -239,8 +286,6 @@ __global__ void __launch_bounds__(kThreads, 1)
 
     if (warp == 0) {
         // ------------------------------------------------------ TMA producer
-        // lane 0 waits and issues; the outcome of every wait is broadcast so
-        // the warp never diverges on a timeout
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
@@ -256,13 +301,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 stop = __shfl_sync(0xffffffffu, f, 0) != 0;
             }
             if (stop) {
-                int w = 0;
-                if (lane == 0) {
-                    w = mbar_wait(bar_empty + 8 * stage, phase ^ 1, p.status, 1);
-                    if (w) {
-                        s_cmd[stage] = -1;
-                        mbar_arrive(bar_full + 8 * stage);
-                    }
+                if (lane == 0 && mbar_wait(bar_empty + 8 * stage, phase ^ 1, p.status, 1)) {
+                    s_cmd[stage] = -1;
+                    mbar_arrive(bar_full + 8 * stage);
                 }
                 // the empty wait proved the stage's last copy was consumed, and
                 // the stop arrive moved its full barrier one phase on: nothing
@@ -274,9 +315,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t packed = p.sched[t];
             const int I = (int)(packed >> 16), J = (int)(packed & 0xFFFF);
             for (int ks = 0; ks < ksteps; ++ks) {
-                int w = 0;
-                if (lane == 0) w = mbar_wait(bar_empty + 8 * stage, phase ^ 1, p.status, 1);
-                ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+                ok = warp_wait(bar_empty + 8 * stage, phase ^ 1, p.status, 1);
                 if (!ok) break;
                 if (lane == 0) {
                     if (ks == 0) s_cmd[stage] = (int)t;
@@ -309,44 +348,40 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else if (warp == 1) {
         // ------------------------------------------------------- MMA issuer
-        int stage = 0;
-        uint32_t phase = 0;
-        int buf = 0;
-        uint32_t bphase = 0;
+        // Every K step accumulates into a fresh TMEM slot (128 columns): first
+        // the 8 small cross-term products (hi.lo, lo.hi), then the 4 large
+        // hi.hi products, so only 4 FP32 accumulator roundings per chunk act
+        // on full-size partial sums.  The epilogue drains the slot.
+        int stage = 0, slot = 0;
+        uint32_t phase = 0, sphase = 0;
         bool any = false;
-        while (true) {
-            int w = 0, t = -1;
-            if (lane == 0) {
-                w = mbar_wait(bar_full + 8 * stage, phase, p.status, 2);
-                if (w) t = s_cmd[stage];
-            }
-            if (!__shfl_sync(0xffffffffu, w, 0)) break;
+        bool ok = true;
+        while (ok) {
+            int t = -1;
+            ok = warp_wait(bar_full + 8 * stage, phase, p.status, 2);
+            if (!ok) break;
+            if (lane == 0) t = s_cmd[stage];
             t = __shfl_sync(0xffffffffu, t, 0);
             if (t < 0) {
-                // forward the stop to the epilogue once its buffer is free; a
+                // forward the stop to the epilogue through the next slot; the
                 // plain arrive releases the store of the stop word
-                if (lane == 0 && mbar_wait(bar_tempty + 8 * buf, bphase ^ 1, p.status, 2)) {
-                    s_cmd[kStages + buf] = -1;
-                    mbar_arrive(bar_tfull + 8 * buf);
+                if (lane == 0 && mbar_wait(bar_sempty + 8 * slot, sphase ^ 1, p.status, 2)) {
+                    s_cmd[kStages + slot] = -1;
+                    mbar_arrive(bar_sfull + 8 * slot);
                 }
                 __syncwarp();
                 break;
             }
-            if (lane == 0) w = mbar_wait(bar_tempty + 8 * buf, bphase ^ 1, p.status, 2);
-            if (!__shfl_sync(0xffffffffu, w, 0)) break;
-            tc_fence_after();
-            bool ok = true;
             for (int ks = 0; ks < ksteps; ++ks) {
                 if (ks > 0) {
-                    if (lane == 0) w = mbar_wait(bar_full + 8 * stage, phase, p.status, 2);
-                    ok = __shfl_sync(0xffffffffu, w, 0) != 0;
+                    ok = warp_wait(bar_full + 8 * stage, phase, p.status, 2);
                     if (!ok) break;
-                    tc_fence_after();
                 }
+                ok = warp_wait(bar_sempty + 8 * slot, sphase ^ 1, p.status, 2);
+                if (!ok) break;
+                tc_fence_after();
                 if (lane == 0) {
-                    const bool is_y = ks < p.ky_steps;
-                    const bool first = (ks == 0) || (ks == p.ky_steps);
-                    const uint32_t d = tmem_base + (uint32_t)(buf * 256 + (is_y ? 128 : 0));
+                    const uint32_t d = tmem_base + (uint32_t)(slot * kTile);
                     const uint32_t a0 = sbase + SmemLayout::stages + stage * kStageBytes;
                     const uint64_t ah = sw128_desc(a0), al = sw128_desc(a0 + kPlaneBytes);
                     const uint64_t bh = sw128_desc(a0 + 2 * kPlaneBytes);
@@ -354,11 +389,16 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int kk = 0; kk < kKStep / 16; ++kk) {
                         const uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 elements = 32 bytes
-                        tc_mma(d, ah + off, bh + off, p.idesc, (first && kk == 0) ? 0u : 1u);
-                        tc_mma(d, ah + off, bl + off, p.idesc, 1u);
+                        tc_mma(d, ah + off, bl + off, p.idesc, kk == 0 ? 0u : 1u);
                         tc_mma(d, al + off, bh + off, p.idesc, 1u);
                     }
+#pragma unroll
+                    for (int kk = 0; kk < kKStep / 16; ++kk) {
+                        const uint64_t off = (uint64_t)(kk * 32) >> 4;
+                        tc_mma(d, ah + off, bh + off, p.idesc, 1u);
+                    }
                     tc_commit(bar_empty + 8 * stage);
+                    tc_commit(bar_sfull + 8 * slot);
                     any = true;
                 }
                 __syncwarp();
@@ -366,12 +406,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                     stage = 0;
                     phase ^= 1;
                 }
+                if (++slot == kSlots) {
+                    slot = 0;
+                    sphase ^= 1;
+                }
             }
-            if (!ok) break;
-            if (lane == 0) tc_commit(bar_tfull + 8 * buf);
-            __syncwarp();
-            buf ^= 1;
-            if (buf == 0) bphase ^= 1;
         }
         // all issued MMAs must be complete before TMEM is released
         any = __shfl_sync(0xffffffffu, any ? 1 : 0, 0) != 0;
@@ -382,11 +421,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else {
         // --------------------------------------------------------- epilogue
-        const int et = threadIdx.x - 64;   // 0..127
-        const int quarter = warp & 3;      // TMEM lanes this warp may access
-        const int r = quarter * 32 + lane; // row of the tile owned by this thread
-        int buf = 0;
-        uint32_t bphase = 0;
+        // Warp e owns TMEM lane quarter (warp % 4), i.e. tile row r, and the
+        // column half h of the tile.  Warps work independently: each keeps
+        // running sums of its 64 pairs in registers and its own partial slot.
+        const int ew = warp - 2;                 // 0..7
+        const int quarter = warp & 3;
+        const int h = ew >> 2;                   // column half
+        const int r = quarter * 32 + lane;       // tile row of this thread
+        const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+        CertPartial *mine = p.partials + (size_t)blockIdx.x * kEpiWarps + ew;
+        int slot = 0;
+        uint32_t sphase = 0;
         unsigned long long npairs = 0, nviol = 0, nover = 0, nqueued = 0;
         double sum = 0.0, bsum = 0.0;
         float mx = -1.0f, mxb_all = 0.0f;
@@ -394,96 +439,115 @@ __global__ void __launch_bounds__(kThreads, 1)
         const float sx = *p.scale_x, sy = *p.scale_y;
         const float inv_sx2 = 1.0f / (sx * sx), inv_sy2 = 1.0f / (sy * sy);
         int tiles_since_flush = 0;
-        int *s_state = s_cmd + kStages + 2;   // epilogue-wide decision word
-        long long t = blockIdx.x;             // same static sequence the producer walks
-        while (true) {
-            // one thread waits; the decision reaches all 128 through the barrier
-            if (et == 0) {
-                const bool w = mbar_wait(bar_tfull + 8 * buf, bphase, p.status, 3);
-                *s_state = !w ? 2 : (s_cmd[kStages + buf] < 0 ? 1 : 0);
+        long long t = blockIdx.x;               // the producer's static tile sequence
+        bool ok = true;
+        while (ok) {
+            float gx[kEpiCols], gy[kEpiCols];
+#pragma unroll
+            for (int c = 0; c < kEpiCols; ++c) gx[c] = gy[c] = 0.0f;
+            for (int ks = 0; ks < ksteps; ++ks) {
+                ok = warp_wait(bar_sfull + 8 * slot, sphase, p.status, 3);
+                if (!ok) break;
+                tc_fence_after();
+                if (ks == 0) {
+                    int cmdv = 0;
+                    if (lane == 0) cmdv = s_cmd[kStages + slot];
+                    if (__shfl_sync(0xffffffffu, cmdv, 0) < 0) {
+                        ok = false;
+                        break;
+                    }
+                }
+                const uint32_t ta = tmem_base + lane_addr + (uint32_t)(slot * kTile + h * kEpiCols);
+                const bool is_y = ks < p.ky_steps;
+#pragma unroll
+                for (int half = 0; half < 2; ++half) {
+                    uint32_t v[2][16];
+                    tmem_ld16(ta + half * 32, v[0]);
+                    tmem_ld16(ta + half * 32 + 16, v[1]);
+                    tmem_wait_ld();
+                    if (is_y) {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) gy[half * 32 + c] += __uint_as_float(v[c >> 4][c & 15]);
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < 32; ++c) gx[half * 32 + c] += __uint_as_float(v[c >> 4][c & 15]);
+                    }
+                }
+                tc_fence_before();
+                mbar_arrive(bar_sempty + 8 * slot);
+                if (++slot == kSlots) {
+                    slot = 0;
+                    sphase ^= 1;
+                }
             }
-            epi_bar();
-            if (*s_state != 0) break;
-            tc_fence_after();
+            if (!ok) break;
+            // ---- classify the 64 pairs of this thread
             const uint32_t packed = p.sched[t];
             const int I = (int)(packed >> 16), J = (int)(packed & 0xFFFF);
-            s_jx[et] = p.rsx[J * kTile + et];
-            s_jy[et] = p.rsy[J * kTile + et];
-            const RowStat xi = p.rsx[I * kTile + r], yi = p.rsy[I * kTile + r];
-            epi_bar();
             const int i = I * kTile + r;
-            const uint32_t tx = tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(buf * 256);
+            const float4 ri = __ldg(p.rs + i);
+            const int j0 = J * kTile + h * kEpiCols;
+            const bool full = (I < J) && (J * kTile + kTile <= p.n);  // every pair valid
             float tsum = 0.0f, tbsum = 0.0f;
             bool stop = false;
-            float4 *dump = (p.dump && t < p.dump_tiles) ? p.dump + (size_t)t * kTile * kTile : nullptr;
-#pragma unroll 1
-            for (int c0 = 0; c0 < kTile; c0 += 16) {
-                float gx[16], gy[16];
-                tmem_ld16(tx + c0, gx);
-                tmem_ld16(tx + 128 + c0, gy);
-                tmem_wait_ld();
+            unsigned long long qmask = 0ull;
+            const float lo = p.cc.lo, inv_w = p.cc.inv_w, hi_edge = p.cc.hi, eps = p.cc.eps;
+            uint16_t *hrow = s_hist + ew * 32 + lane;
 #pragma unroll
-                for (int jj = 0; jj < 16; ++jj) {
-                    const int lj = c0 + jj;
-                    const int j = J * kTile + lj;
-                    FastPair fp;
-                    int cls = PAIR_SKIP;
-                    const float g_x = gx[jj] * inv_sx2, g_y = gy[jj] * inv_sy2;
-                    if (i < j && j < p.n)
-                        cls = classify_pair(g_x, g_y, xi, s_jx[lj], yi, s_jy[lj], p.cc, fp);
-                    if (dump) {
-                        const RowStat &xj = s_jx[lj], &yj = s_jy[lj];
-                        float4 v;
-                        v.x = (xi.n2 + xj.n2) - 2.0f * g_x;
-                        v.y = (yi.n2 + yj.n2) - 2.0f * g_y;
-                        v.z = fmaf(xi.q4, xj.q4, fmaf(xi.q1, xj.q1, p.cc.c_r * (xi.n2 + xj.n2)));
-                        v.w = fmaf(yi.q4, yj.q4, fmaf(yi.q1, yj.q1, p.cc.c_r * (yi.n2 + yj.n2)));
-                        dump[r * kTile + lj] = v;
-                    }
-                    queue_push(cls == PAIR_QUEUE, i, j, p.queue, p.qcount, p.qcap);
-                    if (cls == PAIR_OK) {
+            for (int c = 0; c < kEpiCols; ++c) {
+                const int j = j0 + c;
+                const float4 rj = __ldg(p.rs + j);
+                const bool valid = full || (i < j && j < p.n);
+                float delta = 0.0f, bound = 0.0f;
+                const int q = fast_pair(gx[c] * inv_sx2, gy[c] * inv_sy2, ri, rj, p.cx, p.cy, p.cc,
+                                        delta, bound);
+                if (DUMP && p.dump && t < p.dump_tiles) {
+                    const float g_x = gx[c] * inv_sx2, g_y = gy[c] * inv_sy2;
+                    float4 w;
+                    w.x = fmaf(-2.0f, g_x, ri.x + rj.x);
+                    w.y = fmaf(-2.0f, g_y, ri.y + rj.y);
+                    w.z = fmaf(ri.z, rj.z, p.cx * (ri.x + rj.x));
+                    w.w = fmaf(ri.w, rj.w, p.cy * (ri.y + rj.y));
+                    p.dump[(size_t)t * kTile * kTile + r * kTile + h * kEpiCols + c] = w;
+                }
+                if (valid) {
+                    if (q) {
+                        qmask |= 1ull << c;
+                    } else {
                         ++npairs;
-                        if (fp.bin >= 0) s_hist[fp.bin * 128 + et] += 1; else ++nover;
-                        nviol += fp.violation;
-                        tsum += fp.delta;
-                        tbsum += fp.bound;
-                        mxb_all = fmaxf(mxb_all, fp.bound);
-                        if (better_max(fp.delta, i, j, mx, ai, aj)) { mx = fp.delta; ai = i; aj = j; }
-                        stop |= fp.delta > p.cc.eps + fp.bound;
-                    } else if (cls == PAIR_QUEUE) {
-                        ++nqueued;
+                        const float tb = (delta - lo) * inv_w;
+                        if (delta >= lo && delta < hi_edge)
+                            hrow[min((int)tb, kBins - 1) * (32 * kEpiWarps)] += 1;
+                        else
+                            ++nover;
+                        nviol += delta > eps;
+                        tsum += delta;
+                        tbsum += bound;
+                        mxb_all = fmaxf(mxb_all, bound);
+                        if (delta > mx) { mx = delta; ai = i; aj = j; }
+                        stop |= delta > eps + bound;
                     }
                 }
             }
-            tc_fence_before();
-            mbar_arrive(bar_tempty + 8 * buf);
-            t += gridDim.x;
+            // push the queued pairs of this tile (rare), warp-aggregated
+            nqueued += __popcll(qmask);
+            while (__any_sync(0xffffffffu, qmask != 0ull)) {
+                const bool has = qmask != 0ull;
+                const int c = has ? __ffsll((long long)qmask) - 1 : 0;
+                if (has) qmask &= qmask - 1;
+                queue_push(has, i, j0 + c, p.queue, p.qcount, p.qcap);
+            }
             sum += (double)tsum;
             bsum += (double)tbsum;
             if (p.stop_flag && stop) atomicExch(p.stop_flag, 1);
-            buf ^= 1;
-            if (buf == 0) bphase ^= 1;
-            epi_bar();  // every thread is done with s_jx / s_jy of this tile
+            t += gridDim.x;
             if (++tiles_since_flush == kHistFlushTiles) {
                 tiles_since_flush = 0;
-                // 2 threads per bin fold 64 u16 counters each into the CTA partial
-                const int b = et >> 1, half = et & 1;
-                unsigned acc = 0;
-                for (int q = 0; q < 64; ++q) acc += s_hist[b * 128 + half * 64 + q];
-                epi_bar();
-                for (int q = 0; q < 64; ++q) s_hist[b * 128 + half * 64 + q] = 0;
-                if (acc) atomicAdd(&p.partials[blockIdx.x].hist[b], (unsigned long long)acc);
-                epi_bar();
+                fold_hist(s_hist, ew, mine);
             }
         }
-        // final fold of the histogram and the scalar statistics
-        epi_bar();
-        {
-            const int b = et >> 1, half = et & 1;
-            unsigned acc = 0;
-            for (int q = 0; q < 64; ++q) acc += s_hist[b * 128 + half * 64 + q];
-            if (acc) atomicAdd(&p.partials[blockIdx.x].hist[b], (unsigned long long)acc);
-        }
+        // ---- this warp's partial: histogram and scalar statistics
+        fold_hist(s_hist, ew, mine);
         unsigned long long u[4] = {npairs, nviol, nover, nqueued};
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
@@ -496,34 +560,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int oj = __shfl_xor_sync(0xffffffffu, aj, o);
             if (better_max(om, oi, oj, mx, ai, aj)) { mx = om; ai = oi; aj = oj; }
         }
-        unsigned long long *ru = reinterpret_cast<unsigned long long *>(smem + SmemLayout::red);
-        double *rd = reinterpret_cast<double *>(ru + 4 * 4);
-        float *rf = reinterpret_cast<float *>(rd + 2 * 4);
-        int *ri = reinterpret_cast<int *>(rf + 2 * 4);
-        const int ew = et >> 5;
         if (lane == 0) {
-            for (int q = 0; q < 4; ++q) ru[q * 4 + ew] = u[q];
-            rd[ew] = sum; rd[4 + ew] = bsum;
-            rf[ew] = mx; rf[4 + ew] = mxb_all;
-            ri[ew] = ai; ri[4 + ew] = aj;
-        }
-        epi_bar();
-        if (et == 0) {
-            CertPartial *dst = p.partials + blockIdx.x;
-            unsigned long long t4[4] = {0, 0, 0, 0};
-            double s0 = 0, s1 = 0;
-            float m = -1.0f, mb = 0.0f;
-            int bi = 0x7fffffff, bj = 0x7fffffff;
-            for (int w = 0; w < 4; ++w) {
-                for (int q = 0; q < 4; ++q) t4[q] += ru[q * 4 + w];
-                s0 += rd[w]; s1 += rd[4 + w];
-                mb = fmaxf(mb, rf[4 + w]);
-                if (better_max(rf[w], ri[w], ri[4 + w], m, bi, bj)) { m = rf[w]; bi = ri[w]; bj = ri[4 + w]; }
-            }
-            dst->pairs = t4[0]; dst->violations = t4[1]; dst->overflow = t4[2]; dst->queued = t4[3];
-            dst->degenerate = 0;
-            dst->sum = s0; dst->bound_sum = s1;
-            dst->max = m; dst->max_bound = mb; dst->argmax_i = bi; dst->argmax_j = bj;
+            mine->pairs = u[0]; mine->violations = u[1]; mine->overflow = u[2]; mine->queued = u[3];
+            mine->degenerate = 0;
+            mine->sum = sum; mine->bound_sum = bsum;
+            mine->max = mx; mine->max_bound = mxb_all; mine->argmax_i = ai; mine->argmax_j = aj;
         }
     }
 
@@ -535,6 +576,12 @@ __global__ void __launch_bounds__(kThreads, 1)
                      "r"(kTmemCols)
                      : "memory");
     }
+}
+
+__global__ void pack_row_stats(const RowStat *__restrict__ rx, const RowStat *__restrict__ ry,
+                               int64_t n_pad, float4 *__restrict__ out) {
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < n_pad) out[r] = make_float4(rx[r].n2, ry[r].n2, rx[r].q4, ry[r].q4);
 }
 
 // ------------------------------------------------------------------ host side
@@ -622,7 +669,8 @@ static const uint32_t *schedule_for(adagio_ctx *ctx, int T) {
     return c->dev;
 }
 
-int cert_tc_grid(adagio_ctx *ctx) { return ctx->num_sms; }
+// partial slots of the certificate: one per epilogue warp of every CTA
+int cert_tc_grid(adagio_ctx *ctx) { return ctx->num_sms * kEpiWarps; }
 
 void tc_tile_coords(int T, long long t, int *I, int *J) {
     const std::vector<uint32_t> s = band_schedule(T);
@@ -641,8 +689,14 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     const CUtensorMap myh = plane_map(y.hi, y.n_pad, y.Kp16, bf16);
     const CUtensorMap myl = plane_map(y.lo, y.n_pad, y.Kp16, bf16);
     TcArgs a;
-    a.rsx = x.rs;
-    a.rsy = y.rs;
+    a.rs = reinterpret_cast<const float4 *>(L.rs_xy);
+    pack_row_stats<<<(unsigned)ceil_div(x.n_pad, 256), 256, 0, st>>>(x.rs, y.rs, x.n_pad,
+                                                                     (float4 *)L.rs_xy);
+    ADAGIO_CHECK_LAUNCH();
+    // ex = q4_i q4_j + (c_acc + c_r)(n2_i + n2_j) dominates the split model's
+    // q1 term, because 2 |a| |b| <= |a|^2 + |b|^2
+    a.cx = x.bm.cacc + L.cc.c_r;
+    a.cy = y.bm.cacc + L.cc.c_r;
     a.scale_x = x.scale;
     a.scale_y = y.scale;
     const int T = (int)(x.n_pad / kTile);
@@ -667,9 +721,15 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     a.dump = reinterpret_cast<float4 *>(L.dump);
     a.dump_tiles = L.dump_tiles;
     ADAGIO_CUDA(cudaMemsetAsync(L.partials, 0, sizeof(CertPartial) * L.grid, st));
-    ADAGIO_CUDA(cudaFuncSetAttribute(cert_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)kSmemBytes));
-    cert_tc_kernel<<<L.grid, kThreads, kSmemBytes, st>>>(mxh, mxl, myh, myl, a);
+    if (L.dump) {
+        ADAGIO_CUDA(cudaFuncSetAttribute(cert_tc_kernel<true>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+        cert_tc_kernel<true><<<L.grid / kEpiWarps, kThreads, kSmemBytes, st>>>(mxh, mxl, myh, myl, a);
+    } else {
+        ADAGIO_CUDA(cudaFuncSetAttribute(cert_tc_kernel<false>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+        cert_tc_kernel<false><<<L.grid / kEpiWarps, kThreads, kSmemBytes, st>>>(mxh, mxl, myh, myl, a);
+    }
     ADAGIO_CHECK_LAUNCH();
     return true;
 }

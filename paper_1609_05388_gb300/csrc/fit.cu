@@ -18,6 +18,7 @@
 #include "pca.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <cstring>
 #include <vector>
 
@@ -126,9 +127,15 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
         s_cap = o->s >= 0 ? o->s : o->m / 2;
         k_cap = o->m - s_cap;
     }
+    if (search && o->use_predictor) s_cap = std::max(s_cap, std::min(64, d));
     const size_t mark = ctx->ws.off;
+    using clk = std::chrono::steady_clock;
+    const auto t_start = clk::now();
+    double pca_ms = 0.0;
     PCA pca;
     pca.init(ctx, X, n, d, ldx, s_cap, o->seed, o->max_iter, o->tol, o->oversample, st);
+    pca_ms += std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
+    pca.elapsed_ms = &pca_ms;
     Prober pr{};
     pr.ctx = ctx;
     pr.X = X;
@@ -167,7 +174,17 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
         r_final = cap;
         s_final = pr.split_s(cap);
     } else {
-        const int start = (trace && trace->start_r > 0) ? std::min(trace->start_r, cap) : 0;
+        int start = (trace && trace->start_r > 0) ? std::min(trace->start_r, cap) : 0;
+        bool verify_only = trace && trace->verify_only;
+        if (o->use_predictor) {
+            // spectrum features from this fit's own PCA, then the network's guess
+            pca.extend(std::min(64, d), st);
+            float *feats = ws_array<float>(ctx, 68);
+            spectrum_features(pca.theta, pca.s_done, pca.C, d, n, o->eps, feats, st);
+            start = std::max(1, std::min(predict_one(ctx, feats, st), cap));
+            verify_only = true;
+            ctx->last_fit.predicted_m = start;
+        }
         int last_fail = 0, first_ok = -1;
         if (start > 0) {
             // a predicted dimension is verified first; on failure the search
@@ -187,7 +204,7 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
                 last_fail = r;
             }
         }
-        const bool accept_prediction = trace && trace->verify_only && first_ok == start && start > 0;
+        const bool accept_prediction = verify_only && first_ok == start && start > 0;
         if (first_ok >= 0 && !accept_prediction) {
             int lo = last_fail, hi = first_ok;
             while (hi - lo > 1) {
@@ -217,6 +234,13 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
     }
     if (m_out) *m_out = r_final;
     if (s_out) *s_out = s_final;
+    if (!(search && o->use_predictor)) ctx->last_fit.predicted_m = 0;
+    ctx->last_fit.probes = (int)pr.probes.size();
+    ctx->last_fit.full_certs = 0;
+    for (const auto &q : pr.probes) ctx->last_fit.full_certs += q.ok ? 1 : 0;
+    ctx->last_fit.pca_iterations = pca.iterations;
+    ctx->last_fit.s_computed = pca.s_done;
+    ctx->last_fit.pca_ms = pca_ms;
     if (trace) {
         trace->probes.clear();
         for (const auto &p : pr.probes) trace->probes.push_back({p.r, p.ok ? 1 : 0, p.max});
@@ -224,6 +248,7 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
         trace->s_computed = pca.s_done;
     }
     ADAGIO_CUDA(cudaStreamSynchronize(st));
+    ctx->last_fit.total_ms = std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
     ctx->ws.off = mark;
     return status;
 }

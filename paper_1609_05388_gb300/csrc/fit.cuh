@@ -40,9 +40,10 @@ int fit_entry(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
               const adagio_fit_opts *opts, float *A, int m_cap, int *m_out, int *s_out,
               adagio_cert *cert, void *stream, FitTrace *trace);
 
-// Fit that starts from the dimension predictor's guess (mlp.cu).
-int fit_predicted(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
-                  const adagio_fit_opts *opts, float *A, int m_cap, int *m_out, int *s_out,
-                  adagio_cert *cert, void *stream);
+// Dimension predictor (mlp.cu).
+bool has_predictor(const adagio_ctx *ctx);
+int predict_one(adagio_ctx *ctx, const float *feats, cudaStream_t st);
+void spectrum_features(const double *theta, int have, const float *C, int d, int64_t n, double eps,
+                       float *feats, cudaStream_t st);
 
 }  // namespace adagio

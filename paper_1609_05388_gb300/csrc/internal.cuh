@@ -78,6 +78,7 @@ struct adagio_ctx {
     adagio::Predictor *predictor = nullptr;
     // statistics of the most recent certificate (for diagnostics)
     adagio_cert_stats last_stats{-1.0, -1.0, -1.0, 0, 0, 0};
+    adagio_fit_stats last_fit{0, 0, 0, 0, 0.0, 0.0, 0};
     int collect_timing = 0;
 };
 

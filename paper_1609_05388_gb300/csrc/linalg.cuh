@@ -26,6 +26,13 @@ void gemm_tn_splitk(int M, int N, int64_t K, const float *A, int64_t lda, const 
                     int64_t ldb, float *C, int64_t ldc, float *partials, cudaStream_t st);
 int64_t splitk_chunks(int64_t K);
 
+// C[M x N] (FP64, row-major, ld N) = A B with FP64 accumulation, split over K
+// in chunks of kchunk so that small outputs still use many SMs; partials holds
+// ceil(K / kchunk) * M * N doubles.
+void gemm_f64_splitk(int M, int N, int K, MatView<float> A, MatView<float> B, double *C,
+                     double *partials, int kchunk, cudaStream_t st);
+constexpr int kF64Chunk = 32;
+
 // Y[n x m] = X[n x d] A[m x d]^T, both row-major (the embedding, Algorithm 1).
 void embed_gemm(const float *X, int64_t ldx, int64_t n, int d, const float *A, int64_t lda, int m,
                 float *Y, int64_t ldy, cudaStream_t st);
@@ -36,7 +43,7 @@ void embed_gemm(const float *X, int64_t ldx, int64_t n, int d, const float *A, i
 void cholesky_upper(double *G, int b, double floor_rel, cudaStream_t st);
 
 // V (b x d rows, FP32, leading dimension ldv) <- R^{-T} V, i.e. row i of the
-// result is (v_i - sum_{k<i} R_ki r_k) / R_ii; FP64 arithmetic.
+// result is (v_i - sum_{k<i} R_ki r_k) / R_ii; FP32 arithmetic.
 void trsm_rows(const double *R, int b, float *V, int64_t ldv, int d, cudaStream_t st);
 
 // Symmetric eigen-decomposition of a b x b matrix (b <= kJacobiMax) by

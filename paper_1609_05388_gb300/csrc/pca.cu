@@ -20,6 +20,7 @@
 #include "prep.cuh"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstring>
 
@@ -37,6 +38,7 @@ size_t pca_bytes(int64_t n, int d, int s_cap, int oversample) {
     bytes += align_up((size_t)b * b * sizeof(float), 256);                          // U
     bytes += align_up((size_t)(b + std::max(s_cap, 1)) * sizeof(double), 256);     // theta
     bytes += align_up((size_t)b * sizeof(float), 256);                              // residuals
+    bytes += align_up((size_t)ceil_div(d, kF64Chunk) * b * b * sizeof(double), 256); // split-K
     (void)oversample;
     return bytes + 8192;
 }
@@ -74,6 +76,7 @@ void PCA::init(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int64_t ldx
     theta_blk = ws_array<double>(ctx, bmax);
     theta = ws_array<double>(ctx, std::max(s_cap, 1));
     res = ws_array<float>(ctx, bmax);
+    f64part = ws_array<double>(ctx, (size_t)ceil_div(d, kF64Chunk) * bmax * bmax);
     unsigned hflag = 0;
     ADAGIO_CUDA(cudaMemcpyAsync(&hflag, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
     ADAGIO_CUDA(cudaStreamSynchronize(st));
@@ -91,8 +94,8 @@ void PCA::deflate(float *M, int r, cudaStream_t st) {
 
 void PCA::orth(float *M, int b, cudaStream_t st) {
     for (int pass = 0; pass < 2; ++pass) {
-        gemm<float, float, double, double>(b, b, d, 1.0, MatView<float>{M, d, 1},
-                                           MatView<float>{M, 1, d}, 0.0, G, b, st);
+        gemm_f64_splitk(b, b, d, MatView<float>{M, d, 1}, MatView<float>{M, 1, d}, G, f64part,
+                        kF64Chunk, st);
         cholesky_upper(G, b, pass == 0 ? 1e-12 : 1e-15, st);
         trsm_rows(G, b, M, d, d, st);
     }
@@ -100,6 +103,14 @@ void PCA::orth(float *M, int b, cudaStream_t st) {
 
 void PCA::extend(int s_needed, cudaStream_t st) {
     s_needed = std::min(s_needed, s_cap);
+    const auto t0 = std::chrono::steady_clock::now();
+    struct Timer {
+        double *acc;
+        std::chrono::steady_clock::time_point t0;
+        ~Timer() {
+            if (acc) *acc += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        }
+    } timer{elapsed_ms, t0};
     while (s_done < s_needed) {
         const int remaining = d - s_done;
         const int s_blk = std::min({s_cap - s_done, kJacobiMax - p, remaining});
@@ -109,34 +120,40 @@ void PCA::extend(int s_needed, cudaStream_t st) {
         orth(V, b, st);
         float *hres = nullptr;
         double *hth = nullptr;
+        // Rayleigh-Ritz (and the convergence test) every kRREvery iterations and
+        // on the last one; CholeskyQR2 keeps V orthonormal in between
+        constexpr int kRREvery = 4;
         for (int it = 0; it < max_iter; ++it) {
             ++iterations;
             // W = V C (C symmetric)
             gemm<float, float, float, float>(b, d, d, 1.0f, MatView<float>{V, d, 1},
                                              MatView<float>{C, d, 1}, 0.0f, W, d, st);
             deflate(W, b, st);
-            // Rayleigh-Ritz: H = V W^T, H = U diag(theta) U^T
-            gemm<float, float, double, double>(b, b, d, 1.0, MatView<float>{V, d, 1},
-                                               MatView<float>{W, 1, d}, 0.0, H, b, st);
-            jacobi_eig(H, b, theta_blk, U, 30, st);
-            // V <- U^T V, W <- U^T W
-            gemm<float, float, float, float>(b, d, b, 1.0f, MatView<float>{U, 1, b},
-                                             MatView<float>{V, d, 1}, 0.0f, T, d, st);
-            std::swap(V, T);
-            gemm<float, float, float, float>(b, d, b, 1.0f, MatView<float>{U, 1, b},
-                                             MatView<float>{W, d, 1}, 0.0f, T, d, st);
-            std::swap(W, T);
-            ritz_residuals(W, V, d, d, theta_blk, s_blk, res, st);
-            char *hs = reinterpret_cast<char *>(host_stage(ctx, (size_t)b * 8 + (size_t)b * 4 + 64));
-            hth = reinterpret_cast<double *>(hs);
-            hres = reinterpret_cast<float *>(hs + (size_t)b * 8);
-            ADAGIO_CUDA(cudaMemcpyAsync(hth, theta_blk, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
-            ADAGIO_CUDA(cudaMemcpyAsync(hres, res, sizeof(float) * s_blk, cudaMemcpyDeviceToHost, st));
-            ADAGIO_CUDA(cudaStreamSynchronize(st));
-            if (s_done == 0) theta1 = std::max(hth[0], 0.0);
-            float worst = 0.0f;
-            for (int i = 0; i < s_blk; ++i) worst = std::max(worst, hres[i]);
-            if (!(worst > tol * theta1) || b == remaining || it == max_iter - 1) break;
+            const bool last = it == max_iter - 1 || b == remaining;
+            if ((it % kRREvery) == kRREvery - 1 || last || it == 0) {
+                // Rayleigh-Ritz: H = V W^T, H = U diag(theta) U^T
+                gemm_f64_splitk(b, b, d, MatView<float>{V, d, 1}, MatView<float>{W, 1, d}, H, f64part,
+                                kF64Chunk, st);
+                jacobi_eig(H, b, theta_blk, U, 30, st);
+                // V <- U^T V, W <- U^T W
+                gemm<float, float, float, float>(b, d, b, 1.0f, MatView<float>{U, 1, b},
+                                                 MatView<float>{V, d, 1}, 0.0f, T, d, st);
+                std::swap(V, T);
+                gemm<float, float, float, float>(b, d, b, 1.0f, MatView<float>{U, 1, b},
+                                                 MatView<float>{W, d, 1}, 0.0f, T, d, st);
+                std::swap(W, T);
+                ritz_residuals(W, V, d, d, theta_blk, s_blk, res, st);
+                char *hs = reinterpret_cast<char *>(host_stage(ctx, (size_t)b * 8 + (size_t)b * 4 + 64));
+                hth = reinterpret_cast<double *>(hs);
+                hres = reinterpret_cast<float *>(hs + (size_t)b * 8);
+                ADAGIO_CUDA(cudaMemcpyAsync(hth, theta_blk, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
+                ADAGIO_CUDA(cudaMemcpyAsync(hres, res, sizeof(float) * s_blk, cudaMemcpyDeviceToHost, st));
+                ADAGIO_CUDA(cudaStreamSynchronize(st));
+                if (s_done == 0) theta1 = std::max(hth[0], 0.0);
+                float worst = 0.0f;
+                for (int i = 0; i < s_blk; ++i) worst = std::max(worst, hres[i]);
+                if (!(worst > tol * theta1) || last) break;
+            }
             // next iterate: V <- orth(W)
             std::swap(V, W);
             orth(V, b, st);

@@ -17,8 +17,9 @@ struct PCA {
     float *P = nullptr;        // s_cap x d principal rows (first s_done valid)
     double *theta = nullptr;   // eigenvalue estimates of those rows
     float *V = nullptr, *W = nullptr, *T = nullptr, *U = nullptr, *coef = nullptr, *res = nullptr;
-    double *G = nullptr, *H = nullptr, *theta_blk = nullptr;
+    double *G = nullptr, *H = nullptr, *theta_blk = nullptr, *f64part = nullptr;
     unsigned *flags = nullptr;
+    double *elapsed_ms = nullptr;  // optional: extend() adds its wall time here
 
     void init(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx, int s_cap,
               uint64_t seed, int max_iter, double tol, int oversample, cudaStream_t st);

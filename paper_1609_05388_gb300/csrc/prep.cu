@@ -143,28 +143,30 @@ __global__ void split_kernel(const float *__restrict__ X, int64_t n, int64_t n_p
 }  // namespace
 
 BoundModel bound_model(int precision, int K) {
-    // Coefficients of the pair error bound (cert_common.cuh), eight (BF16) to
-    // sixteen (FP16) standard deviations of the observed error of each
-    // arithmetic.
-    //  * products: the split arithmetic drops the lo*lo product and the
-    //    residual beyond hi + lo; the relative error of one term has an RMS of
-    //    3.2e-6 (BF16) or 5.4e-8 (FP16, scaled) and averages over the K terms,
-    //    hence the 4-norm form;
-    //  * accumulation: FP32 rounding of the running sum; per step at most
-    //    2^-24 of a partial sum bounded by ||a||_2 ||b||_2.
+    // Coefficients of the pair error bound (cert_common.cuh).
+    //  * products (c4): the split arithmetic drops lo*lo and the residual
+    //    beyond hi + lo; the relative error of one term has an RMS of 3.2e-6
+    //    (BF16) or 5.4e-8 (FP16, power-of-two scaled) and averages over the K
+    //    terms, hence the 4-norm form; eight (BF16) to sixteen (FP16) RMS.
+    //  * accumulation (cacc, times ||a||_2 ||b||_2):
+    //      FP32 SIMT: one FMA chain of K round-to-nearest steps, three RMS of
+    //      its random-walk error;
+    //      tensor cores: the FP32 accumulator truncates (up to one unit in the
+    //      last place per MMA, observed about half on average); each 64-wide
+    //      K chunk ends with 4 full-size MMAs (<= 4 * 2^-23 of the chunk's
+    //      absolute Gram, which sums to <= ||a|| ||b|| over the chunks) and the
+    //      chunks are added in FP32 with round to nearest (<= 2^-24 of the
+    //      running sum per chunk).
     BoundModel bm;
     const float u = 5.9604645e-08f;  // 2^-24
-    float steps;
-    switch (precision) {
-        case ADAGIO_PREC_FP16X3: bm.c4 = 9.0e-7f; steps = (float)K / 16.0f; break;
-        case ADAGIO_PREC_BF16X3: bm.c4 = 2.6e-5f; steps = (float)K / 16.0f; break;
-        default: bm.c4 = 0.0f; steps = (float)K; break;
+    if (precision == ADAGIO_PREC_FP32) {
+        bm.c4 = 0.0f;
+        bm.cacc = 3.0f * u * sqrtf(fmaxf((float)K, 1.0f) / 3.0f);
+    } else {
+        bm.c4 = precision == ADAGIO_PREC_FP16X3 ? 9.0e-7f : 2.6e-5f;
+        const float chunks = fmaxf((float)K / 64.0f, 1.0f);
+        bm.cacc = 8.0f * u + chunks * u;
     }
-    // the tensor cores' internal accumulation is not specified; its term gets
-    // twice the margin of the FP32 FMA chain (checked on the GPU by the
-    // tile-bound dump)
-    const float margin = precision == ADAGIO_PREC_FP32 ? 3.0f : 6.0f;
-    bm.cacc = margin * u * sqrtf(fmaxf(steps, 1.0f) / 3.0f);
     return bm;
 }
 

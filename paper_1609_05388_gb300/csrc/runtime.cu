@@ -186,6 +186,12 @@ int adagio_last_cert_stats(const adagio_ctx *ctx, adagio_cert_stats *out) {
     return ADAGIO_OK;
 }
 
+int adagio_last_fit_stats(const adagio_ctx *ctx, adagio_fit_stats *out) {
+    if (!ctx || !out) return ADAGIO_E_INVALID_ARG;
+    *out = ctx->last_fit;
+    return ADAGIO_OK;
+}
+
 uint64_t adagio_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 }  // extern "C"

@@ -1,0 +1,44 @@
+"""Runs certificates of the MNIST-shaped workload at a chosen size, for profilers.
+
+    python -m paper_1609_05388_gb300.profile_cert --n 16384 --m 400 --precision fp16x3 --reps 2
+
+The embedding is Y = X A^T with A = [P ; S (I - P^T P)] fitted by the library at
+dimension m, as in the benchmark; each repetition is one full adagio_distortion
+call (prep, tile kernel, recompute, finaliser).  Prints one JSON line with the
+per-stage times of the last repetition.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+
+import torch
+
+from . import adagio as lib
+from . import synth
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--m", type=int, default=400)
+    ap.add_argument("--eps", type=float, default=0.1)
+    ap.add_argument("--precision", default="fp16x3", choices=["fp32", "fp16x3", "bf16x3"])
+    ap.add_argument("--reps", type=int, default=2)
+    a = ap.parse_args()
+    prec = {"fp32": lib.PREC_FP32, "fp16x3": lib.PREC_FP16X3, "bf16x3": lib.PREC_BF16X3}[a.precision]
+    wl = synth.mnist_like(seed=1, n=a.n)
+    X = torch.from_numpy(wl.X).cuda()
+    with lib.Context(0) as ctx:
+        A, m, s, _, _ = ctx.fit(X, eps=0.0, m=a.m, seed=11, precision=lib.PREC_FP32)
+        Y = ctx.embed(A, X)
+        ctx.set_timing(True)
+        for _ in range(a.reps):
+            c = ctx.distortion(X, Y, a.eps, precision=prec)
+        st = ctx.last_cert_stats()
+    print(json.dumps({"n": a.n, "m": a.m, "precision": a.precision, "pairs": c.pairs,
+                      "max": c.max, "recomputed": c.recomputed, **st}))
+
+
+if __name__ == "__main__":
+    main()
