@@ -242,6 +242,73 @@ int adagio_fit(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
                const adagio_fit_opts *opts, float *A, int m_cap, int *m_out, int *s_out,
                adagio_cert *cert, void *stream);
 
+/* ------------------------------------------------------------- batched fit */
+/*
+ * One data set of a batched fit.  Inputs are set by the caller; the fields
+ * marked "out" are written by adagio_fit_batched.
+ */
+typedef struct {
+    const float *X;     /* device: n x d rows (row-major), leading dimension ldx >= d */
+    int64_t n;          /* points, >= 2 */
+    int d;              /* dimensions, >= 1 */
+    int64_t ldx;
+    double eps;         /* target maximum distortion in (0, 1); <= 0: fixed m */
+    int m;              /* the fixed target dimension when eps <= 0 */
+    int m_cap;          /* rows A can hold; the search probes up to min(m_cap, d) */
+    float *A;           /* device: m_cap x d (leading dimension d); out: first m_out rows */
+    int m_out, s_out;   /* out: chosen m and its number of principal rows */
+    int status;         /* out: ADAGIO_OK or ADAGIO_E_NOT_CERTIFIABLE */
+    int probes;         /* out: certificates the search ran */
+    int full_certs;     /* out: of those, the ones that ran to completion */
+    adagio_cert cert;   /* out: certificate of the returned map */
+} adagio_instance;
+
+/* Capture each lock-step round as one CUDA graph (instantiated and launched
+ * once) instead of launching its kernels one by one. */
+#define ADAGIO_BATCH_GRAPH 1
+
+/*
+ * Fits `count` independent data sets of uneven n and d.  The paper has no
+ * batched form: every instance gets exactly the fit adagio_fit computes for
+ * it with the same opts (Algorithm 1 with the Sec. 4.1 split, the certified
+ * search for the smallest m reaching eps), bit for bit.  The instances run in
+ * lock-step rounds: each round enqueues, on one stream per instance, the next
+ * piece of every unfinished instance (subspace iterations up to the next
+ * convergence test, or one probe of the search: JL rows, A, Y = X A^T and the
+ * exhaustive certificate), then synchronises once and takes every instance's
+ * host decision.  Small instances therefore share the GPU instead of running
+ * one after another, and a round costs one synchronisation for all of them.
+ *  count  1 .. 4096 instances; inst[i] as described above (X and A on the
+ *         device of ctx)
+ *  opts   shared options: s (-1 = floor(m/2)), seed, jl_dist, precision,
+ *         use_predictor (one batched network call after the first 64
+ *         principal directions), hist_lo/hist_hi, max_iter, tol, oversample;
+ *         opts->eps and opts->m are ignored (each instance has its own)
+ *  flags  0 or ADAGIO_BATCH_GRAPH
+ * The recompute queues and the workspace for all instances are reserved
+ * before the first round.  Synchronises `stream`.  Returns ADAGIO_OK when
+ * every instance has a map (an instance whose eps is not reached at its cap
+ * gets status ADAGIO_E_NOT_CERTIFIABLE and the map at the cap, as adagio_fit
+ * does); errors: INVALID_ARG, NONFINITE (in any instance), WORKSPACE,
+ * QUEUE_OVERFLOW, TIMEOUT, CUDA.
+ */
+int adagio_fit_batched(adagio_ctx *ctx, int count, adagio_instance *inst,
+                       const adagio_fit_opts *opts, int flags, void *stream);
+
+/*
+ * Statistics of the most recent adagio_fit_batched on ctx.
+ *  rounds       lock-step rounds (one synchronisation each)
+ *  graphs       rounds that ran as a captured CUDA graph
+ *  pca_rounds   rounds that advanced some instance's subspace iteration
+ *  total_ms     wall time of the call
+ */
+typedef struct {
+    int rounds, graphs, pca_rounds;
+    double total_ms;
+} adagio_batch_stats;
+
+int adagio_last_batch_stats(const adagio_ctx *ctx, adagio_batch_stats *out);
+
 /* ----------------------------------------------------- dimension predictor */
 /*
  * A small network predicts the target dimension the certified search would

@@ -68,7 +68,24 @@ class CertStatsStruct(ctypes.Structure):
 class FitStatsStruct(ctypes.Structure):
     _fields_ = [("probes", ctypes.c_int), ("full_certs", ctypes.c_int),
                 ("pca_iterations", ctypes.c_int), ("s_computed", ctypes.c_int),
-                ("pca_ms", ctypes.c_double), ("total_ms", ctypes.c_double)]
+                ("pca_ms", ctypes.c_double), ("total_ms", ctypes.c_double),
+                ("predicted_m", ctypes.c_int)]
+
+
+class InstanceStruct(ctypes.Structure):
+    _fields_ = [("X", ctypes.c_void_p), ("n", ctypes.c_int64), ("d", ctypes.c_int),
+                ("ldx", ctypes.c_int64), ("eps", ctypes.c_double), ("m", ctypes.c_int),
+                ("m_cap", ctypes.c_int), ("A", ctypes.c_void_p), ("m_out", ctypes.c_int),
+                ("s_out", ctypes.c_int), ("status", ctypes.c_int), ("probes", ctypes.c_int),
+                ("full_certs", ctypes.c_int), ("cert", CertStruct)]
+
+
+class BatchStatsStruct(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_int), ("graphs", ctypes.c_int), ("pca_rounds", ctypes.c_int),
+                ("total_ms", ctypes.c_double)]
+
+
+BATCH_GRAPH = 1
 
 
 class AdagioError(RuntimeError):
@@ -125,10 +142,24 @@ def _load() -> ctypes.CDLL:
         "adagio_fit": (i32, [vp, vp, i64, i32, i64, ctypes.POINTER(FitOptsStruct), vp, i32,
                              ctypes.POINTER(i32), ctypes.POINTER(i32), ctypes.POINTER(CertStruct),
                              vp]),
+        "adagio_fit_batched": (i32, [vp, i32, ctypes.POINTER(InstanceStruct),
+                                     ctypes.POINTER(FitOptsStruct), i32, vp]),
+        "adagio_last_batch_stats": (i32, [vp, ctypes.POINTER(BatchStatsStruct)]),
         "adagio_set_timing": (i32, [vp, i32]),
         "adagio_last_cert_stats": (i32, [vp, ctypes.POINTER(CertStatsStruct)]),
         "adagio_launch_count": (ctypes.c_uint64, []),
         "adagio_last_fit_stats": (i32, [vp, ctypes.POINTER(FitStatsStruct)]),
+        "adagio_mlp_num_params": (i64, []),
+        "adagio_mlp_init": (i32, [vp, ctypes.c_uint64]),
+        "adagio_mlp_set_params": (i32, [vp, vp, i64]),
+        "adagio_mlp_get_params": (i32, [vp, vp, i64]),
+        "adagio_mlp_forward": (i32, [vp, vp, i32, vp, vp]),
+        "adagio_mlp_grad": (i32, [vp, vp, vp, i32, ctypes.POINTER(f64), vp, vp]),
+        "adagio_mlp_train_step": (i32, [vp, vp, vp, i32, ctypes.c_float, ctypes.POINTER(f64), vp]),
+        "adagio_predict_m": (i32, [vp, vp, i32, vp, vp]),
+        "adagio_features": (i32, [vp, vp, i64, i32, i64, f64, ctypes.POINTER(FitOptsStruct), vp, vp]),
+        "adagio_mlp_save": (i32, [vp, ctypes.c_char_p]),
+        "adagio_mlp_load": (i32, [vp, ctypes.c_char_p]),
         "adagio_debug_tile_bounds": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, i32, i64, vp, vp,
                                            vp]),
         "adagio_distortion_noalloc": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, f64, f64, f64,
@@ -150,7 +181,12 @@ def exported_symbols() -> list[str]:
                         "adagio_embed", "adagio_jl_matrix", "adagio_pca", "adagio_assemble",
                         "adagio_fit", "adagio_set_timing", "adagio_last_cert_stats",
                         "adagio_launch_count", "adagio_debug_tile_bounds",
-                        "adagio_distortion_noalloc", "adagio_last_fit_stats") if hasattr(LIB, n)]
+                        "adagio_distortion_noalloc", "adagio_last_fit_stats",
+                        "adagio_mlp_num_params", "adagio_mlp_init", "adagio_mlp_set_params",
+                        "adagio_mlp_get_params", "adagio_mlp_forward", "adagio_mlp_grad",
+                        "adagio_mlp_train_step", "adagio_predict_m", "adagio_features",
+                        "adagio_mlp_save", "adagio_mlp_load", "adagio_fit_batched",
+                        "adagio_last_batch_stats") if hasattr(LIB, n)]
 
 
 def launch_count() -> int:
@@ -340,6 +376,66 @@ class Context:
                                         a.ld, _stream(a, *(v for v in (p, s_) if v))))
         return A
 
+    # ------------------------------------------------------ dimension predictor
+    @staticmethod
+    def mlp_num_params() -> int:
+        return int(LIB.adagio_mlp_num_params())
+
+    def mlp_init(self, seed: int = 0):
+        self._check(LIB.adagio_mlp_init(self.h, seed))
+
+    def mlp_set_params(self, vec):
+        v = np.ascontiguousarray(vec, dtype=np.float32)
+        self._check(LIB.adagio_mlp_set_params(self.h, v.ctypes.data, v.size))
+
+    def mlp_get_params(self) -> np.ndarray:
+        v = np.empty(self.mlp_num_params(), dtype=np.float32)
+        self._check(LIB.adagio_mlp_get_params(self.h, v.ctypes.data, v.size))
+        return v
+
+    def mlp_forward(self, feats) -> np.ndarray:
+        f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, 68)
+        y = np.empty(f.shape[0], dtype=np.float32)
+        self._check(LIB.adagio_mlp_forward(self.h, f.ctypes.data, f.shape[0], y.ctypes.data, None))
+        return y
+
+    def mlp_grad(self, feats, target):
+        f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, 68)
+        t = np.ascontiguousarray(target, dtype=np.float32).reshape(-1)
+        g = np.empty(self.mlp_num_params(), dtype=np.float32)
+        loss = ctypes.c_double(0.0)
+        self._check(LIB.adagio_mlp_grad(self.h, f.ctypes.data, t.ctypes.data, f.shape[0],
+                                        ctypes.byref(loss), g.ctypes.data, None))
+        return loss.value, g
+
+    def mlp_train_step(self, feats, target, lr: float) -> float:
+        f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, 68)
+        t = np.ascontiguousarray(target, dtype=np.float32).reshape(-1)
+        loss = ctypes.c_double(0.0)
+        self._check(LIB.adagio_mlp_train_step(self.h, f.ctypes.data, t.ctypes.data, f.shape[0],
+                                              lr, ctypes.byref(loss), None))
+        return loss.value
+
+    def predict_m(self, feats) -> np.ndarray:
+        f = np.ascontiguousarray(feats, dtype=np.float32).reshape(-1, 68)
+        m = np.empty(f.shape[0], dtype=np.int32)
+        self._check(LIB.adagio_predict_m(self.h, f.ctypes.data, f.shape[0], m.ctypes.data, None))
+        return m
+
+    def features(self, X, eps: float, opts: FitOptsStruct | None = None) -> np.ndarray:
+        x = _Arr(X)
+        out = np.empty(68, dtype=np.float32)
+        self._check(LIB.adagio_features(self.h, x.ptr, x.rows, x.cols, x.ld, eps,
+                                        ctypes.byref(opts) if opts is not None else None,
+                                        out.ctypes.data, _stream(x)))
+        return out
+
+    def mlp_save(self, path: str):
+        self._check(LIB.adagio_mlp_save(self.h, path.encode()))
+
+    def mlp_load(self, path: str):
+        self._check(LIB.adagio_mlp_load(self.h, path.encode()))
+
     # ---------------------------------------------------------------------- fit
     @staticmethod
     def default_opts(**kw) -> FitOptsStruct:
@@ -371,3 +467,47 @@ class Context:
                                         m_cap, ctypes.byref(mo), ctypes.byref(so), ctypes.byref(c),
                                         _stream(x, a)), allow=(E_NOT_CERTIFIABLE,))
         return A[: mo.value], mo.value, so.value, Certificate.from_struct(c), rc
+
+    def fit_batched(self, Xs, eps, m_cap=None, m=None, graph: bool = False,
+                    opts: FitOptsStruct | None = None, **kw):
+        """Fits a list of CUDA float32 tensors (n_i x d_i) in one batched call.
+
+        eps: one value or one per instance (<= 0: fixed m[i]).  Returns a list of
+        dicts (A, m, s, status, probes, full_certs, cert), A on the device.
+        """
+        import torch
+        count = len(Xs)
+        epss = list(eps) if hasattr(eps, "__len__") else [eps] * count
+        caps = list(m_cap) if hasattr(m_cap, "__len__") else [m_cap] * count
+        ms = list(m) if hasattr(m, "__len__") else [m] * count
+        o = opts if opts is not None else self.default_opts(**kw)
+        arr = (InstanceStruct * count)()
+        keep = []
+        for i, X in enumerate(Xs):
+            if not (_is_torch(X) and X.is_cuda and X.dtype == torch.float32 and X.stride(1) == 1):
+                raise TypeError("fit_batched takes CUDA float32 tensors with contiguous rows")
+            n, d = X.shape
+            cap = caps[i] if caps[i] is not None else (d if epss[i] > 0 else ms[i])
+            A = torch.empty((max(cap, 1), d), dtype=torch.float32, device=X.device)
+            keep.append((X, A))
+            e = arr[i]
+            e.X, e.n, e.d, e.ldx = X.data_ptr(), n, d, X.stride(0) if n > 1 else d
+            e.eps = float(epss[i]) if epss[i] is not None else 0.0
+            e.m = int(ms[i] or 0)
+            e.m_cap = int(cap)
+            e.A = A.data_ptr()
+        stream = torch.cuda.current_stream().cuda_stream
+        self._check(LIB.adagio_fit_batched(self.h, count, arr, ctypes.byref(o),
+                                           BATCH_GRAPH if graph else 0, stream))
+        out = []
+        for i in range(count):
+            e = arr[i]
+            out.append({"A": keep[i][1][: e.m_out], "m": e.m_out, "s": e.s_out,
+                        "status": e.status, "probes": e.probes, "full_certs": e.full_certs,
+                        "cert": Certificate.from_struct(e.cert)})
+        return out
+
+    def last_batch_stats(self) -> dict:
+        s = BatchStatsStruct()
+        self._check(LIB.adagio_last_batch_stats(self.h, ctypes.byref(s)))
+        return {k: getattr(s, k) for k, _ in BatchStatsStruct._fields_}

@@ -6,6 +6,7 @@
 #include "jl.cuh"
 #include "linalg.cuh"
 #include "pca.cuh"
+#include "api_guard.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -13,28 +14,6 @@
 #include <exception>
 
 using namespace adagio;
-
-#define API_BEGIN(ctx)                                  \
-    if (!(ctx)) return ADAGIO_E_INVALID_ARG;            \
-    (ctx)->last_error.clear();                          \
-    try {                                               \
-        DeviceGuard guard_((ctx)->device);              \
-        ws_reset(ctx);
-
-#define API_END(ctx)                                    \
-    }                                                   \
-    catch (const Error &e) {                            \
-        (ctx)->last_error = e.msg;                      \
-        return e.code;                                  \
-    }                                                   \
-    catch (const std::exception &e) {                   \
-        (ctx)->last_error = e.what();                   \
-        return ADAGIO_E_CUDA;                           \
-    }                                                   \
-    catch (...) {                                       \
-        (ctx)->last_error = "unknown failure";          \
-        return ADAGIO_E_CUDA;                           \
-    }
 
 static size_t staging_bytes(adagio_ctx *ctx, const void *p, int64_t rows, int cols) {
     return is_device_ptr(p, ctx->device) ? 0 : align_up((size_t)rows * cols * sizeof(float), 256);

@@ -11,14 +11,14 @@ namespace adagio {
 
 // Initial capacity of the recompute queue: 1/1024 of the pairs (at least
 // 2^20 entries); it grows to the observed need when a run overflows it.
-static unsigned long long queue_capacity(unsigned long long pairs) {
+unsigned long long cert_queue_capacity(unsigned long long pairs) {
     unsigned long long q = pairs / 1024;
     if (q < (1ull << 20)) q = 1ull << 20;
     if (q > pairs) q = pairs;
     return q;
 }
 
-static void ensure_queue(adagio_ctx *ctx, unsigned long long cap) {
+void cert_ensure_queue(adagio_ctx *ctx, unsigned long long cap) {
     if (ctx->qbuf_cap >= cap) return;
     if (ctx->qbuf_fixed)
         fail(ADAGIO_E_QUEUE_OVERFLOW, "recompute queue needs %llu entries, fixed capacity is %llu", cap,
@@ -39,94 +39,188 @@ static void ensure_queue(adagio_ctx *ctx, unsigned long long cap) {
     ctx->qbuf_cap = cap;
 }
 
-static int tile_grid(adagio_ctx *ctx, int precision) {
+void cert_init() {
+    cert_tc_init();
+    cert_simt_init();
+    recompute_init();
+}
+
+static int partial_slots(adagio_ctx *ctx, int64_t n, int precision) {
     if (precision == ADAGIO_PREC_FP32) return ctx->num_sms;  // 1 CTA / SM (64 KB hist + regs)
-    return cert_tc_grid(ctx);
+    return cert_tc_ctas(ctx, n) * 8;                          // one slot per epilogue warp
 }
 
 static int recompute_grid(adagio_ctx *ctx) { return ctx->num_sms * 4; }
 
-size_t certify_bytes(adagio_ctx *ctx, int64_t n, int d, int m, int precision) {
+size_t cert_prep_x_bytes(int64_t n, int d, int precision) {
     const bool tc = precision != ADAGIO_PREC_FP32;
-    const unsigned long long pairs = (unsigned long long)n * (n - 1) / 2;
-    size_t b = prep_bytes(n, d, !tc, tc) + prep_bytes(n, m, !tc, tc);
-    b += align_up(sizeof(CertPartial) * (tile_grid(ctx, precision) + recompute_grid(ctx)), 256);
-    (void)pairs;
-    b += 4096 + sizeof(CertDevResult);
+    return prep_bytes(n, d, !tc, tc);
+}
+
+size_t cert_job_bytes(adagio_ctx *ctx, int64_t n, int m, int precision) {
+    const bool tc = precision != ADAGIO_PREC_FP32;
+    size_t b = prep_bytes(n, m, !tc, tc);
+    b += align_up(sizeof(CertPartial) * (partial_slots(ctx, n, precision) + recompute_grid(ctx)), 256);
+    b += 4 * 256 + align_up(sizeof(CertDevResult), 256);
     if (tc) b += align_up((size_t)((n + 127) / 128 * 128) * sizeof(float4), 256);
-    return b;
+    return b + 1024;
+}
+
+size_t certify_bytes(adagio_ctx *ctx, int64_t n, int d, int m, int precision) {
+    return cert_prep_x_bytes(n, d, precision) + cert_job_bytes(ctx, n, m, precision) + 4096;
+}
+
+void cert_prepare_x(adagio_ctx *ctx, const float *X, int64_t ldx, int64_t n, int d, int precision,
+                    PrepMat &px, unsigned *flags, cudaStream_t st) {
+    const bool tc = precision != ADAGIO_PREC_FP32;
+    prep_matrix(ctx, X, n, d, ldx, precision, !tc, tc, px, flags, st);
+}
+
+void cert_job_setup(adagio_ctx *ctx, CertJob &job, int2 *queue, unsigned long long qcap) {
+    job.flags = ws_array<unsigned>(ctx, 1);
+    job.stop = ws_array<int>(ctx, 1);
+    job.status = ws_array<int>(ctx, 1);
+    job.qcount = ws_array<unsigned long long>(ctx, 1);
+    job.nparts = partial_slots(ctx, job.n, job.opt.precision);
+    job.rgrid = recompute_grid(ctx);
+    job.partials = ws_array<CertPartial>(ctx, job.nparts);
+    job.rparts = ws_array<CertPartial>(ctx, job.rgrid);
+    job.dres = ws_array<CertDevResult>(ctx, 1);
+    const bool tc = job.opt.precision != ADAGIO_PREC_FP32;
+    const int64_t n_pad = (job.n + kTileRows - 1) / kTileRows * kTileRows;
+    job.rs_xy = tc ? ws_array<float4>(ctx, (size_t)n_pad) : nullptr;
+    job.queue = queue;
+    job.qcap = qcap;
+}
+
+void cert_job_enqueue(adagio_ctx *ctx, CertJob &job, cudaStream_t st, cudaEvent_t *ev) {
+    const bool tc = job.opt.precision != ADAGIO_PREC_FP32;
+    const CertOptions &opt = job.opt;
+    if (job.clear_flags) ADAGIO_CUDA(cudaMemsetAsync(job.flags, 0, sizeof(unsigned), st));
+    ADAGIO_CUDA(cudaMemsetAsync(job.stop, 0, sizeof(int), st));
+    ADAGIO_CUDA(cudaMemsetAsync(job.status, 0, sizeof(int), st));
+    ADAGIO_CUDA(cudaMemsetAsync(job.qcount, 0, sizeof(unsigned long long), st));
+    prep_matrix(ctx, job.Y, job.n, job.m, job.ldy, opt.precision, !tc, tc, job.py, job.flags, st);
+    if (ev) ADAGIO_CUDA(cudaEventRecord(ev[1], st));
+
+    CertLaunch L;
+    L.ctx = ctx;
+    L.x = job.px;
+    L.y = &job.py;
+    L.cc.lo = (float)opt.lo;
+    L.cc.hi = (float)opt.hi;
+    L.cc.w = (float)((opt.hi - opt.lo) / kBins);
+    L.cc.inv_w = (float)(kBins / (opt.hi - opt.lo));
+    L.cc.eps = (float)opt.eps;
+    L.cc.c_r = 8.0f * 5.9604645e-08f;
+    L.cc.lo_is_floor = opt.lo <= 0.0;
+    L.grid = job.nparts;
+    L.partials = job.partials;
+    L.queue = job.queue;
+    L.qcount = job.qcount;
+    L.qcap = job.qcap;
+    L.stop_flag = opt.stop_early ? job.stop : nullptr;
+    L.status = job.status;
+    L.dump = opt.dump;
+    L.dump_tiles = opt.dump_tiles;
+    L.rs_xy = job.rs_xy;
+    if (tc) {
+        if (!launch_cert_tc(L, opt.precision, st))
+            fail(ADAGIO_E_UNSUPPORTED, "tensor-core certificate does not support n=%lld",
+                 (long long)job.n);
+    } else {
+        launch_cert_simt(L, st);
+    }
+    if (ev) ADAGIO_CUDA(cudaEventRecord(ev[2], st));
+    launch_recompute(job.X, job.ldx, job.d, job.Y, job.ldy, job.m, job.queue, job.qcount, job.qcap,
+                     L.cc, job.rparts, job.rgrid, st);
+    launch_finalize(job.partials, job.nparts, job.rparts, job.rgrid, job.qcount, job.flags,
+                    job.status, job.stop, job.dres, st);
+}
+
+int cert_job_collect(const CertJob &job, const CertDevResult &h, adagio_cert *out, bool *stopped) {
+    const unsigned long long pairs = (unsigned long long)job.n * (unsigned long long)(job.n - 1) / 2;
+    if (h.flags & 1u) fail(ADAGIO_E_NONFINITE, "input holds NaN or Inf");
+    if (h.status != 0)
+        fail(ADAGIO_E_TIMEOUT, "certificate kernel gave up a bounded wait (status %d)", h.status);
+    // a stopped certificate found a certain violation on the fast path: its
+    // verdict does not depend on the recompute queue, so an overflow is moot
+    if (h.qlen > job.qcap && !h.stopped) return ADAGIO_E_QUEUE_OVERFLOW;
+    if (stopped) *stopped = h.stopped != 0;
+    if (!h.stopped) {
+        if (h.fast_pairs + h.queued != pairs || h.queued != h.qlen ||
+            h.recomputed + h.degenerate != h.qlen)
+            fail(ADAGIO_E_CUDA,
+                 "internal: pair accounting mismatch (fast %llu + queued %llu != %llu, recomputed "
+                 "%llu, degenerate %llu)",
+                 h.fast_pairs, h.queued, pairs, h.recomputed, h.degenerate);
+    }
+    const CertOptions &opt = job.opt;
+    std::memset(out, 0, sizeof(*out));
+    out->pairs = pairs;
+    out->degenerate = h.degenerate;
+    out->violations = h.violations;
+    out->overflow = h.overflow;
+    out->recomputed = h.recomputed + h.degenerate;
+    std::memcpy(out->hist, h.hist, sizeof(out->hist));
+    const unsigned long long good = pairs - h.degenerate;
+    if (h.max >= 0.0f) {
+        out->max = h.max;
+        out->argmax_i = h.argmax_i;
+        out->argmax_j = h.argmax_j;
+    } else {
+        out->max = 0.0;
+        out->argmax_i = out->argmax_j = -1;
+    }
+    out->mean = good ? h.sum / (double)good : 0.0;
+    out->max_err_bound = std::max((double)h.max_bound, 1e-12);
+    out->mean_err_bound = good ? h.bound_sum / (double)good : 0.0;
+    out->hist_lo = opt.lo;
+    out->hist_hi = opt.hi;
+    out->eps = opt.eps;
+    return ADAGIO_OK;
 }
 
 int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_t ldy, int64_t n,
             int d, int m, const CertOptions &opt, adagio_cert *out, cudaStream_t st,
-            bool *stopped) {
+            bool *stopped, const PrepMat *px_ready) {
     const bool tc = opt.precision != ADAGIO_PREC_FP32;
     const unsigned long long pairs = (unsigned long long)n * (unsigned long long)(n - 1) / 2;
-    if (!ctx->qbuf_fixed) ensure_queue(ctx, queue_capacity(pairs));
+    if (!ctx->qbuf_fixed) cert_ensure_queue(ctx, cert_queue_capacity(pairs));
+    if (tc) tc_prepare(ctx, (int)((n + kTileRows - 1) / kTileRows));
     const size_t mark = ctx->ws.off;
-
     for (int attempt = 0; attempt < 2; ++attempt) {
         ctx->ws.off = mark;
-        unsigned *flags = ws_array<unsigned>(ctx, 1);
-        int *stop = ws_array<int>(ctx, 1);
-        int *status = ws_array<int>(ctx, 1);
-        unsigned long long *qcount = ws_array<unsigned long long>(ctx, 1);
-        ADAGIO_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
-        ADAGIO_CUDA(cudaMemsetAsync(stop, 0, sizeof(int), st));
-        ADAGIO_CUDA(cudaMemsetAsync(status, 0, sizeof(int), st));
-        ADAGIO_CUDA(cudaMemsetAsync(qcount, 0, sizeof(unsigned long long), st));
-
         cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
         if (ctx->collect_timing) {
             for (auto &e : ev) ADAGIO_CUDA(cudaEventCreate(&e));
             ADAGIO_CUDA(cudaEventRecord(ev[0], st));
         }
-        PrepMat px, py;
-        prep_matrix(ctx, X, n, d, ldx, opt.precision, !tc, tc, px, flags, st);
-        prep_matrix(ctx, Y, n, m, ldy, opt.precision, !tc, tc, py, flags, st);
-
-        CertLaunch L;
-        L.ctx = ctx;
-        L.x = &px;
-        L.y = &py;
-        L.cc.lo = (float)opt.lo;
-        L.cc.hi = (float)opt.hi;
-        L.cc.w = (float)((opt.hi - opt.lo) / kBins);
-        L.cc.inv_w = (float)(kBins / (opt.hi - opt.lo));
-        L.cc.eps = (float)opt.eps;
-        L.cc.c_r = 8.0f * 5.9604645e-08f;
-        L.cc.lo_is_floor = opt.lo <= 0.0;
-        L.grid = tile_grid(ctx, opt.precision);
-        L.partials = ws_array<CertPartial>(ctx, L.grid);
-        const int rgrid = recompute_grid(ctx);
-        CertPartial *rparts = ws_array<CertPartial>(ctx, rgrid);
-        const unsigned long long qcap = ctx->qbuf_cap;
-        L.queue = ctx->qbuf;
-        L.qcount = qcount;
-        L.qcap = qcap;
-        L.stop_flag = opt.stop_early ? stop : nullptr;
-        L.status = status;
-        L.dump = opt.dump;
-        L.dump_tiles = opt.dump_tiles;
-        CertDevResult *dres = ws_array<CertDevResult>(ctx, 1);
-        if (tc) L.rs_xy = ws_array<float4>(ctx, (size_t)px.n_pad);
-
-        if (ctx->collect_timing) ADAGIO_CUDA(cudaEventRecord(ev[1], st));
-        if (tc) {
-            if (!launch_cert_tc(L, opt.precision, st))
-                fail(ADAGIO_E_UNSUPPORTED, "tensor-core certificate does not support d=%d m=%d", d, m);
+        CertJob job;
+        job.X = X;
+        job.ldx = ldx;
+        job.Y = Y;
+        job.ldy = ldy;
+        job.n = n;
+        job.d = d;
+        job.m = m;
+        job.opt = opt;
+        cert_job_setup(ctx, job, ctx->qbuf, ctx->qbuf_cap);
+        PrepMat px;
+        if (px_ready) {
+            job.px = px_ready;
         } else {
-            launch_cert_simt(L, st);
+            // X's prep reports a non-finite input through the job's flag word
+            ADAGIO_CUDA(cudaMemsetAsync(job.flags, 0, sizeof(unsigned), st));
+            cert_prepare_x(ctx, X, ldx, n, d, opt.precision, px, job.flags, st);
+            job.px = &px;
+            job.clear_flags = false;
         }
-        if (ctx->collect_timing) ADAGIO_CUDA(cudaEventRecord(ev[2], st));
-        launch_recompute(X, ldx, d, Y, ldy, m, L.queue, qcount, qcap, L.cc, rparts, rgrid, st);
-        launch_finalize(L.partials, L.grid, rparts, rgrid, qcount, flags, status, stop, dres, st);
+        cert_job_enqueue(ctx, job, st, ctx->collect_timing ? ev : nullptr);
         if (ctx->collect_timing) ADAGIO_CUDA(cudaEventRecord(ev[3], st));
-
-        CertDevResult *h = reinterpret_cast<CertDevResult *>(host_stage(ctx, sizeof(CertDevResult) + 64));
-        unsigned long long *hq = reinterpret_cast<unsigned long long *>(h + 1);
-        ADAGIO_CUDA(cudaMemcpyAsync(h, dres, sizeof(CertDevResult), cudaMemcpyDeviceToHost, st));
-        ADAGIO_CUDA(cudaMemcpyAsync(hq, qcount, sizeof(unsigned long long), cudaMemcpyDeviceToHost, st));
+        CertDevResult *h =
+            reinterpret_cast<CertDevResult *>(host_stage(ctx, sizeof(CertDevResult) + 64));
+        ADAGIO_CUDA(cudaMemcpyAsync(h, job.dres, sizeof(CertDevResult), cudaMemcpyDeviceToHost, st));
         ADAGIO_CUDA(cudaStreamSynchronize(st));
         adagio_cert_stats &cs = ctx->last_stats;
         cs.prep_ms = cs.tile_ms = cs.recompute_ms = -1.0;
@@ -138,54 +232,20 @@ int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_
             cs.recompute_ms = ms[2];
             for (auto &e : ev) cudaEventDestroy(e);
         }
-        cs.queued = *hq;
-        cs.grid = L.grid;
-        {
-            const int64_t T = px.n_pad / kTileRows;
-            cs.tiles = T * (T + 1) / 2;
-        }
-
-        if (h->flags & 1u) fail(ADAGIO_E_NONFINITE, "input holds NaN or Inf");
-        if (h->status != 0)
-            fail(ADAGIO_E_TIMEOUT, "certificate kernel gave up a bounded wait (status %d)", h->status);
-        if (*hq > qcap) {
+        cs.queued = h->qlen;
+        cs.grid = job.nparts;
+        const int64_t T = (n + kTileRows - 1) / kTileRows;
+        cs.tiles = T * (T + 1) / 2;
+        const int rc = cert_job_collect(job, *h, out, stopped);
+        if (rc == ADAGIO_E_QUEUE_OVERFLOW) {
+            const unsigned long long need = h->qlen;
             if (attempt == 0 && !ctx->qbuf_fixed) {
-                ensure_queue(ctx, std::min<unsigned long long>(pairs, *hq + *hq / 8 + 1024));
+                cert_ensure_queue(ctx, std::min<unsigned long long>(pairs, need + need / 8 + 1024));
                 continue;
             }
             fail(ADAGIO_E_QUEUE_OVERFLOW, "recompute queue overflow (%llu pairs > capacity %llu)",
-                 (unsigned long long)*hq, qcap);
+                 need, job.qcap);
         }
-        if (stopped) *stopped = h->stopped != 0;
-        if (!h->stopped) {
-            if (h->fast_pairs + h->queued != pairs || h->queued != *hq ||
-                h->recomputed + h->degenerate != *hq)
-                fail(ADAGIO_E_CUDA,
-                     "internal: pair accounting mismatch (fast %llu + queued %llu != %llu, recomputed %llu, degenerate %llu)",
-                     h->fast_pairs, h->queued, pairs, h->recomputed, h->degenerate);
-        }
-        std::memset(out, 0, sizeof(*out));
-        out->pairs = pairs;
-        out->degenerate = h->degenerate;
-        out->violations = h->violations;
-        out->overflow = h->overflow;
-        out->recomputed = h->recomputed + h->degenerate;
-        std::memcpy(out->hist, h->hist, sizeof(out->hist));
-        const unsigned long long good = pairs - h->degenerate;
-        if (h->max >= 0.0f) {
-            out->max = h->max;
-            out->argmax_i = h->argmax_i;
-            out->argmax_j = h->argmax_j;
-        } else {
-            out->max = 0.0;
-            out->argmax_i = out->argmax_j = -1;
-        }
-        out->mean = good ? h->sum / (double)good : 0.0;
-        out->max_err_bound = std::max((double)h->max_bound, 1e-12);
-        out->mean_err_bound = good ? h->bound_sum / (double)good : 0.0;
-        out->hist_lo = opt.lo;
-        out->hist_hi = opt.hi;
-        out->eps = opt.eps;
         ctx->ws.off = mark;
         return ADAGIO_OK;
     }

@@ -35,13 +35,18 @@ struct CertDevResult {
     unsigned flags;
     int status;
     int stopped;  // the early-exit flag fired: statistics are partial
+    unsigned long long qlen;  // pairs pushed to the recompute queue (may exceed its capacity)
 };
 
 void launch_cert_simt(const CertLaunch &L, cudaStream_t st);
 int cert_simt_threads();
 // tcgen05 tile kernel; returns false when the shape is not supported
 bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st);
-int cert_tc_grid(adagio_ctx *ctx);
+void cert_tc_init();
+void cert_simt_init();
+void recompute_init();
+// every certificate kernel's attributes, set once (call before a capture)
+void cert_init();
 void tc_tile_coords(int T, long long t, int *I, int *J);
 
 // Exact recompute of the queued pairs from the original (uncentred) inputs.
@@ -53,6 +58,7 @@ void launch_recompute(const float *X, int64_t ldx, int d, const float *Y, int64_
 void launch_finalize(const CertPartial *fast, int nfast, const CertPartial *rec, int nrec,
                      const unsigned long long *qcount, const unsigned *flags, const int *status,
                      const int *stop_flag, CertDevResult *out, cudaStream_t st);
+int cert_tc_ctas(adagio_ctx *ctx, int64_t n);
 
 // Full certificate of (X, Y) given device pointers.  Fills `out`; returns the
 // status (ADAGIO_OK, ADAGIO_E_NONFINITE, ...).  stop_early: the tile kernels
@@ -72,7 +78,47 @@ struct CertOptions {
 void tile_coords(int precision, int T, long long t, int *I, int *J);
 int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_t ldy, int64_t n,
             int d, int m, const CertOptions &opt, adagio_cert *out, cudaStream_t st,
-            bool *stopped = nullptr);
+            bool *stopped = nullptr, const PrepMat *px_ready = nullptr);
 size_t certify_bytes(adagio_ctx *ctx, int64_t n, int d, int m, int precision);
+
+// The certificate as three host steps, so that many can be enqueued before
+// one synchronisation (batched fits, graph capture):
+//   cert_job_setup    carves the job's device scratch from the workspace
+//   cert_job_enqueue  enqueues all device work (no host sync, no allocation)
+//   cert_job_collect  interprets the copied-back CertDevResult
+struct CertJob {
+    const float *X = nullptr, *Y = nullptr;
+    int64_t ldx = 0, ldy = 0, n = 0;
+    int d = 0, m = 0;
+    CertOptions opt;
+    const PrepMat *px = nullptr;      // prepared X (owned by the caller, reusable)
+    unsigned *flags = nullptr;
+    int *stop = nullptr, *status = nullptr;
+    unsigned long long *qcount = nullptr;
+    CertPartial *partials = nullptr, *rparts = nullptr;
+    int nparts = 0, rgrid = 0;
+    CertDevResult *dres = nullptr;
+    float4 *rs_xy = nullptr;
+    int2 *queue = nullptr;
+    unsigned long long qcap = 0;
+    PrepMat py;                        // Y prep, carved from the workspace by enqueue
+    bool clear_flags = true;           // enqueue zeroes `flags` (false: the caller did)
+};
+size_t cert_job_bytes(adagio_ctx *ctx, int64_t n, int m, int precision);
+size_t cert_prep_x_bytes(int64_t n, int d, int precision);
+// prepares X for certificates (the split planes or the FP32 copy)
+void cert_prepare_x(adagio_ctx *ctx, const float *X, int64_t ldx, int64_t n, int d, int precision,
+                    PrepMat &px, unsigned *flags, cudaStream_t st);
+void cert_job_setup(adagio_ctx *ctx, CertJob &job, int2 *queue, unsigned long long qcap);
+// carves the Y prep from the workspace; `ev` (optional) gets ev[1] after the
+// preps and ev[2] after the tile kernel
+void cert_job_enqueue(adagio_ctx *ctx, CertJob &job, cudaStream_t st, cudaEvent_t *ev = nullptr);
+// 0 = ok; ADAGIO_E_QUEUE_OVERFLOW when the queue was too small (retry with more)
+int cert_job_collect(const CertJob &job, const CertDevResult &h, adagio_cert *out, bool *stopped);
+unsigned long long cert_queue_capacity(unsigned long long pairs);
+void cert_ensure_queue(adagio_ctx *ctx, unsigned long long cap);
+// tensor path: makes the tile schedule of T tile rows resident (call before capture)
+void tc_prepare(adagio_ctx *ctx, int T);
+
 
 }  // namespace adagio

@@ -177,12 +177,15 @@ void launch_cert_simt(const CertLaunch &L, cudaStream_t st) {
     p.dump = reinterpret_cast<float4 *>(L.dump);
     p.dump_tiles = L.dump_tiles;
     const size_t smem = (size_t)kBins * NT * sizeof(unsigned);
-    ADAGIO_CUDA(cudaFuncSetAttribute(cert_simt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+    set_max_dyn_smem((const void *)cert_simt_kernel, (int)smem);
     cert_simt_kernel<<<L.grid, NT, smem, st>>>(p);
     ADAGIO_CHECK_LAUNCH();
 }
 
 int cert_simt_threads() { return NT; }
+
+void cert_simt_init() {
+    set_max_dyn_smem((const void *)cert_simt_kernel, (int)((size_t)kBins * NT * sizeof(unsigned)));
+}
 
 }  // namespace adagio

@@ -637,46 +637,46 @@ std::vector<uint32_t> band_schedule(int T) {
 }  // namespace
 
 // Per-context cache of the device copy of the schedule.
-struct SchedCache {
-    int T = -1;
-    uint32_t *dev = nullptr;
-    size_t cap = 0;
-};
-
-static std::mutex g_sched_mu;
-
+// The schedule of T tile rows, resident on the device for the context's
+// lifetime (built on first use: a synchronous upload, so callers that capture
+// graphs make it resident first with tc_prepare).
 static const uint32_t *schedule_for(adagio_ctx *ctx, int T) {
-    std::lock_guard<std::mutex> lk(g_sched_mu);
-    static thread_local std::vector<std::pair<adagio_ctx *, SchedCache>> caches;
-    SchedCache *c = nullptr;
-    for (auto &e : caches)
-        if (e.first == ctx) c = &e.second;
-    if (!c) {
-        caches.push_back({ctx, SchedCache{}});
-        c = &caches.back().second;
+    auto it = ctx->tc_sched.find(T);
+    if (it != ctx->tc_sched.end()) return it->second;
+    std::vector<uint32_t> s = band_schedule(T);
+    uint32_t *dev = nullptr;
+    ADAGIO_CUDA(cudaMalloc(&dev, s.size() * sizeof(uint32_t)));
+    cudaError_t e = cudaMemcpy(dev, s.data(), s.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(dev);
+        ADAGIO_CUDA(e);
     }
-    if (c->T != T) {
-        std::vector<uint32_t> s = band_schedule(T);
-        if (s.size() > c->cap) {
-            if (c->dev) cudaFree(c->dev);
-            c->dev = nullptr;
-            ADAGIO_CUDA(cudaMalloc(&c->dev, s.size() * sizeof(uint32_t)));
-            c->cap = s.size();
-        }
-        ADAGIO_CUDA(cudaMemcpy(c->dev, s.data(), s.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
-        c->T = T;
-    }
-    return c->dev;
+    ctx->tc_sched[T] = dev;
+    return dev;
 }
 
-// partial slots of the certificate: one per epilogue warp of every CTA
-int cert_tc_grid(adagio_ctx *ctx) { return ctx->num_sms * kEpiWarps; }
+void tc_prepare(adagio_ctx *ctx, int T) { (void)schedule_for(ctx, T); }
+
+// CTAs of one certificate launch: one per SM (the shared-memory footprint
+// allows one), never more than there are tiles, so that small problems of a
+// batch leave SMs to the others
+int cert_tc_ctas(adagio_ctx *ctx, int64_t n) {
+    const long long T = (n + kTile - 1) / kTile;
+    const long long tiles = T * (T + 1) / 2;
+    return (int)std::min<long long>(ctx->num_sms, tiles);
+}
 
 void tc_tile_coords(int T, long long t, int *I, int *J) {
     const std::vector<uint32_t> s = band_schedule(T);
     const uint32_t v = s.at((size_t)t);
     *I = (int)(v >> 16);
     *J = (int)(v & 0xFFFF);
+}
+
+// raises the kernels' dynamic shared-memory limit (once per device)
+void cert_tc_init() {
+    set_max_dyn_smem((const void *)cert_tc_kernel<true>, (int)kSmemBytes);
+    set_max_dyn_smem((const void *)cert_tc_kernel<false>, (int)kSmemBytes);
 }
 
 bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
@@ -721,15 +721,11 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     a.dump = reinterpret_cast<float4 *>(L.dump);
     a.dump_tiles = L.dump_tiles;
     ADAGIO_CUDA(cudaMemsetAsync(L.partials, 0, sizeof(CertPartial) * L.grid, st));
-    if (L.dump) {
-        ADAGIO_CUDA(cudaFuncSetAttribute(cert_tc_kernel<true>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+    cert_tc_init();
+    if (L.dump)
         cert_tc_kernel<true><<<L.grid / kEpiWarps, kThreads, kSmemBytes, st>>>(mxh, mxl, myh, myl, a);
-    } else {
-        ADAGIO_CUDA(cudaFuncSetAttribute(cert_tc_kernel<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBytes));
+    else
         cert_tc_kernel<false><<<L.grid / kEpiWarps, kThreads, kSmemBytes, st>>>(mxh, mxl, myh, myl, a);
-    }
     ADAGIO_CHECK_LAUNCH();
     return true;
 }

@@ -2,9 +2,7 @@
 // certified search for the smallest target dimension (the question Table 3
 // answers: how many dimensions reach distortion eps).
 //
-// Search: probe r = 16, 32, 64, ... (the last probe is m_cap) until the
-// exhaustive certificate's maximum is <= eps, then bisect between the last
-// failing and the first passing probe with mid = floor((lo + hi) / 2).  Each
+// Search: the state machine of search.cuh (doubling, then bisection).  Each
 // probe builds A_r = [P_s ; S_k (I - P_s^T P_s)] with s = floor(r/2),
 // k = ceil(r/2) (P_s is a prefix of the incrementally computed principal
 // rows; S_k is a prefix of the counter-generated JL rows, rescaled), embeds
@@ -16,6 +14,7 @@
 #include "jl.cuh"
 #include "linalg.cuh"
 #include "pca.cuh"
+#include "search.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -60,6 +59,7 @@ struct Prober {
     PCA *pca;
     float *S, *A, *Abest, *T, *Y;
     CertOptions copt;
+    const PrepMat *px = nullptr;  // X prepared once for every probe's certificate
     int fixed_s;  // >= 0: every probe uses this many principal rows
     struct Rec {
         int r;
@@ -89,7 +89,7 @@ struct Prober {
         CertOptions co = copt;
         co.stop_early = stop_early;
         bool stopped = false;
-        certify(ctx, X, ldx, Y, r, n, d, r, co, &c, st, &stopped);
+        certify(ctx, X, ldx, Y, r, n, d, r, co, &c, st, &stopped, px);
         const bool ok = !stopped && c.max <= copt.eps;
         probes.push_back({r, ok, c.max});
         last_r = r;
@@ -160,6 +160,13 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
         pr.copt.hi = search ? 2.0 * eps : 1.0;
     }
     pr.fixed_s = o->s;
+    PrepMat px;
+    {
+        unsigned *xflags = ws_array<unsigned>(ctx, 1);
+        ADAGIO_CUDA(cudaMemsetAsync(xflags, 0, sizeof(unsigned), st));
+        cert_prepare_x(ctx, X, ldx, n, d, o->precision, px, xflags, st);
+        pr.px = &px;  // X is finite: the PCA's preparation checked it
+    }
 
     int status = ADAGIO_OK;
     int r_final, s_final;
@@ -167,7 +174,7 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
         pr.build(cap, st);
         if (cert) {
             embed_gemm(X, ldx, n, d, pr.A, d, cap, pr.Y, cap, st);
-            certify(ctx, X, ldx, pr.Y, cap, n, d, cap, pr.copt, cert, st);
+            certify(ctx, X, ldx, pr.Y, cap, n, d, cap, pr.copt, cert, st, nullptr, &px);
         }
         ADAGIO_CUDA(cudaMemcpyAsync(A_out, pr.A, sizeof(float) * (size_t)cap * d,
                                     cudaMemcpyDeviceToDevice, st));
@@ -185,33 +192,9 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
             verify_only = true;
             ctx->last_fit.predicted_m = start;
         }
-        int last_fail = 0, first_ok = -1;
-        if (start > 0) {
-            // a predicted dimension is verified first; on failure the search
-            // continues above it
-            if (pr.probe(start, true, st)) first_ok = start; else last_fail = start;
-        }
-        if (first_ok < 0) {
-            std::vector<int> seq;
-            for (int r = 16; r < cap; r *= 2)
-                if (r > last_fail) seq.push_back(r);
-            seq.push_back(cap);
-            for (int r : seq) {
-                if (pr.probe(r, true, st)) {
-                    first_ok = r;
-                    break;
-                }
-                last_fail = r;
-            }
-        }
-        const bool accept_prediction = verify_only && first_ok == start && start > 0;
-        if (first_ok >= 0 && !accept_prediction) {
-            int lo = last_fail, hi = first_ok;
-            while (hi - lo > 1) {
-                const int mid = (lo + hi) / 2;
-                if (pr.probe(mid, true, st)) hi = mid; else lo = mid;
-            }
-        }
+        Search se;
+        se.begin(cap, start, verify_only);
+        for (int r; (r = se.next()) > 0;) se.record(pr.probe(r, true, st));
         if (pr.best_r > 0) {
             r_final = pr.best_r;
             s_final = pr.best_s;
@@ -223,7 +206,7 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
             pr.build(cap, st);
             embed_gemm(X, ldx, n, d, pr.A, d, cap, pr.Y, cap, st);
             adagio_cert c;
-            certify(ctx, X, ldx, pr.Y, cap, n, d, cap, pr.copt, &c, st);
+            certify(ctx, X, ldx, pr.Y, cap, n, d, cap, pr.copt, &c, st, nullptr, &px);
             if (cert) *cert = c;
             ADAGIO_CUDA(cudaMemcpyAsync(A_out, pr.A, sizeof(float) * (size_t)cap * d,
                                         cudaMemcpyDeviceToDevice, st));

@@ -43,6 +43,9 @@ int fit_entry(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
 // Dimension predictor (mlp.cu).
 bool has_predictor(const adagio_ctx *ctx);
 int predict_one(adagio_ctx *ctx, const float *feats, cudaStream_t st);
+// predictions for B feature rows (device, B x 68) into dm (device) and m_host
+// (pinned host); enqueued only, the caller synchronises
+void predict_many(adagio_ctx *ctx, const float *feats, int B, int *dm, int *m_host, cudaStream_t st);
 void spectrum_features(const double *theta, int have, const float *C, int d, int64_t n, double eps,
                        float *feats, cudaStream_t st);
 

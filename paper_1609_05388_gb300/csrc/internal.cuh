@@ -9,6 +9,7 @@
 
 #include <cstdarg>
 #include <cstdio>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -80,6 +81,14 @@ struct adagio_ctx {
     adagio_cert_stats last_stats{-1.0, -1.0, -1.0, 0, 0, 0};
     adagio_fit_stats last_fit{0, 0, 0, 0, 0.0, 0.0, 0};
     int collect_timing = 0;
+    // tile schedules of the tensor-core certificate, by tile-row count T
+    // (built once, resident for the context's lifetime)
+    std::map<int, uint32_t *> tc_sched;
+    // streams and pinned host memory of batched fits (grown on demand)
+    std::vector<cudaStream_t> batch_streams;
+    void *batch_host = nullptr;
+    size_t batch_host_bytes = 0;
+    adagio_batch_stats last_batch{0, 0, 0, 0.0};
 };
 
 namespace adagio {
@@ -98,6 +107,9 @@ struct DeviceGuard {
 
 // Workspace management -------------------------------------------------------
 void ws_reset(adagio_ctx *ctx);
+// raises a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device (a no-op once done), so that launches need no attribute call
+void set_max_dyn_smem(const void *fn, int bytes);
 void ws_reserve(adagio_ctx *ctx, size_t bytes);           // capacity >= bytes
 void *ws_alloc(adagio_ctx *ctx, size_t bytes, size_t align = 256);
 template <typename T>

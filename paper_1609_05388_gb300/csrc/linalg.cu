@@ -378,16 +378,23 @@ void embed_gemm(const float *X, int64_t ldx, int64_t n, int d, const float *A, i
     }
 }
 
+void linalg_init() {
+    const size_t b = kJacobiMax;
+    set_max_dyn_smem((const void *)cholesky_kernel, (int)(b * (b + 1) * sizeof(double)));
+    set_max_dyn_smem((const void *)trsm_rows_kernel, (int)((b * b + b * kTrsmCols) * sizeof(float)));
+    set_max_dyn_smem((const void *)jacobi_kernel, (int)(2 * b * (b + 1) * sizeof(float)));
+}
+
 void cholesky_upper(double *G, int b, double floor_rel, cudaStream_t st) {
     const size_t smem = (size_t)b * (b + 1) * sizeof(double);
-    ADAGIO_CUDA(cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    set_max_dyn_smem((const void *)cholesky_kernel, (int)smem);
     cholesky_kernel<<<1, 1024, smem, st>>>(G, b, floor_rel);
     ADAGIO_CHECK_LAUNCH();
 }
 
 void trsm_rows(const double *R, int b, float *V, int64_t ldv, int d, cudaStream_t st) {
     const size_t smem = ((size_t)b * b + (size_t)b * kTrsmCols) * sizeof(float);
-    ADAGIO_CUDA(cudaFuncSetAttribute(trsm_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    set_max_dyn_smem((const void *)trsm_rows_kernel, (int)smem);
     trsm_rows_kernel<<<(unsigned)ceil_div(d, kTrsmCols), kTrsmCols, smem, st>>>(R, b, V, ldv, d);
     ADAGIO_CHECK_LAUNCH();
 }
@@ -395,7 +402,7 @@ void trsm_rows(const double *R, int b, float *V, int64_t ldv, int d, cudaStream_
 void jacobi_eig(const double *H, int b, double *theta, float *U, int max_sweeps, cudaStream_t st) {
     if (b > kJacobiMax) fail(ADAGIO_E_INVALID_ARG, "internal: Jacobi block %d > %d", b, kJacobiMax);
     const size_t smem = (size_t)2 * b * (b + 1) * sizeof(float);
-    ADAGIO_CUDA(cudaFuncSetAttribute(jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    set_max_dyn_smem((const void *)jacobi_kernel, (int)smem);
     jacobi_kernel<<<1, kJacobiThreads, smem, st>>>(H, b, theta, U, max_sweeps);
     ADAGIO_CHECK_LAUNCH();
 }

@@ -310,6 +310,18 @@ int predict_one(adagio_ctx *ctx, const float *feats, cudaStream_t st) {
     return m;
 }
 
+void predict_many(adagio_ctx *ctx, const float *feats, int B, int *dm, int *m_host, cudaStream_t st) {
+    Predictor *p = predictor(ctx, false);
+    ensure_batch(p, B);
+    Batch bt = carve(p);
+    forward(p, feats, B, bt, st);
+    output_kernel<<<1, 256, 0, st>>>(bt.y, p->master + kOffB3, nullptr, B, nullptr, nullptr);
+    ADAGIO_CHECK_LAUNCH();
+    predict_kernel<<<(unsigned)ceil_div(B, 256), 256, 0, st>>>(bt.y, B, dm);
+    ADAGIO_CHECK_LAUNCH();
+    ADAGIO_CUDA(cudaMemcpyAsync(m_host, dm, B * sizeof(int), cudaMemcpyDeviceToHost, st));
+}
+
 void spectrum_features(const double *theta, int have, const float *C, int d, int64_t n, double eps,
                        float *feats, cudaStream_t st) {
     features_kernel<<<1, 128, 0, st>>>(theta, have, C, d, n, (float)eps, feats);

@@ -43,8 +43,13 @@ size_t pca_bytes(int64_t n, int d, int s_cap, int oversample) {
     return bytes + 8192;
 }
 
-void PCA::init(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int64_t ldx, int s_cap_,
-               uint64_t seed_, int max_iter_, double tol_, int oversample_, cudaStream_t st) {
+size_t pca_host_bytes() { return (size_t)kJacobiMax * 12 + 128; }
+
+void *PCA::stage(size_t bytes) { return hbuf ? hbuf : host_stage(ctx, bytes); }
+
+void PCA::init_enqueue(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int64_t ldx,
+                       int s_cap_, uint64_t seed_, int max_iter_, double tol_, int oversample_,
+                       cudaStream_t st) {
     ctx = ctx_;
     n = n_;
     d = d_;
@@ -56,6 +61,7 @@ void PCA::init(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int64_t ldx
     s_done = 0;
     iterations = 0;
     theta1 = 0.0;
+    blk = Block{};
     flags = ws_array<unsigned>(ctx, 1);
     ADAGIO_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
     // centred FP32 copy (K0) and the covariance C = Xc^T Xc
@@ -77,10 +83,20 @@ void PCA::init(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int64_t ldx
     theta = ws_array<double>(ctx, std::max(s_cap, 1));
     res = ws_array<float>(ctx, bmax);
     f64part = ws_array<double>(ctx, (size_t)ceil_div(d, kF64Chunk) * bmax * bmax);
-    unsigned hflag = 0;
-    ADAGIO_CUDA(cudaMemcpyAsync(&hflag, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
-    ADAGIO_CUDA(cudaStreamSynchronize(st));
+    unsigned *hflag = reinterpret_cast<unsigned *>(stage(pca_host_bytes()));
+    ADAGIO_CUDA(cudaMemcpyAsync(hflag, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+}
+
+void PCA::init_check() {
+    const unsigned hflag = *reinterpret_cast<unsigned *>(stage(pca_host_bytes()));
     if (hflag & 1u) fail(ADAGIO_E_NONFINITE, "input holds NaN or Inf");
+}
+
+void PCA::init(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int64_t ldx, int s_cap_,
+               uint64_t seed_, int max_iter_, double tol_, int oversample_, cudaStream_t st) {
+    init_enqueue(ctx_, X, n_, d_, ldx, s_cap_, seed_, max_iter_, tol_, oversample_, st);
+    ADAGIO_CUDA(cudaStreamSynchronize(st));
+    init_check();
 }
 
 // rows of M (r x d) <- M - (M P^T) P over the s_done finished directions
@@ -101,8 +117,92 @@ void PCA::orth(float *M, int b, cudaStream_t st) {
     }
 }
 
+// Rayleigh-Ritz (and the convergence test) on the first iteration, every
+// kRREvery-th and the last; CholeskyQR2 keeps V orthonormal in between
+constexpr int kRREvery = 4;
+
+void PCA::begin_block(int s_needed, cudaStream_t st) {
+    (void)s_needed;
+    blk.remaining = d - s_done;
+    blk.s_blk = std::min({s_cap - s_done, kJacobiMax - p, blk.remaining});
+    blk.b = std::min(blk.s_blk + p, blk.remaining);
+    blk.it = 0;
+    blk.last = false;
+    blk.active = true;
+    rademacher_block(seed + (uint64_t)s_done * 0x9E3779B9ull, blk.b, d, V, d, st);
+    deflate(V, blk.b, st);
+    orth(V, blk.b, st);
+}
+
+void PCA::advance(int s_needed, cudaStream_t st) {
+    if (!blk.active) begin_block(s_needed, st);
+    const int b = blk.b, s_blk = blk.s_blk;
+    for (;;) {
+        ++iterations;
+        // W = V C (C symmetric)
+        gemm<float, float, float, float>(b, d, d, 1.0f, MatView<float>{V, d, 1},
+                                         MatView<float>{C, d, 1}, 0.0f, W, d, st);
+        deflate(W, b, st);
+        const int it = blk.it;
+        blk.last = it == max_iter - 1 || b == blk.remaining;
+        if ((it % kRREvery) == kRREvery - 1 || blk.last || it == 0) {
+            // Rayleigh-Ritz: H = V W^T, H = U diag(theta) U^T
+            gemm_f64_splitk(b, b, d, MatView<float>{V, d, 1}, MatView<float>{W, 1, d}, H, f64part,
+                            kF64Chunk, st);
+            jacobi_eig(H, b, theta_blk, U, 30, st);
+            // V <- U^T V, W <- U^T W
+            gemm<float, float, float, float>(b, d, b, 1.0f, MatView<float>{U, 1, b},
+                                             MatView<float>{V, d, 1}, 0.0f, T, d, st);
+            std::swap(V, T);
+            gemm<float, float, float, float>(b, d, b, 1.0f, MatView<float>{U, 1, b},
+                                             MatView<float>{W, d, 1}, 0.0f, T, d, st);
+            std::swap(W, T);
+            ritz_residuals(W, V, d, d, theta_blk, s_blk, res, st);
+            char *hs = reinterpret_cast<char *>(stage(pca_host_bytes()));
+            ADAGIO_CUDA(cudaMemcpyAsync(hs, theta_blk, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
+            ADAGIO_CUDA(cudaMemcpyAsync(hs + (size_t)kJacobiMax * 8, res, sizeof(float) * s_blk,
+                                        cudaMemcpyDeviceToHost, st));
+            return;
+        }
+        // next iterate: V <- orth(W)
+        std::swap(V, W);
+        orth(V, b, st);
+        ++blk.it;
+    }
+}
+
+void PCA::resolve(cudaStream_t st) {
+    const char *hs = reinterpret_cast<const char *>(stage(pca_host_bytes()));
+    const double *hth = reinterpret_cast<const double *>(hs);
+    const float *hres = reinterpret_cast<const float *>(hs + (size_t)kJacobiMax * 8);
+    if (s_done == 0) theta1 = std::max(hth[0], 0.0);
+    float worst = 0.0f;
+    for (int i = 0; i < blk.s_blk; ++i) worst = std::max(worst, hres[i]);
+    if (!(worst > tol * theta1) || blk.last) {
+        accept_block(st);
+        return;
+    }
+    std::swap(V, W);
+    orth(V, blk.b, st);
+    ++blk.it;
+}
+
+// accept the first s_blk Ritz vectors; re-orthonormalise against the earlier
+// blocks and among themselves
+void PCA::accept_block(cudaStream_t st) {
+    const int s_blk = blk.s_blk;
+    float *dst = P + (size_t)s_done * d;
+    copy_rows(V, d, dst, d, s_blk, d, st);
+    deflate(dst, s_blk, st);
+    orth(dst, s_blk, st);
+    canonical_signs(dst, s_blk, d, d, st);
+    ADAGIO_CUDA(cudaMemcpyAsync(theta + s_done, theta_blk, sizeof(double) * s_blk,
+                                cudaMemcpyDeviceToDevice, st));
+    s_done += s_blk;
+    blk.active = false;
+}
+
 void PCA::extend(int s_needed, cudaStream_t st) {
-    s_needed = std::min(s_needed, s_cap);
     const auto t0 = std::chrono::steady_clock::now();
     struct Timer {
         double *acc;
@@ -111,63 +211,10 @@ void PCA::extend(int s_needed, cudaStream_t st) {
             if (acc) *acc += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
         }
     } timer{elapsed_ms, t0};
-    while (s_done < s_needed) {
-        const int remaining = d - s_done;
-        const int s_blk = std::min({s_cap - s_done, kJacobiMax - p, remaining});
-        const int b = std::min(s_blk + p, remaining);
-        rademacher_block(seed + (uint64_t)s_done * 0x9E3779B9ull, b, d, V, d, st);
-        deflate(V, b, st);
-        orth(V, b, st);
-        float *hres = nullptr;
-        double *hth = nullptr;
-        // Rayleigh-Ritz (and the convergence test) every kRREvery iterations and
-        // on the last one; CholeskyQR2 keeps V orthonormal in between
-        constexpr int kRREvery = 4;
-        for (int it = 0; it < max_iter; ++it) {
-            ++iterations;
-            // W = V C (C symmetric)
-            gemm<float, float, float, float>(b, d, d, 1.0f, MatView<float>{V, d, 1},
-                                             MatView<float>{C, d, 1}, 0.0f, W, d, st);
-            deflate(W, b, st);
-            const bool last = it == max_iter - 1 || b == remaining;
-            if ((it % kRREvery) == kRREvery - 1 || last || it == 0) {
-                // Rayleigh-Ritz: H = V W^T, H = U diag(theta) U^T
-                gemm_f64_splitk(b, b, d, MatView<float>{V, d, 1}, MatView<float>{W, 1, d}, H, f64part,
-                                kF64Chunk, st);
-                jacobi_eig(H, b, theta_blk, U, 30, st);
-                // V <- U^T V, W <- U^T W
-                gemm<float, float, float, float>(b, d, b, 1.0f, MatView<float>{U, 1, b},
-                                                 MatView<float>{V, d, 1}, 0.0f, T, d, st);
-                std::swap(V, T);
-                gemm<float, float, float, float>(b, d, b, 1.0f, MatView<float>{U, 1, b},
-                                                 MatView<float>{W, d, 1}, 0.0f, T, d, st);
-                std::swap(W, T);
-                ritz_residuals(W, V, d, d, theta_blk, s_blk, res, st);
-                char *hs = reinterpret_cast<char *>(host_stage(ctx, (size_t)b * 8 + (size_t)b * 4 + 64));
-                hth = reinterpret_cast<double *>(hs);
-                hres = reinterpret_cast<float *>(hs + (size_t)b * 8);
-                ADAGIO_CUDA(cudaMemcpyAsync(hth, theta_blk, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
-                ADAGIO_CUDA(cudaMemcpyAsync(hres, res, sizeof(float) * s_blk, cudaMemcpyDeviceToHost, st));
-                ADAGIO_CUDA(cudaStreamSynchronize(st));
-                if (s_done == 0) theta1 = std::max(hth[0], 0.0);
-                float worst = 0.0f;
-                for (int i = 0; i < s_blk; ++i) worst = std::max(worst, hres[i]);
-                if (!(worst > tol * theta1) || last) break;
-            }
-            // next iterate: V <- orth(W)
-            std::swap(V, W);
-            orth(V, b, st);
-        }
-        // accept the first s_blk Ritz vectors; re-orthonormalise against the
-        // earlier blocks and among themselves
-        float *dst = P + (size_t)s_done * d;
-        copy_rows(V, d, dst, d, s_blk, d, st);
-        deflate(dst, s_blk, st);
-        orth(dst, s_blk, st);
-        canonical_signs(dst, s_blk, d, d, st);
-        ADAGIO_CUDA(cudaMemcpyAsync(theta + s_done, theta_blk, sizeof(double) * s_blk,
-                                    cudaMemcpyDeviceToDevice, st));
-        s_done += s_blk;
+    while (needs(s_needed)) {
+        advance(s_needed, st);
+        ADAGIO_CUDA(cudaStreamSynchronize(st));
+        resolve(st);
     }
 }
 

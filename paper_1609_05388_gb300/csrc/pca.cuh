@@ -2,6 +2,8 @@
 
 #include "internal.cuh"
 
+#include <algorithm>
+
 namespace adagio {
 
 // Incremental randomized PCA of one data set (see pca.cu).  All buffers come
@@ -20,17 +22,42 @@ struct PCA {
     double *G = nullptr, *H = nullptr, *theta_blk = nullptr, *f64part = nullptr;
     unsigned *flags = nullptr;
     double *elapsed_ms = nullptr;  // optional: extend() adds its wall time here
+    // pinned host buffer of at least pca_host_bytes() for the convergence
+    // checks; null: the context's staging buffer at each use
+    void *hbuf = nullptr;
 
     void init(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx, int s_cap,
               uint64_t seed, int max_iter, double tol, int oversample, cudaStream_t st);
     // make sure the first s_needed rows of P are computed (synchronises)
     void extend(int s_needed, cudaStream_t st);
 
+    // The same computation as a resumable sequence, for lock-step batches:
+    //   init_enqueue ; sync ; init_check
+    //   while (needs(s)) { advance(s) ; sync ; resolve() }
+    // advance enqueues work up to the next convergence test (with its copy to
+    // the host); resolve reads it after the caller synchronised the stream and
+    // enqueues the next iteration or the acceptance of the block.
+    void init_enqueue(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx, int s_cap,
+                      uint64_t seed, int max_iter, double tol, int oversample, cudaStream_t st);
+    void init_check();
+    bool needs(int s_needed) const { return s_done < std::min(s_needed, s_cap); }
+    void advance(int s_needed, cudaStream_t st);
+    void resolve(cudaStream_t st);
+
    private:
+    struct Block {
+        bool active = false;
+        int it = 0, s_blk = 0, b = 0, remaining = 0;
+        bool last = false;
+    } blk;
+    void *stage(size_t bytes);
+    void begin_block(int s_needed, cudaStream_t st);
+    void accept_block(cudaStream_t st);
     void deflate(float *M, int r, cudaStream_t st);
     void orth(float *M, int b, cudaStream_t st);
 };
 
 size_t pca_bytes(int64_t n, int d, int s_cap, int oversample);
+size_t pca_host_bytes();
 
 }  // namespace adagio

@@ -159,19 +159,22 @@ __global__ void finalize_kernel(const CertPartial *__restrict__ fast, int nfast,
         out->flags = *flags;
         out->status = status ? *status : 0;
         out->stopped = stop_flag ? *stop_flag : 0;
-        (void)qcount;
+        out->qlen = *qcount;
     }
 }
 
 }  // namespace
+
+void recompute_init() {
+    set_max_dyn_smem((const void *)recompute_kernel, (int)((size_t)kBins * RT * sizeof(unsigned)));
+}
 
 void launch_recompute(const float *X, int64_t ldx, int d, const float *Y, int64_t ldy, int m,
                       const int2 *queue, const unsigned long long *qcount,
                       unsigned long long qcap, CertConst cc, CertPartial *partials, int grid,
                       cudaStream_t st) {
     const size_t smem = (size_t)kBins * RT * sizeof(unsigned);
-    ADAGIO_CUDA(cudaFuncSetAttribute(recompute_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
+    set_max_dyn_smem((const void *)recompute_kernel, (int)smem);
     recompute_kernel<<<grid, RT, smem, st>>>(X, ldx, d, Y, ldy, m, queue, qcount, qcap, cc,
                                             partials);
     ADAGIO_CHECK_LAUNCH();

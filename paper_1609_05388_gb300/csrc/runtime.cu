@@ -3,6 +3,8 @@
 
 #include <atomic>
 #include <cstring>
+#include <map>
+#include <mutex>
 
 namespace adagio {
 
@@ -19,6 +21,18 @@ void fail(int code, const char *fmt, ...) {
 }
 
 void ws_reset(adagio_ctx *ctx) { ctx->ws.off = 0; }
+
+void set_max_dyn_smem(const void *fn, int bytes) {
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> done;
+    int dev = 0;
+    ADAGIO_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(mu);
+    int &have = done[{fn, dev}];
+    if (have >= bytes) return;
+    ADAGIO_CUDA(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    have = bytes;
+}
 
 void ws_reserve(adagio_ctx *ctx, size_t bytes) {
     Workspace &w = ctx->ws;
@@ -161,6 +175,9 @@ int adagio_ctx_destroy(adagio_ctx *ctx) {
         if (ctx->ws.base) cudaFree(ctx->ws.base);
         if (ctx->qbuf && !ctx->qbuf_fixed) cudaFree(ctx->qbuf);
         if (ctx->host_stage) cudaFreeHost(ctx->host_stage);
+        for (auto &e : ctx->tc_sched) cudaFree(e.second);
+        for (cudaStream_t s : ctx->batch_streams) cudaStreamDestroy(s);
+        if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
         if (prev >= 0) cudaSetDevice(prev);
     }
     delete ctx;
@@ -183,6 +200,12 @@ int adagio_set_timing(adagio_ctx *ctx, int enable) {
 int adagio_last_cert_stats(const adagio_ctx *ctx, adagio_cert_stats *out) {
     if (!ctx || !out) return ADAGIO_E_INVALID_ARG;
     *out = ctx->last_stats;
+    return ADAGIO_OK;
+}
+
+int adagio_last_batch_stats(const adagio_ctx *ctx, adagio_batch_stats *out) {
+    if (!ctx || !out) return ADAGIO_E_INVALID_ARG;
+    *out = ctx->last_batch;
     return ADAGIO_OK;
 }
 
