@@ -2,11 +2,13 @@
 
 A step is one pass of the whole hot path over the 60 000 x 784 MNIST-shaped
 input (eps = 0.1): centring, covariance and randomized PCA, JL matrix,
-assembly, embedding and the certified dimension search, whose probes each
-run the exhaustive all-pairs certificate.  value = n(n-1)/2 / (step time):
-pairs of the returned embedding certified per second of time-to-certified-
-embedding, inputs resident in HBM.  The plain FP32 GPU path (SIMT Gram tiles,
-plain search) is timed on the same input for comparison.
+assembly, embedding, the learned dimension guess and its verification by the
+exhaustive all-pairs certificate (the certified search continues from the
+guess when it fails).  value = n(n-1)/2 / (step time): pairs of the returned
+embedding certified per second of time-to-certified-embedding, inputs
+resident in HBM.  Timed on the same input for comparison: the same split
+precision with the plain search (no predictor), and the plain FP32 GPU path
+(SIMT Gram tiles, plain search).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl adagio|reference]
 
@@ -46,7 +48,12 @@ def parse():
     p.add_argument("--precision", default="auto")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-predictor", action="store_true",
+                   help="time the plain search as the headline step")
     return p.parse_args()
+
+
+PREDICTOR = os.path.join(ROOT, "paper_1609_05388_gb300", "predictor_mnist_like.bin")
 
 
 def dist_setup(n_gpus):
@@ -232,8 +239,13 @@ def main():
     ctx = lib.Context(local)
     st = torch.cuda.current_stream()
 
-    def step(precision, Xin=X):
-        return ctx.fit(Xin, eps=EPS, m_cap=d, seed=11, precision=precision)
+    learned = 0 if args.no_predictor else 1
+    if learned:
+        ctx.mlp_load(PREDICTOR)
+
+    def step(precision, use_predictor=learned, Xin=X):
+        return ctx.fit(Xin, eps=EPS, m_cap=d, seed=11, precision=precision,
+                       use_predictor=use_predictor)
 
     for _ in range(args.warmup):
         step(prec)
@@ -257,19 +269,28 @@ def main():
     fit_stats = ctx.last_fit_stats()
     value = sum_over_ranks(pg, pairs / (ms / 1e3))
 
-    # plain FP32 GPU path (SIMT tiles, plain search) on the same input
-    plain = None
-    if not args.no_plain and prec != lib.PREC_FP32:
-        step(lib.PREC_FP32)
+    def timed(precision, use_predictor):
+        step(precision, use_predictor)
         torch.cuda.synchronize()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record(st)
-        pr = step(lib.PREC_FP32)
+        pr = step(precision, use_predictor)
         f1.record(st)
         torch.cuda.synchronize()
         pms = f0.elapsed_time(f1)
-        plain = {"value": pairs / (pms / 1e3), "unit": "pairs/s", "ms_per_step": pms, "m": pr[1],
-                 "max": pr[3].max, "max_err_bound": pr[3].max_err_bound}
+        fs = ctx.last_fit_stats()
+        return {"value": pairs / (pms / 1e3), "unit": "pairs/s", "ms_per_step": pms, "m": pr[1],
+                "max": pr[3].max, "max_err_bound": pr[3].max_err_bound,
+                "probes": fs["probes"], "full_certs": fs["full_certs"]}
+
+    # the same precision with the plain search, and the plain FP32 GPU path
+    # (SIMT tiles, plain search), on the same input
+    plain_search = plain = None
+    if not args.no_plain:
+        if learned:
+            plain_search = timed(prec, 0)
+        if prec != lib.PREC_FP32:
+            plain = timed(lib.PREC_FP32, 0)
 
     # roofline of the dominant kernel (the all-pairs tile kernel) at the returned m
     Y = ctx.embed(A, X)
@@ -302,7 +323,7 @@ def main():
     ke = max(1, min(args.steps, 2))
     for _ in range(ke):
         Ah, mh, sh, ch, rch = ctx.fit(X_host, eps=EPS, m_cap=d, seed=11, precision=prec,
-                                      A=np.empty((d, d), np.float32))
+                                      use_predictor=learned, A=np.empty((d, d), np.float32))
     e2e_s = (time.perf_counter() - t0) / ke
     e2e = {"value": sum_over_ranks(pg, pairs / e2e_s), "unit": "pairs/s",
            "h2d_bytes_per_step": int(X_host.nbytes), "d2h_bytes_per_step": int(mh * d * 4 + 712),
@@ -322,13 +343,18 @@ def main():
             "config": {"workload": WORKLOAD, "n": n, "d": d, "eps": EPS, "pairs": pairs,
                        "parallelism": "replicas" if world > 1 else "single-gpu",
                        "l2": "inputs larger than L2 (X 188 MB fp32; split planes 200 MB)",
-                       "search": "gallop 16,32,64,... then bisect; failing probes stop early"},
+                       "search": ("learned guess verified by the exhaustive certificate, then "
+                                  "doubling and bisection from it on failure" if learned else
+                                  "doubling 16,32,64,... then bisection") +
+                                 "; failing probes stop at the first certain violation",
+                       "predictor": os.path.basename(PREDICTOR) if learned else None},
             "time_to_certified_embedding_s": ms / 1e3,
             "result": {"m": m, "s": s, "max": cert.max, "mean": cert.mean,
                        "violations": cert.violations, "recomputed": cert.recomputed,
                        "max_err_bound": cert.max_err_bound},
             "fit_stats": fit_stats,
             "certificate_only": {"value": pairs / (tile_ms / 1e3), "unit": "pairs/s (tile kernel)"},
+            "plain_search": plain_search,
             "plain_fp32": plain,
             "roofline": roof,
             "gpu_launches": launches,

@@ -261,6 +261,9 @@ typedef struct {
     int probes;         /* out: certificates the search ran */
     int full_certs;     /* out: of those, the ones that ran to completion */
     adagio_cert cert;   /* out: certificate of the returned map */
+    float *feats;       /* device, 68 floats, or NULL: out: the predictor's
+                           features of X (see adagio_features), taken from
+                           this fit's own PCA */
 } adagio_instance;
 
 /* Capture each lock-step round as one CUDA graph (instantiated and launched

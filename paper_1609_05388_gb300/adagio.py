@@ -77,7 +77,7 @@ class InstanceStruct(ctypes.Structure):
                 ("ldx", ctypes.c_int64), ("eps", ctypes.c_double), ("m", ctypes.c_int),
                 ("m_cap", ctypes.c_int), ("A", ctypes.c_void_p), ("m_out", ctypes.c_int),
                 ("s_out", ctypes.c_int), ("status", ctypes.c_int), ("probes", ctypes.c_int),
-                ("full_certs", ctypes.c_int), ("cert", CertStruct)]
+                ("full_certs", ctypes.c_int), ("cert", CertStruct), ("feats", ctypes.c_void_p)]
 
 
 class BatchStatsStruct(ctypes.Structure):
@@ -469,11 +469,12 @@ class Context:
         return A[: mo.value], mo.value, so.value, Certificate.from_struct(c), rc
 
     def fit_batched(self, Xs, eps, m_cap=None, m=None, graph: bool = False,
-                    opts: FitOptsStruct | None = None, **kw):
+                    features: bool = False, opts: FitOptsStruct | None = None, **kw):
         """Fits a list of CUDA float32 tensors (n_i x d_i) in one batched call.
 
         eps: one value or one per instance (<= 0: fixed m[i]).  Returns a list of
-        dicts (A, m, s, status, probes, full_certs, cert), A on the device.
+        dicts (A, m, s, status, probes, full_certs, cert, and with features=True
+        the predictor's 68 features as a numpy array), A on the device.
         """
         import torch
         count = len(Xs)
@@ -496,6 +497,10 @@ class Context:
             e.m = int(ms[i] or 0)
             e.m_cap = int(cap)
             e.A = A.data_ptr()
+            if features:
+                F = torch.zeros(68, dtype=torch.float32, device=X.device)
+                keep[-1] = (X, A, F)
+                e.feats = F.data_ptr()
         stream = torch.cuda.current_stream().cuda_stream
         self._check(LIB.adagio_fit_batched(self.h, count, arr, ctypes.byref(o),
                                            BATCH_GRAPH if graph else 0, stream))
@@ -505,6 +510,8 @@ class Context:
             out.append({"A": keep[i][1][: e.m_out], "m": e.m_out, "s": e.s_out,
                         "status": e.status, "probes": e.probes, "full_certs": e.full_certs,
                         "cert": Certificate.from_struct(e.cert)})
+            if features:
+                out[-1]["feats"] = keep[i][2].cpu().numpy()
         return out
 
     def last_batch_stats(self) -> dict:

@@ -55,6 +55,7 @@ struct Inst {
     Wait wait = Wait::None;
     bool predicting = false;         // PCA up to the predictor's 64 directions
     bool final_probe = false;        // the full certificate at the cap
+    bool feats_pending = false;      // search over; PCA up to 64 directions for the features
     int r = 0;
     int retried_r = 0;
     bool done = false;
@@ -125,11 +126,12 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
             I.cap = std::min(p.m_cap, d);
             I.s_cap = o.s >= 0 ? std::min(o.s, I.cap) : I.cap / 2;
             I.k_cap = o.s >= 0 ? I.cap : I.cap - I.cap / 2;
-            if (o.use_predictor) I.s_cap = std::max(I.s_cap, std::min(64, d));
+            if (o.use_predictor || p.feats) I.s_cap = std::max(I.s_cap, std::min(64, d));
         } else {
             I.cap = p.m;
             I.s_cap = o.s >= 0 ? o.s : p.m / 2;
             I.k_cap = p.m - I.s_cap;
+            if (p.feats) I.s_cap = std::max(I.s_cap, std::min(64, d));
         }
         ws_fixed += pca_bytes(p.n, d, I.s_cap, o.oversample);
         ws_fixed += align_up((size_t)std::max(I.k_cap, 1) * d * sizeof(float), 256);
@@ -312,6 +314,16 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
         I.wait = Wait::Cert;
     };
 
+    // the predictor's features of a finished instance, then it is done
+    auto emit_feats = [&](Inst &I) {
+        const adagio_instance &p = *I.pub;
+        if (p.feats)
+            spectrum_features(I.pca.theta, I.pca.s_done, I.pca.C, p.d, p.n, I.search ? p.eps : 0.0,
+                              p.feats, I.st);
+        I.feats_pending = false;
+        I.done = true;
+    };
+
     auto finish = [&](Inst &I, int r, int s, const adagio_cert &c, const float *Asrc, int status) {
         adagio_instance &p = *I.pub;
         ADAGIO_CUDA(cudaMemcpyAsync(p.A, Asrc, sizeof(float) * (size_t)r * p.d, cudaMemcpyDeviceToDevice,
@@ -322,7 +334,8 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
         p.status = status;
         p.probes = I.probes;
         p.full_certs = I.full;
-        I.done = true;
+        if (p.feats && I.pca.needs(std::min(64, p.d))) I.feats_pending = true;
+        else emit_feats(I);
     };
 
     for (;;) {
@@ -360,6 +373,12 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
         run_round([&]() {
             for (Inst &I : in) {
                 if (I.done) continue;
+                if (I.feats_pending) {
+                    I.pca.advance(std::min(64, I.pub->d), I.st);
+                    I.wait = Wait::Pca;
+                    any_pca = true;
+                    continue;
+                }
                 if (I.predicting) {
                     const int s_need = std::min(64, I.pub->d);
                     if (I.pca.needs(s_need)) {
@@ -388,6 +407,7 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
             I.wait = Wait::None;
             if (w == Wait::Pca) {
                 I.pca.resolve(I.st);
+                if (I.feats_pending && !I.pca.needs(std::min(64, I.pub->d))) emit_feats(I);
                 continue;
             }
             if (w != Wait::Cert) continue;

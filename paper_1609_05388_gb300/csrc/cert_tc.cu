@@ -22,7 +22,8 @@
 //               bounds the full-size roundings to 4 per chunk
 //   warps 2..9  epilogue: two warps per TMEM lane quarter, 64 columns each;
 //               they drain every slot into register running sums (round to
-//               nearest) and classify their 64 pairs at the end of a tile
+//               nearest) and classify their 64 pairs at the end of a tile,
+//               without data-dependent branches
 // The producer decides the tile sequence and sends it down the pipeline (a
 // tile index per first stage, -1 to stop, forwarded through a slot), so early
 // exit needs no CTA-wide barrier, and the epilogue warps never wait on one
@@ -52,6 +53,8 @@ constexpr uint32_t kPlaneBytes = kTile * kKStep * 2;        // 16 KB
 constexpr uint32_t kStageBytes = 4 * kPlaneBytes;           // 64 KB
 constexpr uint32_t kTmemCols = kSlots * kTile;              // 512
 constexpr int kHistFlushTiles = 1000;                       // u16 counters: <= 64 per tile
+// per-thread histogram: two 16-bit bin counters per 32-bit word
+constexpr int kHistWords = kBins / 2;
 constexpr long long kSpinLimit = 4000000000ll;              // clock64 cycles (~2 s)
 
 struct TcArgs {
@@ -74,8 +77,8 @@ struct TcArgs {
 
 struct SmemLayout {
     static constexpr uint32_t stages = 0;
-    static constexpr uint32_t hist = kStages * kStageBytes;                  // u16 [64][256]
-    static constexpr uint32_t bars = hist + kBins * 32 * kEpiWarps * 2;
+    static constexpr uint32_t hist = kStages * kStageBytes;                  // u32 [32][256]
+    static constexpr uint32_t bars = hist + kHistWords * 32 * kEpiWarps * 4;
     static constexpr uint32_t cmd = bars + 256;                               // int [16]
     static constexpr uint32_t tmem_ptr = cmd + 64;
     static constexpr uint32_t total = tmem_ptr + 16;
@@ -189,49 +192,75 @@ __device__ __forceinline__ void tmem_wait_ld() {
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Folds this warp's 32 per-thread u16 counters of every bin into its partial.
-__device__ __forceinline__ void fold_hist(uint16_t *s_hist, int ew, CertPartial *dst) {
+// Folds this warp's 32 per-thread counters of every bin into its partial
+// (the bins and their total, part of `pairs`).
+__device__ __forceinline__ void fold_hist(uint32_t *s_hist, int ew, CertPartial *dst) {
     const int lane = threadIdx.x & 31;
-    for (int b = 0; b < kBins; ++b) {
-        uint16_t *c = s_hist + b * (32 * kEpiWarps) + ew * 32 + lane;
-        unsigned v = *c;
+    unsigned long long pairs = 0;
+    for (int w = 0; w < kHistWords; ++w) {
+        uint32_t *c = s_hist + w * (32 * kEpiWarps) + ew * 32 + lane;
+        const uint32_t v = *c;
         *c = 0;
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        if (lane == 0) dst->hist[b] += v;
+        unsigned a = v & 0xFFFFu, b = v >> 16;
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            b += __shfl_xor_sync(0xffffffffu, b, o);
+        }
+        if (lane == 0) {
+            dst->hist[2 * w] += a;
+            dst->hist[2 * w + 1] += b;
+            pairs += a + b;
+        }
     }
+    if (lane == 0) dst->pairs += pairs;
     __syncwarp();
 }
 
-// Fast classification of one pair from its Gram entries (Eq. 2), two MUFU
-// operations per pair.  With p = dx2 dy2 and s = sqrt(p):
+// Fast classification of one pair from its Gram entries (Eq. 2), branch-free
+// (every pair of the unrolled tile row takes the same instruction path, so
+// the compiler interleaves independent pairs), two MUFU operations per pair.
+// With p = dx2 dy2 and s = sqrt(p):
 //   rho = sqrt(dy2 / dx2) = dy2 / s,   delta = |rho - 1| = |dy2 - dx2| / (dx2 + s)
 // (the second form has no cancellation).  The Gram error bounds are
 // ex = q4x_i q4x_j + cx (n2x_i + n2x_j), likewise ey, and the distortion error
 // is at most B = 0.55 rho (ex / dx2 + ey / dy2) + 1e-6 delta + 1e-9 (the last
 // terms cover the approximate reciprocal square root and reciprocal).
-// Returns 0 = fast result valid, 1 = needs the exact recompute.
-__device__ __forceinline__ int fast_pair(float gx, float gy, const float4 &ri, const float4 &rj,
-                                         float cx, float cy, const CertConst &cc, float &delta,
-                                         float &bound) {
+// queue = the fast result cannot be used: the Gram values are too
+// ill-conditioned to bound (or not finite), B exceeds the maximum's
+// tolerance, or B > 1e-6 and a histogram edge or eps lies within B of delta.
+struct PairOut {
+    float delta, bound, t;
+    bool queue;
+};
+
+struct EpiConst {
+    float m2sx, m2sy;      // -2 / scale^2 of the split planes
+    float cx, cy;
+    float inv_w, t0;       // t = delta * inv_w + t0 = (delta - lo) / w
+    float tmin;            // lowest real histogram edge index (1 when lo <= 0)
+    float eps;
+};
+
+__device__ __forceinline__ PairOut fast_pair(float gx, float gy, const float4 &ri, const float4 &rj,
+                                             const EpiConst &k) {
+    PairOut o;
     const float sx = ri.x + rj.x, sy = ri.y + rj.y;
-    const float dx2 = fmaf(-2.0f, gx, sx), dy2 = fmaf(-2.0f, gy, sy);
-    const float ex = fmaf(ri.z, rj.z, cx * sx), ey = fmaf(ri.w, rj.w, cy * sy);
-    if (!(dx2 > 8.0f * ex) || !(dy2 > 8.0f * ey)) return 1;
+    const float dx2 = fmaf(k.m2sx, gx, sx), dy2 = fmaf(k.m2sy, gy, sy);
+    const float ex = fmaf(ri.z, rj.z, k.cx * sx), ey = fmaf(ri.w, rj.w, k.cy * sy);
+    const bool cond = (dx2 > 8.0f * ex) & (dy2 > 8.0f * ey);
     const float pp = dx2 * dy2;
     const float rs = rsqrtf(pp);
     const float sq = pp * rs;                       // sqrt(dx2 dy2)
-    delta = __fdividef(fabsf(dy2 - dx2), dx2 + sq);
+    o.delta = __fdividef(fabsf(dy2 - dx2), dx2 + sq);
     const float rho = dy2 * rs;
     const float inv_p = rs * rs;                    // 1 / (dx2 dy2)
-    bound = fmaf(0.55f * rho * inv_p, fmaf(ex, dy2, ey * dx2), fmaf(1e-6f, delta, 1e-9f));
-    if (bound > kMaxTol) return 1;
-    if (bound > kExempt) {
-        const float t = (delta - cc.lo) * cc.inv_w;
-        const float tn = rintf(t);
-        const bool edge_real = !(cc.lo_is_floor && tn <= 0.0f) && tn <= (float)kBins;
-        if ((edge_real && fabsf(t - tn) * cc.w < bound) || fabsf(delta - cc.eps) < bound) return 1;
-    }
-    return 0;
+    o.bound = fmaf(0.55f * rho * inv_p, fmaf(ex, dy2, ey * dx2), fmaf(1e-6f, o.delta, 1e-9f));
+    o.t = fmaf(o.delta, k.inv_w, k.t0);
+    const float tn = rintf(o.t);
+    const bool near_edge = (fabsf(o.t - tn) < o.bound * k.inv_w) & (tn >= k.tmin) & (tn <= (float)kBins);
+    const bool near_eps = fabsf(o.delta - k.eps) < o.bound;
+    o.queue = !cond | !(o.bound <= kMaxTol) | ((o.bound > kExempt) & (near_edge | near_eps));
+    return o;
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -241,12 +270,13 @@ __global__ void __launch_bounds__(kThreads, 1)
                    const __grid_constant__ CUtensorMap map_yh, const __grid_constant__ CUtensorMap map_yl,
                    TcArgs p) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
-    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
-                                                ~uintptr_t(1023));
+    // 1024-byte alignment of the stage buffers (128-byte swizzle atoms), by
+    // an offset from the shared array so the address space stays known
+    uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sbase = smem_u32(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
-    uint16_t *s_hist = reinterpret_cast<uint16_t *>(smem + SmemLayout::hist);
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem + SmemLayout::hist);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SmemLayout::bars);
     int *s_cmd = reinterpret_cast<int *>(smem + SmemLayout::cmd);  // [kStages] stage, [kStages + s] slot
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + SmemLayout::tmem_ptr);
@@ -270,7 +300,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    for (int e = threadIdx.x; e < kBins * 32 * kEpiWarps; e += kThreads) s_hist[e] = 0;
+    for (int e = threadIdx.x; e < kHistWords * 32 * kEpiWarps; e += kThreads) s_hist[e] = 0;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          smem_u32(s_tmem)),
@@ -432,12 +462,24 @@ __global__ void __launch_bounds__(kThreads, 1)
         CertPartial *mine = p.partials + (size_t)blockIdx.x * kEpiWarps + ew;
         int slot = 0;
         uint32_t sphase = 0;
-        unsigned long long npairs = 0, nviol = 0, nover = 0, nqueued = 0;
+        unsigned long long nviol = 0, nqueued = 0, nover = 0;
         double sum = 0.0, bsum = 0.0;
         float mx = -1.0f, mxb_all = 0.0f;
         int ai = 0x7fffffff, aj = 0x7fffffff;
-        const float sx = *p.scale_x, sy = *p.scale_y;
-        const float inv_sx2 = 1.0f / (sx * sx), inv_sy2 = 1.0f / (sy * sy);
+        EpiConst k;
+        {
+            const float sx = *p.scale_x, sy = *p.scale_y;
+            k.m2sx = -2.0f / (sx * sx);
+            k.m2sy = -2.0f / (sy * sy);
+            k.cx = p.cx;
+            k.cy = p.cy;
+            k.inv_w = p.cc.inv_w;
+            k.t0 = -p.cc.lo * p.cc.inv_w;
+            k.tmin = p.cc.lo_is_floor ? 1.0f : 0.0f;
+            k.eps = p.cc.eps;
+        }
+        const float lo = p.cc.lo, hi_edge = p.cc.hi, eps = p.cc.eps;
+        uint32_t *hrow = s_hist + ew * 32 + lane;  // bins 2w, 2w+1 at hrow[w * 256]
         int tiles_since_flush = 0;
         long long t = blockIdx.x;               // the producer's static tile sequence
         bool ok = true;
@@ -460,17 +502,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t ta = tmem_base + lane_addr + (uint32_t)(slot * kTile + h * kEpiCols);
                 const bool is_y = ks < p.ky_steps;
 #pragma unroll
-                for (int half = 0; half < 2; ++half) {
-                    uint32_t v[2][16];
-                    tmem_ld16(ta + half * 32, v[0]);
-                    tmem_ld16(ta + half * 32 + 16, v[1]);
+                for (int qd = 0; qd < 4; ++qd) {
+                    uint32_t v[16];
+                    tmem_ld16(ta + qd * 16, v);
                     tmem_wait_ld();
                     if (is_y) {
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) gy[half * 32 + c] += __uint_as_float(v[c >> 4][c & 15]);
+                        for (int c = 0; c < 16; ++c) gy[qd * 16 + c] += __uint_as_float(v[c]);
                     } else {
 #pragma unroll
-                        for (int c = 0; c < 32; ++c) gx[half * 32 + c] += __uint_as_float(v[c >> 4][c & 15]);
+                        for (int c = 0; c < 16; ++c) gx[qd * 16 + c] += __uint_as_float(v[c]);
                     }
                 }
                 tc_fence_before();
@@ -481,53 +522,46 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             if (!ok) break;
-            // ---- classify the 64 pairs of this thread
+            // ---- classify the 64 pairs of this thread (no data-dependent branch)
             const uint32_t packed = p.sched[t];
             const int I = (int)(packed >> 16), J = (int)(packed & 0xFFFF);
             const int i = I * kTile + r;
             const float4 ri = __ldg(p.rs + i);
             const int j0 = J * kTile + h * kEpiCols;
             const bool full = (I < J) && (J * kTile + kTile <= p.n);  // every pair valid
-            float tsum = 0.0f, tbsum = 0.0f;
-            bool stop = false;
+            float tsum = 0.0f, tbsum = 0.0f, tmx = -1.0f, tmxb = 0.0f, tmdb = -1.0f;
+            int tviol = 0, tover = 0, targ = 0;
             unsigned long long qmask = 0ull;
-            const float lo = p.cc.lo, inv_w = p.cc.inv_w, hi_edge = p.cc.hi, eps = p.cc.eps;
-            uint16_t *hrow = s_hist + ew * 32 + lane;
 #pragma unroll
             for (int c = 0; c < kEpiCols; ++c) {
                 const int j = j0 + c;
                 const float4 rj = __ldg(p.rs + j);
-                const bool valid = full || (i < j && j < p.n);
-                float delta = 0.0f, bound = 0.0f;
-                const int q = fast_pair(gx[c] * inv_sx2, gy[c] * inv_sy2, ri, rj, p.cx, p.cy, p.cc,
-                                        delta, bound);
+                const bool valid = full | ((i < j) & (j < p.n));
+                const PairOut o = fast_pair(gx[c], gy[c], ri, rj, k);
                 if (DUMP && p.dump && t < p.dump_tiles) {
-                    const float g_x = gx[c] * inv_sx2, g_y = gy[c] * inv_sy2;
                     float4 w;
-                    w.x = fmaf(-2.0f, g_x, ri.x + rj.x);
-                    w.y = fmaf(-2.0f, g_y, ri.y + rj.y);
+                    w.x = fmaf(k.m2sx, gx[c], ri.x + rj.x);
+                    w.y = fmaf(k.m2sy, gy[c], ri.y + rj.y);
                     w.z = fmaf(ri.z, rj.z, p.cx * (ri.x + rj.x));
                     w.w = fmaf(ri.w, rj.w, p.cy * (ri.y + rj.y));
                     p.dump[(size_t)t * kTile * kTile + r * kTile + h * kEpiCols + c] = w;
                 }
-                if (valid) {
-                    if (q) {
-                        qmask |= 1ull << c;
-                    } else {
-                        ++npairs;
-                        const float tb = (delta - lo) * inv_w;
-                        if (delta >= lo && delta < hi_edge)
-                            hrow[min((int)tb, kBins - 1) * (32 * kEpiWarps)] += 1;
-                        else
-                            ++nover;
-                        nviol += delta > eps;
-                        tsum += delta;
-                        tbsum += bound;
-                        mxb_all = fmaxf(mxb_all, bound);
-                        if (delta > mx) { mx = delta; ai = i; aj = j; }
-                        stop |= delta > eps + bound;
-                    }
-                }
+                const bool okp = valid & !o.queue;
+                qmask |= (valid & o.queue) ? (1ull << c) : 0ull;
+                const bool in_range = (o.delta >= lo) & (o.delta < hi_edge);
+                // pairs not counted in a bin add 0 (to bin 0's word)
+                const int bin = (okp & in_range) ? min((int)o.t, kBins - 1) : 0;
+                const uint32_t inc = (okp & in_range) ? ((bin & 1) ? 0x10000u : 1u) : 0u;
+                atomicAdd(hrow + (bin >> 1) * (32 * kEpiWarps), inc);
+                tover += (okp & !in_range) ? 1 : 0;
+                tviol += (okp & (o.delta > eps)) ? 1 : 0;
+                tsum += okp ? o.delta : 0.0f;
+                tbsum += okp ? o.bound : 0.0f;
+                tmxb = fmaxf(tmxb, okp ? o.bound : 0.0f);
+                tmdb = fmaxf(tmdb, okp ? o.delta - o.bound : -1.0f);
+                const bool better = okp & (o.delta > tmx);
+                tmx = better ? o.delta : tmx;
+                targ = better ? c : targ;
             }
             // push the queued pairs of this tile (rare), warp-aggregated
             nqueued += __popcll(qmask);
@@ -537,21 +571,31 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (has) qmask &= qmask - 1;
                 queue_push(has, i, j0 + c, p.queue, p.qcount, p.qcap);
             }
+            nviol += (unsigned)tviol;
+            nover += (unsigned)tover;
             sum += (double)tsum;
             bsum += (double)tbsum;
-            if (p.stop_flag && stop) atomicExch(p.stop_flag, 1);
+            mxb_all = fmaxf(mxb_all, tmxb);
+            if (tmx >= 0.0f && better_max(tmx, i, j0 + targ, mx, ai, aj)) {
+                mx = tmx;
+                ai = i;
+                aj = j0 + targ;
+            }
+            // a certain violation: delta - B > eps for some pair
+            if (p.stop_flag && tmdb > eps) atomicExch(p.stop_flag, 1);
             t += gridDim.x;
             if (++tiles_since_flush == kHistFlushTiles) {
                 tiles_since_flush = 0;
                 fold_hist(s_hist, ew, mine);
             }
         }
-        // ---- this warp's partial: histogram and scalar statistics
+        // ---- this warp's partial: histogram (with pairs and overflow) and
+        // the scalar statistics
         fold_hist(s_hist, ew, mine);
-        unsigned long long u[4] = {npairs, nviol, nover, nqueued};
+        unsigned long long u[3] = {nviol, nqueued, nover};
         for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-            for (int q = 0; q < 4; ++q) u[q] += __shfl_xor_sync(0xffffffffu, u[q], o);
+            for (int q = 0; q < 3; ++q) u[q] += __shfl_xor_sync(0xffffffffu, u[q], o);
             sum += __shfl_xor_sync(0xffffffffu, sum, o);
             bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
             mxb_all = fmaxf(mxb_all, __shfl_xor_sync(0xffffffffu, mxb_all, o));
@@ -561,7 +605,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (better_max(om, oi, oj, mx, ai, aj)) { mx = om; ai = oi; aj = oj; }
         }
         if (lane == 0) {
-            mine->pairs = u[0]; mine->violations = u[1]; mine->overflow = u[2]; mine->queued = u[3];
+            mine->violations = u[0]; mine->queued = u[1];
+            mine->overflow = u[2];
+            mine->pairs += u[2];   // fold_hist added the binned pairs
             mine->degenerate = 0;
             mine->sum = sum; mine->bound_sum = bsum;
             mine->max = mx; mine->max_bound = mxb_all; mine->argmax_i = ai; mine->argmax_j = aj;

@@ -1,53 +1,85 @@
 """Trains the dimension predictor on instances labelled by the certified search.
 
-    python -m paper_1609_05388_gb300.train_predictor --instances 300 --out predictor.bin
+    python -m paper_1609_05388_gb300.train_predictor --instances 2048 --out predictor.bin
 
 Instances come from the MNIST-shaped family (synth.mnist_like_family: rank,
-cluster count, sparsity and eps vary) with n log-uniform in [n_lo, n_hi]; each
-is labelled with the dimension the plain certified search returns (gallop and
-bisect with exhaustive certificates), its features come from adagio_features,
-and the network is trained full-batch with Adam on y = log m.  The last
-`--holdout` instances are kept out of training and reported.
+cluster count, sparsity and eps vary) with n log-uniform in [n_lo, n_hi].
+Batches of them are fitted with adagio_fit_batched: each is labelled with the
+dimension the plain certified search returns (doubling and bisection with
+exhaustive certificates) and its features come from the same fit's PCA.
+Instances that are not certifiable at m = d carry no label and are dropped.
+The network is trained full-batch with Adam on y = log m; the last
+`--holdout` instances are kept out of training and reported.  Synthetic data
+is generated by a pool of worker processes (started with `spawn`, before the
+first GPU call) while the GPU labels the previous batch.
 """
 from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
 import time
 
 import numpy as np
 
-from . import adagio as lib
 from . import synth
+
+
+def _make(args):
+    seed, n_lo, n_hi = args
+    rng = np.random.default_rng(seed)
+    n = int(np.exp(rng.uniform(np.log(n_lo), np.log(n_hi))))
+    return synth.mnist_like_family(rng, n)
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--instances", type=int, default=300)
-    ap.add_argument("--holdout", type=int, default=30)
+    ap.add_argument("--instances", type=int, default=2048)
+    ap.add_argument("--holdout", type=int, default=128)
+    ap.add_argument("--batch", type=int, default=64)
     ap.add_argument("--n-lo", type=int, default=2000)
     ap.add_argument("--n-hi", type=int, default=60000)
-    ap.add_argument("--steps", type=int, default=4000)
+    ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--workers", type=int, default=12)
     ap.add_argument("--out", required=True)
     a = ap.parse_args()
-    rng = np.random.default_rng(a.seed)
+    pool = mp.get_context("spawn").Pool(a.workers)
+    jobs = [(a.seed * 1_000_003 + k, a.n_lo, a.n_hi) for k in range(a.instances)]
+    stream = pool.imap(_make, jobs, chunksize=2)
+
+    import torch
+    from . import adagio as lib
+
     feats, labels, ns = [], [], []
+    dropped = 0
     t0 = time.time()
+    gpu_s = 0.0
     with lib.Context(0) as ctx:
-        for k in range(a.instances):
-            n = int(np.exp(rng.uniform(np.log(a.n_lo), np.log(a.n_hi))))
-            X, eps = synth.mnist_like_family(rng, n)
-            A, m, s, c, rc = ctx.fit(X, eps=eps, m_cap=X.shape[1], seed=1)
-            feats.append(ctx.features(X, eps))
-            labels.append(np.log(m))
-            ns.append(n)
+        for b0 in range(0, a.instances, a.batch):
+            items = [next(stream) for _ in range(min(a.batch, a.instances - b0))]
+            t1 = time.time()
+            dX = [torch.from_numpy(X).cuda() for X, _ in items]
+            res = ctx.fit_batched(dX, [e for _, e in items], graph=True, features=True)
+            torch.cuda.synchronize()
+            gpu_s += time.time() - t1
+            for (X, _), r in zip(items, res):
+                if r["status"] != lib.OK:
+                    dropped += 1
+                    continue
+                feats.append(r["feats"])
+                labels.append(np.log(r["m"]))
+                ns.append(X.shape[0])
+            del dX
         label_s = time.time() - t0
+        pool.close()
         F = np.array(feats, dtype=np.float32)
         t = np.array(labels, dtype=np.float32)
-        tr = slice(0, a.instances - a.holdout)
-        ho = slice(a.instances - a.holdout, a.instances)
+        N = len(t)
+        tr = slice(0, N - a.holdout)
+        ho = slice(N - a.holdout, N)
         ctx.mlp_init(a.seed)
+        loss = float("nan")
         for it in range(a.steps):
             lr = 3e-3 if it < a.steps // 2 else (1e-3 if it < 3 * a.steps // 4 else 3e-4)
             loss = ctx.mlp_train_step(F[tr], t[tr], lr)
@@ -55,7 +87,9 @@ def main():
         m_pred = np.ceil(1.05 * np.exp(y))
         m_true = np.exp(t[ho].astype(np.float64))
         ctx.mlp_save(a.out)
-    print(json.dumps({"instances": a.instances, "label_seconds": label_s, "train_loss": loss,
+    print(json.dumps({"instances": a.instances, "labelled": N, "dropped_not_certifiable": dropped,
+                      "label_seconds": label_s, "gpu_label_seconds": gpu_s, "train_loss": loss,
+                      "holdout": a.holdout,
                       "holdout_mean_abs_log_err": float(np.mean(np.abs(y - t[ho]))),
                       "holdout_mean_ratio_pred_over_true": float(np.mean(m_pred / m_true)),
                       "holdout_under_predicted": int(np.sum(m_pred < m_true))}))

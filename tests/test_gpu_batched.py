@@ -167,3 +167,21 @@ def test_batched_workload_64_instances(ctx):
         assert (res[i]["m"], res[i]["s"], res[i]["status"]) == (m, s, rc)
         assert torch.equal(res[i]["A"], A)
         _same_cert(res[i]["cert"], c)
+
+
+def test_batched_features_match_single_call(ctx):
+    """The predictor's features taken from each batched fit's own PCA agree with
+    adagio_features on the same data (same spectrum up to the iteration's
+    tolerance; log n, log d, eps and the constant exactly)."""
+    rng = np.random.default_rng(23)
+    Xs, epss = [], []
+    for n in (900, 2500, 400):
+        X, eps = synth.mnist_like_family(rng, n, d=196)
+        Xs.append(X)
+        epss.append(eps)
+    dX = [torch.from_numpy(X).cuda() for X in Xs]
+    res = ctx.fit_batched(dX, epss, features=True)
+    for X, eps, r in zip(Xs, epss, res):
+        f = ctx.features(X, eps)
+        np.testing.assert_allclose(r["feats"][:16], f[:16], atol=2e-3)
+        np.testing.assert_array_equal(r["feats"][64:], f[64:])
