@@ -128,6 +128,176 @@ __global__ void cholesky_kernel(double *G, int b, double floor_rel) {
     }
 }
 
+// FP32 Cholesky of a b x b SPD Gram (FP64 or FP32 input, row-major), one
+// CTA: G + shift * max(diag) I = R^T R with R upper triangular (FP32,
+// row-major, lower part zero).  Pivots are floored at 1e-7 of the largest
+// diagonal entry (the factor stays finite for a rank-deficient Gram).
+// Right-looking with the trailing matrix resident in registers: the upper
+// triangle is cut into 4 x 4 blocks, each thread owns up to two of them; at
+// step k the owners of row k publish it to a double-buffered shared row, one
+// barrier later every thread applies the rank-1 update to its blocks.
+constexpr int kCholThreads = 512;
+constexpr int kCholBlk = 2;  // 4 x 4 blocks per thread (ceil(40 * 41 / 2 / 512))
+template <typename TG>
+__global__ void __launch_bounds__(kCholThreads) cholesky32_kernel(const TG *__restrict__ G, int b,
+                                                                  float shift_rel,
+                                                                  float *__restrict__ R) {
+    __shared__ float rowbuf[2][kJacobiMax + 4];
+    __shared__ float s_red[kCholThreads / 32];
+    __shared__ float s_shift, s_floor;
+    const int tid = threadIdx.x;
+    float mx = 0.0f;
+    for (int i = tid; i < b; i += kCholThreads) mx = fmaxf(mx, (float)G[(int64_t)i * b + i]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((tid & 31) == 0) s_red[tid >> 5] = mx;
+    for (int e = tid; e < b * b; e += kCholThreads)
+        if (e % b < e / b) R[e] = 0.0f;
+    __syncthreads();
+    if (tid == 0) {
+        float m = 0.0f;
+        for (int w = 0; w < kCholThreads / 32; ++w) m = fmaxf(m, s_red[w]);
+        s_shift = shift_rel * m;
+        s_floor = fmaxf(1e-7f * m, 1e-30f);
+    }
+    __syncthreads();
+    const int nb = (b + 3) / 4;
+    const int nblocks = nb * (nb + 1) / 2;
+    int bi[kCholBlk], bj[kCholBlk];
+    float S[kCholBlk][4][4];
+#pragma unroll
+    for (int q = 0; q < kCholBlk; ++q) {
+        int lin = tid + q * kCholThreads;
+        bi[q] = -1;
+        bj[q] = -1;
+        if (lin < nblocks) {
+            int ib = 0;
+            while (lin >= nb - ib) {
+                lin -= nb - ib;
+                ++ib;
+            }
+            bi[q] = ib;
+            bj[q] = ib + lin;
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int i = bi[q] * 4 + r, j = bj[q] * 4 + c;
+                float v = 0.0f;
+                if (bi[q] >= 0 && i < b && j < b && j >= i) v = (float)G[(int64_t)i * b + j] + (i == j ? s_shift : 0.0f);
+                S[q][r][c] = v;
+            }
+        // publish row 0
+        if (bi[q] == 0)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) rowbuf[0][bj[q] * 4 + c] = S[q][0][c];
+    }
+    for (int k = 0; k < b; ++k) {
+        __syncthreads();
+        const float *row = rowbuf[k & 1];
+        float piv = row[k];
+        if (!(piv > s_floor)) piv = s_floor;
+        const float inv = rsqrtf(piv);
+        const float inv2 = inv * inv;
+        for (int j = k + tid; j < b; j += kCholThreads)
+            R[(int64_t)k * b + j] = j == k ? piv * inv : row[j] * inv;
+        const int kn = k + 1;
+#pragma unroll
+        for (int q = 0; q < kCholBlk; ++q) {
+            if (bi[q] < 0 || bi[q] * 4 + 3 <= k) continue;
+            float a[4], w[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                const int i = bi[q] * 4 + r;
+                a[r] = (i > k && i < b) ? row[i] * inv2 : 0.0f;
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int j = bj[q] * 4 + c;
+                w[c] = (j > k && j < b) ? row[j] : 0.0f;
+            }
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) S[q][r][c] = fmaf(-a[r], w[c], S[q][r][c]);
+            // row k + 1 lives in this block row: publish it for the next step
+            if (kn < b && (kn >> 2) == bi[q]) {
+                const int rr = kn & 3;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float v = rr == 0 ? S[q][0][c] : rr == 1 ? S[q][1][c] : rr == 2 ? S[q][2][c] : S[q][3][c];
+                    rowbuf[kn & 1][bj[q] * 4 + c] = v;
+                }
+            }
+        }
+    }
+}
+
+// V (b x d rows) <- R^{-T} V, two columns per warp: each half-warp solves
+// one column, lane l keeping the solved entries l, l + 16, ... in registers;
+// each step is a lane-local partial dot product and a 16-lane reduction.  R
+// (FP32 upper) is staged transposed in shared memory with a padded stride,
+// so both the staging and the lanes of a step touch distinct banks.
+constexpr int kTrsmWarps = 8;
+constexpr int kTrsmRegs = (kJacobiMax + 15) / 16;
+__global__ void __launch_bounds__(32 * kTrsmWarps) trsm_warp_kernel(const float *__restrict__ R, int b,
+                                                                   float *V, int64_t ldv, int d) {
+    extern __shared__ float Rsm[];  // Rsm[i * (b + 1) + k] = R[k][i]
+    const int ldr = b + 1;
+    for (int e = threadIdx.x; e < b * b; e += blockDim.x) {
+        const int k = e / b, i = e % b;
+        Rsm[i * ldr + k] = R[e];
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 15;
+    const int j = (blockIdx.x * kTrsmWarps + (threadIdx.x >> 5)) * 2 + ((threadIdx.x >> 4) & 1);
+    const bool ok = j < d;
+    float v[kTrsmRegs], x[kTrsmRegs];
+#pragma unroll
+    for (int m = 0; m < kTrsmRegs; ++m) {
+        const int k = lane + 16 * m;
+        v[m] = (ok && k < b) ? V[(int64_t)k * ldv + j] : 0.0f;
+        x[m] = 0.0f;
+    }
+#pragma unroll
+    for (int m = 0; m < kTrsmRegs; ++m) {
+        if (16 * m >= b) break;
+        for (int ii = 0; ii < 16; ++ii) {
+            const int i = 16 * m + ii;
+            if (i >= b) break;
+            // partial of sum_{k < i} R[k][i] x_k over this lane's k
+            float part = 0.0f;
+#pragma unroll
+            for (int q = 0; q <= m; ++q) {
+                const int k = lane + 16 * q;
+                if (k < i) part = fmaf(Rsm[i * ldr + k], x[q], part);
+            }
+            for (int o = 8; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o, 16);
+            const float vi = __shfl_sync(0xffffffffu, v[m], ii, 16);
+            const float xi = __fdividef(vi - part, Rsm[i * ldr + i]);
+            if (lane == ii) x[m] = xi;
+        }
+    }
+    if (ok) {
+#pragma unroll
+        for (int m = 0; m < kTrsmRegs; ++m) {
+            const int k = lane + 16 * m;
+            if (k < b) V[(int64_t)k * ldv + j] = x[m];
+        }
+    }
+}
+
+// C = alpha * sum_z P_z + beta * C (split-K partials, fixed summation order)
+__global__ void splitk_reduce_ab_kernel(const float *__restrict__ part, int chunks, int M, int N,
+                                        float alpha, float beta, float *__restrict__ C, int64_t ldc) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)M * N) return;
+    float acc = 0.0f;
+    for (int z = 0; z < chunks; ++z) acc += part[(int64_t)z * M * N + e];
+    float *c = C + (e / N) * ldc + (e % N);
+    *c = beta != 0.0f ? fmaf(alpha, acc, beta * *c) : alpha * acc;
+}
+
 // Row-wise triangular solve: one thread per column of V, R's upper triangle
 // staged in shared memory as FP32, four independent partial sums per row.
 // FP32 arithmetic: the first CholeskyQR pass only needs a well-conditioned
@@ -172,13 +342,15 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const double *__
     __shared__ float red[kJacobiThreads / 32][2];
     __shared__ int s_done;
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < b * b; e += nt) {
-        const int i = e / b, j = e % b;
-        H[i * ld + j] = (float)(0.5 * (Hin[i * b + j] + Hin[j * b + i]));
-        U[i * ld + j] = (i == j) ? 1.0f : 0.0f;
-    }
+    for (int i = tid >> 5; i < b; i += nt >> 5)
+        for (int j = tid & 31; j < b; j += 32) {
+            H[i * ld + j] = (float)(0.5 * (Hin[i * b + j] + Hin[j * b + i]));
+            U[i * ld + j] = (i == j) ? 1.0f : 0.0f;
+        }
     const int B = (b + 1) & ~1;   // even number of players (index b is a dummy when b is odd)
     const int half = B / 2;
+    const int lx = tid & 31, wy = tid >> 5, nwy = nt >> 5;
+    float prev_off = 3.0e38f;
     __syncthreads();
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int r = 0; r < B - 1; ++r) {
@@ -190,50 +362,56 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const double *__
                 float c = 1.0f, s = 0.0f;
                 if (q < b) {
                     const float apq = H[p * ld + q];
-                    if (apq != 0.0f) {
-                        const float app = H[p * ld + p], aqq = H[q * ld + q];
+                    const float app = H[p * ld + p], aqq = H[q * ld + q];
+                    // a rotation whose angle is below FP32 resolution of the
+                    // diagonal changes nothing: skip its updates
+                    if (fabsf(apq) > 1e-8f * fmaxf(fabsf(app), fabsf(aqq)) && apq != 0.0f) {
                         const float tau = (aqq - app) / (2.0f * apq);
                         const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
                         c = rsqrtf(1.0f + t * t);
                         s = t * c;
+                    } else {
+                        q = b;
                     }
                 }
                 pp[tid] = p; qq[tid] = q; cs[tid] = c; sn[tid] = s;
             }
             __syncthreads();
-            // rows: H <- J^T H
-            for (int e = tid; e < half * b; e += nt) {
-                const int k = e / b, j = e % b;
+            // rows: H <- J^T H  (rotation k over warps, column j over lanes)
+            for (int k = wy; k < half; k += nwy) {
                 const int p = pp[k], q = qq[k];
                 if (q >= b) continue;
                 const float c = cs[k], s = sn[k];
-                const float hp = H[p * ld + j], hq = H[q * ld + j];
-                H[p * ld + j] = c * hp - s * hq;
-                H[q * ld + j] = s * hp + c * hq;
+                for (int j = lx; j < b; j += 32) {
+                    const float hp = H[p * ld + j], hq = H[q * ld + j];
+                    H[p * ld + j] = c * hp - s * hq;
+                    H[q * ld + j] = s * hp + c * hq;
+                }
             }
             __syncthreads();
-            // columns: H <- H J, U <- U J
-            for (int e = tid; e < half * b; e += nt) {
-                const int k = e % half, i = e / half;
-                const int p = pp[k], q = qq[k];
-                if (q >= b) continue;
-                const float c = cs[k], s = sn[k];
-                const float hp = H[i * ld + p], hq = H[i * ld + q];
-                H[i * ld + p] = c * hp - s * hq;
-                H[i * ld + q] = s * hp + c * hq;
-                const float up = U[i * ld + p], uq = U[i * ld + q];
-                U[i * ld + p] = c * up - s * uq;
-                U[i * ld + q] = s * up + c * uq;
+            // columns: H <- H J, U <- U J  (row i over warps, rotation k over lanes)
+            for (int i = wy; i < b; i += nwy) {
+                for (int k = lx; k < half; k += 32) {
+                    const int p = pp[k], q = qq[k];
+                    if (q >= b) continue;
+                    const float c = cs[k], s = sn[k];
+                    const float hp = H[i * ld + p], hq = H[i * ld + q];
+                    H[i * ld + p] = c * hp - s * hq;
+                    H[i * ld + q] = s * hp + c * hq;
+                    const float up = U[i * ld + p], uq = U[i * ld + q];
+                    U[i * ld + p] = c * up - s * uq;
+                    U[i * ld + q] = s * up + c * uq;
+                }
             }
             __syncthreads();
         }
         // convergence: off-diagonal vs diagonal mass
         float off = 0.0f, dia = 0.0f;
-        for (int e = tid; e < b * b; e += nt) {
-            const int i = e / b, j = e % b;
-            const float v = H[i * ld + j];
-            if (i == j) dia += v * v; else off += v * v;
-        }
+        for (int i = wy; i < b; i += nwy)
+            for (int j = lx; j < b; j += 32) {
+                const float v = H[i * ld + j];
+                if (i == j) dia += v * v; else off += v * v;
+            }
         for (int o = 16; o > 0; o >>= 1) {
             off += __shfl_xor_sync(0xffffffffu, off, o);
             dia += __shfl_xor_sync(0xffffffffu, dia, o);
@@ -243,7 +421,11 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const double *__
         if (tid == 0) {
             float o2 = 0.0f, d2 = 0.0f;
             for (int w = 0; w < nt / 32; ++w) { o2 += red[w][0]; d2 += red[w][1]; }
-            s_done = o2 <= 1e-12f * d2;   // off-diagonal norm <= 1e-6 of the diagonal's
+            // converged: off-diagonal norm <= 1e-6 of the diagonal's; or at the
+            // FP32 rounding floor: after the first sweeps (the quadratic
+            // phase) a sweep no longer halves the off-diagonal mass
+            s_done = (o2 <= 1e-12f * d2) || (sweep >= 2 && o2 > 0.25f * prev_off);
+            prev_off = o2;
         }
         __syncthreads();
         if (s_done) break;
@@ -271,6 +453,28 @@ __global__ void ritz_residual_kernel(const float *__restrict__ W, const float *_
     for (int j = lane; j < d; j += 32) {
         const float r = W[(int64_t)row * ld + j] - th * V[(int64_t)row * ld + j];
         acc += r * r;
+    }
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) res[row] = sqrtf(acc);
+}
+
+__global__ void residual_rows_kernel(const float *__restrict__ W, const float *__restrict__ V, int64_t ld,
+                                     int d, const double *__restrict__ theta, int s,
+                                     float *__restrict__ Rm) {
+    const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (int64_t)s * d) return;
+    const int i = (int)(e / d), j = (int)(e % d);
+    Rm[e] = W[(int64_t)i * ld + j] - (float)theta[i] * V[(int64_t)i * ld + j];
+}
+
+__global__ void row_norms_kernel(const float *__restrict__ Rm, int d, int s, float *__restrict__ res) {
+    const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (row >= s) return;
+    float acc = 0.0f;
+    for (int j = lane; j < d; j += 32) {
+        const float r = Rm[(int64_t)row * d + j];
+        acc = fmaf(r, r, acc);
     }
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) res[row] = sqrtf(acc);
@@ -383,6 +587,56 @@ void linalg_init() {
     set_max_dyn_smem((const void *)cholesky_kernel, (int)(b * (b + 1) * sizeof(double)));
     set_max_dyn_smem((const void *)trsm_rows_kernel, (int)((b * b + b * kTrsmCols) * sizeof(float)));
     set_max_dyn_smem((const void *)jacobi_kernel, (int)(2 * b * (b + 1) * sizeof(float)));
+    set_max_dyn_smem((const void *)trsm_warp_kernel, (int)(b * (b + 1) * sizeof(float)));
+}
+
+template <typename TG>
+void cholesky32(const TG *G, int b, float shift_rel, float *R, cudaStream_t st) {
+    if (b > kJacobiMax) fail(ADAGIO_E_INVALID_ARG, "internal: Cholesky block %d > %d", b, kJacobiMax);
+    cholesky32_kernel<TG><<<1, kCholThreads, 0, st>>>(G, b, shift_rel, R);
+    ADAGIO_CHECK_LAUNCH();
+}
+template void cholesky32<double>(const double *, int, float, float *, cudaStream_t);
+template void cholesky32<float>(const float *, int, float, float *, cudaStream_t);
+
+void trsm_warp(const float *R, int b, float *V, int64_t ldv, int d, cudaStream_t st) {
+    if (b > kJacobiMax) fail(ADAGIO_E_INVALID_ARG, "internal: TRSM block %d > %d", b, kJacobiMax);
+    const size_t smem = (size_t)b * (b + 1) * sizeof(float);
+    set_max_dyn_smem((const void *)trsm_warp_kernel, (int)smem);
+    trsm_warp_kernel<<<(unsigned)ceil_div(d, 2 * kTrsmWarps), 32 * kTrsmWarps, smem, st>>>(R, b, V, ldv, d);
+    ADAGIO_CHECK_LAUNCH();
+}
+
+static int device_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        ADAGIO_CUDA(cudaGetDevice(&dev));
+        ADAGIO_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    }
+    return sms;
+}
+
+void gemm_f32(int M, int N, int K, float alpha, MatView<float> A, MatView<float> B, float beta,
+              float *C, int64_t ldc, float *partials, int64_t partial_floats, cudaStream_t st) {
+    if (M <= 0 || N <= 0) return;
+    const int64_t tiles = ceil_div(M, GT) * ceil_div(N, GT);
+    int64_t chunks = std::min<int64_t>(ceil_div(2 * (int64_t)device_sms(), tiles), ceil_div(K, 64));
+    if (partials) chunks = std::min<int64_t>(chunks, partial_floats / ((int64_t)M * N));
+    if (chunks <= 1 || !partials) {
+        gemm<float, float, float, float>(M, N, K, alpha, A, B, beta, C, ldc, st);
+        return;
+    }
+    const int kchunk = (int)(ceil_div(ceil_div(K, chunks), GK) * GK);
+    chunks = ceil_div(K, kchunk);
+    dim3 grid((unsigned)ceil_div(N, GT), (unsigned)ceil_div(M, GT), (unsigned)chunks);
+    gemm_kernel<float, float, float, float><<<grid, GNT, 0, st>>>(M, N, K, kchunk, 1.0f, A, B, 0.0f,
+                                                                   partials, N, (int64_t)M * N);
+    ADAGIO_CHECK_LAUNCH();
+    const int64_t mn = (int64_t)M * N;
+    splitk_reduce_ab_kernel<<<(unsigned)ceil_div(mn, 256), 256, 0, st>>>(partials, (int)chunks, M, N,
+                                                                       alpha, beta, C, ldc);
+    ADAGIO_CHECK_LAUNCH();
 }
 
 void cholesky_upper(double *G, int b, double floor_rel, cudaStream_t st) {
@@ -411,6 +665,22 @@ void ritz_residuals(const float *W, const float *V, int64_t ld, int d, const dou
                     float *res, cudaStream_t st) {
     if (s <= 0) return;
     ritz_residual_kernel<<<(unsigned)ceil_div(s, 8), 256, 0, st>>>(W, V, ld, d, theta, s, res);
+    ADAGIO_CHECK_LAUNCH();
+}
+
+void ritz_residuals_projected(const float *W, const float *V, int64_t ld, int d, int b,
+                              const double *theta, int s, float *Rm, float *coef, float *partials,
+                              int64_t partial_floats, float *res, cudaStream_t st) {
+    if (s <= 0) return;
+    residual_rows_kernel<<<(unsigned)ceil_div((int64_t)s * d, 256), 256, 0, st>>>(W, V, ld, d, theta,
+                                                                                   s, Rm);
+    ADAGIO_CHECK_LAUNCH();
+    // Rm <- Rm - (Rm V^T) V: the part of each residual outside span(V)
+    gemm_f32(s, b, d, 1.0f, MatView<float>{Rm, d, 1}, MatView<float>{V, 1, ld}, 0.0f, coef, b,
+             partials, partial_floats, st);
+    gemm_f32(s, d, b, -1.0f, MatView<float>{coef, b, 1}, MatView<float>{V, ld, 1}, 1.0f, Rm, d,
+             partials, partial_floats, st);
+    row_norms_kernel<<<(unsigned)ceil_div(s, 8), 256, 0, st>>>(Rm, d, s, res);
     ADAGIO_CHECK_LAUNCH();
 }
 

@@ -50,6 +50,23 @@ void cholesky_upper(double *G, int b, double floor_rel, cudaStream_t st);
 // result is (v_i - sum_{k<i} R_ki r_k) / R_ii; FP32 arithmetic.
 void trsm_rows(const double *R, int b, float *V, int64_t ldv, int d, cudaStream_t st);
 
+// FP32 Cholesky (one CTA) of the SPD b x b Gram G (FP64 or FP32, row-major)
+// with a diagonal shift of shift_rel * max(diag G): R (FP32 b x b upper,
+// row-major).  Pivots are floored at 1e-7 of the largest diagonal entry.
+template <typename TG>
+void cholesky32(const TG *G, int b, float shift_rel, float *R, cudaStream_t st);
+
+// V (b x d rows, FP32, leading dimension ldv) <- R^{-T} V with R from
+// cholesky32: one warp per column of V.
+void trsm_warp(const float *R, int b, float *V, int64_t ldv, int d, cudaStream_t st);
+
+// FP32 GEMM like gemm<float...>, split over K when the output has too few
+// tiles to fill the GPU: partial products go to `partials` (up to
+// partial_floats floats) and are summed in a fixed order, so the result is
+// deterministic.  partials == nullptr: no split.
+void gemm_f32(int M, int N, int K, float alpha, MatView<float> A, MatView<float> B, float beta,
+              float *C, int64_t ldc, float *partials, int64_t partial_floats, cudaStream_t st);
+
 // Symmetric eigen-decomposition of a b x b matrix (b <= kJacobiMax) by
 // parallel cyclic Jacobi in one CTA: H (FP64 in) -> theta (descending, FP64
 // out) and U (b x b FP32 row-major, column c = eigenvector of theta[c]).
@@ -59,6 +76,16 @@ void jacobi_eig(const double *H, int b, double *theta, float *U, int max_sweeps,
 // Per-row residual norms ||W_i - theta_i V_i|| for i < s (FP32 out).
 void ritz_residuals(const float *W, const float *V, int64_t ld, int d, const double *theta, int s,
                     float *res, cudaStream_t st);
+
+// Ritz residual norms taken outside the subspace: for i < s,
+// res_i = ||(I - V^T V)(W_i - theta_i V_i)|| with V (b x d) orthonormal rows.
+// For exact Rayleigh-Ritz pairs this equals ||W_i - theta_i V_i|| (the
+// residual is orthogonal to the subspace); it does not count the part that an
+// inexact rotation leaves inside the subspace.  Rm: s x d scratch; coef:
+// s x b scratch; partials: split-K scratch of gemm_f32.
+void ritz_residuals_projected(const float *W, const float *V, int64_t ld, int d, int b,
+                              const double *theta, int s, float *Rm, float *coef, float *partials,
+                              int64_t partial_floats, float *res, cudaStream_t st);
 
 // Flip the sign of each row of P (s x d) so its largest-magnitude entry
 // (lowest index on ties) is positive.

@@ -6,9 +6,10 @@
 //   start    : +-1 block V (b x d, rows are vectors) from the counter RNG
 //   iterate  : W = V C; H = V W^T (FP64); H = U diag(theta) U^T (Jacobi);
 //              V <- U^T V, W <- U^T W (Rayleigh-Ritz); stop when every kept
-//              Ritz residual ||W_i - theta_i V_i|| <= tol * theta_1;
-//              otherwise V <- orth(W) (shifted CholeskyQR2, FP64 Gram and
-//              Cholesky)
+//              Ritz residual ||W_i - theta_i V_i|| <= tol * theta_1 (taken
+//              outside span(V), which is what an exact Rayleigh-Ritz leaves);
+//              otherwise V <- orth(W) (shifted CholeskyQR3 in FP32 with an
+//              FP64 Gram in the first pass)
 //   blocks   : directions are found in blocks of at most kJacobiMax - p;
 //              later blocks iterate in the orthogonal complement of the
 //              earlier ones (deflation), so the rows of P stay sorted by
@@ -26,6 +27,10 @@
 
 namespace adagio {
 
+static int64_t pca_part_floats(int d, int s_cap) {
+    return (int64_t)8 * std::min(kJacobiMax, d) * std::max(d, std::max(s_cap, 1));
+}
+
 size_t pca_bytes(int64_t n, int d, int s_cap, int oversample) {
     const int b = std::min(kJacobiMax, d);
     size_t bytes = prep_bytes(n, d, true, false);
@@ -39,6 +44,8 @@ size_t pca_bytes(int64_t n, int d, int s_cap, int oversample) {
     bytes += align_up((size_t)(b + std::max(s_cap, 1)) * sizeof(double), 256);     // theta
     bytes += align_up((size_t)b * sizeof(float), 256);                              // residuals
     bytes += align_up((size_t)ceil_div(d, kF64Chunk) * b * b * sizeof(double), 256); // split-K
+    bytes += 2 * align_up((size_t)b * b * sizeof(float), 256);                     // G32, R32
+    bytes += align_up(pca_part_floats(d, s_cap) * sizeof(float), 256);             // FP32 split-K
     (void)oversample;
     return bytes + 8192;
 }
@@ -83,6 +90,10 @@ void PCA::init_enqueue(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int
     theta = ws_array<double>(ctx, std::max(s_cap, 1));
     res = ws_array<float>(ctx, bmax);
     f64part = ws_array<double>(ctx, (size_t)ceil_div(d, kF64Chunk) * bmax * bmax);
+    G32 = ws_array<float>(ctx, (size_t)bmax * bmax);
+    R32 = ws_array<float>(ctx, (size_t)bmax * bmax);
+    part_floats = pca_part_floats(d, s_cap);
+    part = ws_array<float>(ctx, (size_t)part_floats);
     unsigned *hflag = reinterpret_cast<unsigned *>(stage(pca_host_bytes()));
     ADAGIO_CUDA(cudaMemcpyAsync(hflag, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
 }
@@ -102,24 +113,38 @@ void PCA::init(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int64_t ldx
 // rows of M (r x d) <- M - (M P^T) P over the s_done finished directions
 void PCA::deflate(float *M, int r, cudaStream_t st) {
     if (s_done == 0 || r == 0) return;
-    gemm<float, float, float, float>(r, s_done, d, 1.0f, MatView<float>{M, d, 1},
-                                     MatView<float>{P, 1, d}, 0.0f, coef, s_done, st);
-    gemm<float, float, float, float>(r, d, s_done, -1.0f, MatView<float>{coef, s_done, 1},
-                                     MatView<float>{P, d, 1}, 1.0f, M, d, st);
+    gemm_f32(r, s_done, d, 1.0f, MatView<float>{M, d, 1}, MatView<float>{P, 1, d}, 0.0f, coef,
+             s_done, part, part_floats, st);
+    gemm_f32(r, d, s_done, -1.0f, MatView<float>{coef, s_done, 1}, MatView<float>{P, d, 1}, 1.0f,
+             M, d, part, part_floats, st);
 }
 
+// Orthonormalises the rows of M (b x d): shifted CholeskyQR3 (Fukaya et al.,
+// SIAM J. Sci. Comput. 2020) in FP32.  The first pass takes its Gram in FP64
+// and a shift of 1e-5 of the largest diagonal entry, so it succeeds for any
+// conditioning an FP32 matrix can carry and leaves a basis with condition
+// number below ~300; two unshifted-size passes with FP32 Grams then restore
+// orthonormality to FP32 precision.
 void PCA::orth(float *M, int b, cudaStream_t st) {
-    for (int pass = 0; pass < 2; ++pass) {
-        gemm_f64_splitk(b, b, d, MatView<float>{M, d, 1}, MatView<float>{M, 1, d}, G, f64part,
-                        kF64Chunk, st);
-        cholesky_upper(G, b, pass == 0 ? 1e-12 : 1e-15, st);
-        trsm_rows(G, b, M, d, d, st);
+    gemm_f64_splitk(b, b, d, MatView<float>{M, d, 1}, MatView<float>{M, 1, d}, G, f64part, kF64Chunk,
+                    st);
+    cholesky32<double>(G, b, 1e-5f, R32, st);
+    trsm_warp(R32, b, M, d, d, st);
+    for (int pass = 1; pass < 3; ++pass) {
+        gemm_f32(b, b, d, 1.0f, MatView<float>{M, d, 1}, MatView<float>{M, 1, d}, 0.0f, G32, b, part,
+                 part_floats, st);
+        cholesky32<float>(G32, b, pass == 1 ? 1e-7f : 0.0f, R32, st);
+        trsm_warp(R32, b, M, d, d, st);
     }
 }
 
-// Rayleigh-Ritz (and the convergence test) on the first iteration, every
-// kRREvery-th and the last; CholeskyQR2 keeps V orthonormal in between
-constexpr int kRREvery = 4;
+// Rayleigh-Ritz (and the convergence test) on the first iteration, then at
+// the iteration where the last test predicts convergence (at most kRRMax
+// iterations later), and on the last; CholeskyQR keeps V orthonormal in
+// between.  The prediction: the Ritz residual of direction i shrinks by about
+// theta_b / theta_i per iteration (the block's smallest Ritz value standing
+// in for the first eigenvalue outside the block).
+constexpr int kRRMax = 8;
 
 void PCA::begin_block(int s_needed, cudaStream_t st) {
     (void)s_needed;
@@ -127,6 +152,7 @@ void PCA::begin_block(int s_needed, cudaStream_t st) {
     blk.s_blk = std::min({s_cap - s_done, kJacobiMax - p, blk.remaining});
     blk.b = std::min(blk.s_blk + p, blk.remaining);
     blk.it = 0;
+    blk.next_rr = 0;
     blk.last = false;
     blk.active = true;
     rademacher_block(seed + (uint64_t)s_done * 0x9E3779B9ull, blk.b, d, V, d, st);
@@ -140,24 +166,31 @@ void PCA::advance(int s_needed, cudaStream_t st) {
     for (;;) {
         ++iterations;
         // W = V C (C symmetric)
-        gemm<float, float, float, float>(b, d, d, 1.0f, MatView<float>{V, d, 1},
-                                         MatView<float>{C, d, 1}, 0.0f, W, d, st);
+        gemm_f32(b, d, d, 1.0f, MatView<float>{V, d, 1}, MatView<float>{C, d, 1}, 0.0f, W, d, part,
+                 part_floats, st);
         deflate(W, b, st);
         const int it = blk.it;
         blk.last = it == max_iter - 1 || b == blk.remaining;
-        if ((it % kRREvery) == kRREvery - 1 || blk.last || it == 0) {
+        if (it >= blk.next_rr || blk.last) {
             // Rayleigh-Ritz: H = V W^T, H = U diag(theta) U^T
             gemm_f64_splitk(b, b, d, MatView<float>{V, d, 1}, MatView<float>{W, 1, d}, H, f64part,
                             kF64Chunk, st);
-            jacobi_eig(H, b, theta_blk, U, 30, st);
+            // the first Rayleigh-Ritz step of a block sees a dense H; later ones
+            // start near-diagonal, where Jacobi converges quadratically for
+            // separated Ritz values.  Rotations inside a cluster of nearly equal
+            // values are left unfinished: they mix directions that are
+            // interchangeable, and the convergence test measures the subspace.
+            jacobi_eig(H, b, theta_blk, U, it == 0 ? 6 : 3, st);
             // V <- U^T V, W <- U^T W
-            gemm<float, float, float, float>(b, d, b, 1.0f, MatView<float>{U, 1, b},
-                                             MatView<float>{V, d, 1}, 0.0f, T, d, st);
+            gemm_f32(b, d, b, 1.0f, MatView<float>{U, 1, b}, MatView<float>{V, d, 1}, 0.0f, T, d,
+                     part, part_floats, st);
             std::swap(V, T);
-            gemm<float, float, float, float>(b, d, b, 1.0f, MatView<float>{U, 1, b},
-                                             MatView<float>{W, d, 1}, 0.0f, T, d, st);
+            gemm_f32(b, d, b, 1.0f, MatView<float>{U, 1, b}, MatView<float>{W, d, 1}, 0.0f, T, d,
+                     part, part_floats, st);
             std::swap(W, T);
-            ritz_residuals(W, V, d, d, theta_blk, s_blk, res, st);
+            // T (the old W) is free: scratch of the residuals
+            ritz_residuals_projected(W, V, d, d, b, theta_blk, s_blk, T, coef, part, part_floats, res,
+                                     st);
             char *hs = reinterpret_cast<char *>(stage(pca_host_bytes()));
             ADAGIO_CUDA(cudaMemcpyAsync(hs, theta_blk, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
             ADAGIO_CUDA(cudaMemcpyAsync(hs + (size_t)kJacobiMax * 8, res, sizeof(float) * s_blk,
@@ -182,6 +215,17 @@ void PCA::resolve(cudaStream_t st) {
         accept_block(st);
         return;
     }
+    int k_pred = 1;
+    const double theta_b = hth[blk.b - 1];
+    for (int i = 0; i < blk.s_blk; ++i) {
+        const double r = hres[i], target = tol * theta1;
+        if (!(r > target)) continue;
+        const double rho = hth[i] > 0.0 ? theta_b / hth[i] : 1.0;
+        int k = kRRMax;
+        if (rho > 0.0 && rho < 0.999) k = (int)std::ceil(std::log(target / r) / std::log(rho));
+        k_pred = std::max(k_pred, std::min(std::max(k, 1), kRRMax));
+    }
+    blk.next_rr = blk.it + k_pred;
     std::swap(V, W);
     orth(V, blk.b, st);
     ++blk.it;

@@ -20,6 +20,8 @@ struct PCA {
     double *theta = nullptr;   // eigenvalue estimates of those rows
     float *V = nullptr, *W = nullptr, *T = nullptr, *U = nullptr, *coef = nullptr, *res = nullptr;
     double *G = nullptr, *H = nullptr, *theta_blk = nullptr, *f64part = nullptr;
+    float *G32 = nullptr, *R32 = nullptr, *part = nullptr;  // FP32 Gram, Cholesky factor, split-K
+    int64_t part_floats = 0;
     unsigned *flags = nullptr;
     double *elapsed_ms = nullptr;  // optional: extend() adds its wall time here
     // pinned host buffer of at least pca_host_bytes() for the convergence
@@ -48,6 +50,7 @@ struct PCA {
     struct Block {
         bool active = false;
         int it = 0, s_blk = 0, b = 0, remaining = 0;
+        int next_rr = 0;  // iteration of the next Rayleigh-Ritz step
         bool last = false;
     } blk;
     void *stage(size_t bytes);
