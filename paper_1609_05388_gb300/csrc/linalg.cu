@@ -329,27 +329,34 @@ __global__ void trsm_rows_kernel(const double *__restrict__ R, int b, float *V, 
 
 constexpr int kJacobiThreads = 512;
 
+// Parallel cyclic Jacobi (round-robin pairing, b / 2 disjoint rotations per
+// round) on H (FP32 in shared memory).  A round's rotations form a
+// block-diagonal orthogonal matrix, so the two-sided update is applied block
+// by block: for rotation pairs (a, b) the 2 x 2 block H_ab becomes
+// A_a H_ab A_b^T, every element read and written once per round.  The
+// eigenvectors accumulate as rows of U^T (row operations, float4 wide).
 __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const double *__restrict__ Hin, int b,
                                                                 double *__restrict__ theta,
                                                                 float *__restrict__ Uout,
                                                                 int max_sweeps) {
     extern __shared__ float sm[];
-    const int ld = b + 1;
-    float *H = sm;                 // [b][ld]
-    float *U = sm + b * ld;        // [b][ld]
+    const int B = (b + 1) & ~1;   // even size (index b is a zero dummy when b is odd)
+    const int half = B / 2;
+    const int ld = B + 1;
+    const int ldu = (B + 3) & ~3;
+    float *H = sm;                 // [B][ld]
+    float *Ut = sm + ((B * ld + 3) & ~3);  // [B][ldu], 16-byte aligned rows
     __shared__ float cs[kJacobiMax / 2 + 1], sn[kJacobiMax / 2 + 1];
     __shared__ int pp[kJacobiMax / 2 + 1], qq[kJacobiMax / 2 + 1];
     __shared__ float red[kJacobiThreads / 32][2];
     __shared__ int s_done;
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int i = tid >> 5; i < b; i += nt >> 5)
-        for (int j = tid & 31; j < b; j += 32) {
-            H[i * ld + j] = (float)(0.5 * (Hin[i * b + j] + Hin[j * b + i]));
-            U[i * ld + j] = (i == j) ? 1.0f : 0.0f;
-        }
-    const int B = (b + 1) & ~1;   // even number of players (index b is a dummy when b is odd)
-    const int half = B / 2;
     const int lx = tid & 31, wy = tid >> 5, nwy = nt >> 5;
+    for (int i = wy; i < B; i += nwy)
+        for (int j = lx; j < B; j += 32) {
+            H[i * ld + j] = (i < b && j < b) ? (float)(0.5 * (Hin[i * b + j] + Hin[j * b + i])) : 0.0f;
+            Ut[i * ldu + j] = (i == j) ? 1.0f : 0.0f;
+        }
     float prev_off = 3.0e38f;
     __syncthreads();
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
@@ -360,47 +367,49 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const double *__
                 else { p = (r + tid) % (B - 1); q = (r - tid + (B - 1)) % (B - 1); }
                 if (p > q) { int t = p; p = q; q = t; }
                 float c = 1.0f, s = 0.0f;
-                if (q < b) {
-                    const float apq = H[p * ld + q];
-                    const float app = H[p * ld + p], aqq = H[q * ld + q];
-                    // a rotation whose angle is below FP32 resolution of the
-                    // diagonal changes nothing: skip its updates
-                    if (fabsf(apq) > 1e-8f * fmaxf(fabsf(app), fabsf(aqq)) && apq != 0.0f) {
-                        const float tau = (aqq - app) / (2.0f * apq);
-                        const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
-                        c = rsqrtf(1.0f + t * t);
-                        s = t * c;
-                    } else {
-                        q = b;
-                    }
+                const float apq = H[p * ld + q];
+                const float app = H[p * ld + p], aqq = H[q * ld + q];
+                // a rotation whose angle is below FP32 resolution of the
+                // diagonal changes nothing: identity
+                if (q < b && fabsf(apq) > 1e-8f * fmaxf(fabsf(app), fabsf(aqq)) && apq != 0.0f) {
+                    const float tau = (aqq - app) / (2.0f * apq);
+                    const float t = (tau >= 0.0f ? 1.0f : -1.0f) / (fabsf(tau) + sqrtf(1.0f + tau * tau));
+                    c = rsqrtf(1.0f + t * t);
+                    s = t * c;
                 }
                 pp[tid] = p; qq[tid] = q; cs[tid] = c; sn[tid] = s;
             }
             __syncthreads();
-            // rows: H <- J^T H  (rotation k over warps, column j over lanes)
-            for (int k = wy; k < half; k += nwy) {
-                const int p = pp[k], q = qq[k];
-                if (q >= b) continue;
-                const float c = cs[k], s = sn[k];
-                for (int j = lx; j < b; j += 32) {
-                    const float hp = H[p * ld + j], hq = H[q * ld + j];
-                    H[p * ld + j] = c * hp - s * hq;
-                    H[q * ld + j] = s * hp + c * hq;
+            // H <- J^T H J, one 2 x 2 block (rotation a = row pair, b = column pair) per step
+            for (int ra = wy; ra < half; ra += nwy) {
+                const int pa = pp[ra], qa = qq[ra];
+                const float ca = cs[ra], sa = sn[ra];
+                const bool ida = sa == 0.0f;
+                for (int rb = lx; rb < half; rb += 32) {
+                    const float sb = sn[rb];
+                    if (ida && sb == 0.0f) continue;
+                    const int pb = pp[rb], qb = qq[rb];
+                    const float cb = cs[rb];
+                    const float h00 = H[pa * ld + pb], h01 = H[pa * ld + qb];
+                    const float h10 = H[qa * ld + pb], h11 = H[qa * ld + qb];
+                    const float t00 = ca * h00 - sa * h10, t01 = ca * h01 - sa * h11;
+                    const float t10 = sa * h00 + ca * h10, t11 = sa * h01 + ca * h11;
+                    H[pa * ld + pb] = cb * t00 - sb * t01;
+                    H[pa * ld + qb] = sb * t00 + cb * t01;
+                    H[qa * ld + pb] = cb * t10 - sb * t11;
+                    H[qa * ld + qb] = sb * t10 + cb * t11;
                 }
-            }
-            __syncthreads();
-            // columns: H <- H J, U <- U J  (row i over warps, rotation k over lanes)
-            for (int i = wy; i < b; i += nwy) {
-                for (int k = lx; k < half; k += 32) {
-                    const int p = pp[k], q = qq[k];
-                    if (q >= b) continue;
-                    const float c = cs[k], s = sn[k];
-                    const float hp = H[i * ld + p], hq = H[i * ld + q];
-                    H[i * ld + p] = c * hp - s * hq;
-                    H[i * ld + q] = s * hp + c * hq;
-                    const float up = U[i * ld + p], uq = U[i * ld + q];
-                    U[i * ld + p] = c * up - s * uq;
-                    U[i * ld + q] = s * up + c * uq;
+                // U^T rows pa, qa (the same rotation as H's rows)
+                if (!ida) {
+                    float4 *up = reinterpret_cast<float4 *>(Ut + pa * ldu);
+                    float4 *uq = reinterpret_cast<float4 *>(Ut + qa * ldu);
+                    for (int v = lx; v < ldu / 4; v += 32) {
+                        const float4 x = up[v], y = uq[v];
+                        up[v] = make_float4(ca * x.x - sa * y.x, ca * x.y - sa * y.y, ca * x.z - sa * y.z,
+                                            ca * x.w - sa * y.w);
+                        uq[v] = make_float4(sa * x.x + ca * y.x, sa * x.y + ca * y.y, sa * x.z + ca * y.z,
+                                            sa * x.w + ca * y.w);
+                    }
                 }
             }
             __syncthreads();
@@ -430,16 +439,17 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const double *__
         __syncthreads();
         if (s_done) break;
     }
-    // sort descending (ties by index) and write out
-    for (int c = tid; c < b; c += nt) {
+    // sort descending (ties by index) and write out: U column `rank` = U^T row c
+    for (int c = wy; c < b; c += nwy) {
         const float tc = H[c * ld + c];
         int rank = 0;
-        for (int o = 0; o < b; ++o) {
+        for (int o = lx; o < b; o += 32) {
             const float to = H[o * ld + o];
             rank += (to > tc) || (to == tc && o < c);
         }
-        theta[rank] = (double)tc;
-        for (int i = 0; i < b; ++i) Uout[i * b + rank] = U[i * ld + c];
+        for (int o = 16; o > 0; o >>= 1) rank += __shfl_xor_sync(0xffffffffu, rank, o);
+        if (lx == 0) theta[rank] = (double)tc;
+        for (int i = lx; i < b; i += 32) Uout[i * b + rank] = Ut[c * ldu + i];
     }
 }
 
@@ -582,11 +592,16 @@ void embed_gemm(const float *X, int64_t ldx, int64_t n, int d, const float *A, i
     }
 }
 
+static size_t jacobi_smem(int b) {
+    const size_t B = (size_t)((b + 1) & ~1);
+    return (B * (B + 1) + B * ((B + 3) & ~(size_t)3)) * sizeof(float) + 16;
+}
+
 void linalg_init() {
     const size_t b = kJacobiMax;
     set_max_dyn_smem((const void *)cholesky_kernel, (int)(b * (b + 1) * sizeof(double)));
     set_max_dyn_smem((const void *)trsm_rows_kernel, (int)((b * b + b * kTrsmCols) * sizeof(float)));
-    set_max_dyn_smem((const void *)jacobi_kernel, (int)(2 * b * (b + 1) * sizeof(float)));
+    set_max_dyn_smem((const void *)jacobi_kernel, (int)(jacobi_smem(kJacobiMax)));
     set_max_dyn_smem((const void *)trsm_warp_kernel, (int)(b * (b + 1) * sizeof(float)));
 }
 
@@ -655,7 +670,7 @@ void trsm_rows(const double *R, int b, float *V, int64_t ldv, int d, cudaStream_
 
 void jacobi_eig(const double *H, int b, double *theta, float *U, int max_sweeps, cudaStream_t st) {
     if (b > kJacobiMax) fail(ADAGIO_E_INVALID_ARG, "internal: Jacobi block %d > %d", b, kJacobiMax);
-    const size_t smem = (size_t)2 * b * (b + 1) * sizeof(float);
+    const size_t smem = jacobi_smem(b);
     set_max_dyn_smem((const void *)jacobi_kernel, (int)smem);
     jacobi_kernel<<<1, kJacobiThreads, smem, st>>>(H, b, theta, U, max_sweeps);
     ADAGIO_CHECK_LAUNCH();
