@@ -116,10 +116,11 @@ __device__ __forceinline__ bool better_max(float m1, int i1, int j1, float m2, i
 }
 
 // Block-wide reduction of per-thread statistics into one CertPartial slot.
-// `s_hist` holds per-thread histograms laid out [bin][thread] (u32), so both
-// the per-pair increment and this fold are bank-conflict free.  Must be
-// called by every thread of the block; ends with a __syncthreads().
-template <int NT>
+// `s_hist` holds HS histogram slots per bin laid out [bin][slot] (u32; one
+// slot per thread when HS = NT, one per warp when HS = NT / 32), so both the
+// per-pair increment and this fold are bank-conflict free.  Must be called by
+// every thread of the block; ends with a __syncthreads().
+template <int NT, int HS = NT>
 __device__ void write_partial(CertPartial *dst, const unsigned *s_hist, unsigned long long pairs,
                               unsigned long long viol, unsigned long long over,
                               unsigned long long queued, unsigned long long degen, double sum,
@@ -154,7 +155,7 @@ __device__ void write_partial(CertPartial *dst, const unsigned *s_hist, unsigned
     if (threadIdx.x < kBins) r_h[threadIdx.x] = 0;
     __syncthreads();
     for (int b = 0; b < kBins; ++b) {
-        unsigned long long v = s_hist[b * NT + threadIdx.x];
+        unsigned long long v = threadIdx.x < HS ? s_hist[b * HS + threadIdx.x] : 0u;
         for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
         if (lane == 0 && v) atomicAdd(&r_h[b], v);
     }

@@ -66,6 +66,24 @@ __device__ __forceinline__ DF warp_sum(DF v) {
     return v;
 }
 
+// acc += sum over this lane's elements k of (a_k - b_k)^2, four independent
+// double-float chains so the loads of consecutive elements overlap
+__device__ __forceinline__ DF sq_dist_lanes(const float *__restrict__ a, const float *__restrict__ b,
+                                            int n, int lane) {
+    DF c0{0.0f, 0.0f}, c1{0.0f, 0.0f}, c2{0.0f, 0.0f}, c3{0.0f, 0.0f};
+    int k = lane;
+    for (; k + 96 < n; k += 128) {
+        const float a0 = __ldg(a + k), a1 = __ldg(a + k + 32), a2 = __ldg(a + k + 64), a3 = __ldg(a + k + 96);
+        const float b0 = __ldg(b + k), b1 = __ldg(b + k + 32), b2 = __ldg(b + k + 64), b3 = __ldg(b + k + 96);
+        add_sq_diff(c0, a0, b0);
+        add_sq_diff(c1, a1, b1);
+        add_sq_diff(c2, a2, b2);
+        add_sq_diff(c3, a3, b3);
+    }
+    for (; k < n; k += 32) add_sq_diff(c0, __ldg(a + k), __ldg(b + k));
+    return df_add(df_add(c0, c1), df_add(c2, c3));
+}
+
 __global__ void __launch_bounds__(RT) recompute_kernel(const float *__restrict__ X, int64_t ldx,
                                                         int d, const float *__restrict__ Y,
                                                         int64_t ldy, int m,
@@ -73,25 +91,22 @@ __global__ void __launch_bounds__(RT) recompute_kernel(const float *__restrict__
                                                         const unsigned long long *__restrict__ qcount,
                                                         unsigned long long qcap, CertConst cc,
                                                         CertPartial *__restrict__ partials) {
-    extern __shared__ unsigned s_hist[];  // [kBins][RT]
-    const int tid = threadIdx.x, lane = tid & 31;
-    for (int b = 0; b < kBins; ++b) s_hist[b * RT + tid] = 0;
+    constexpr int NW = RT / 32;
+    __shared__ unsigned s_hist[kBins * NW];  // [bin][warp]: lane 0 of each warp counts
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int e = tid; e < kBins * NW; e += RT) s_hist[e] = 0;
     __syncthreads();
     const unsigned long long qlen = min(*qcount, qcap);
-    const long long warps = (long long)gridDim.x * (RT / 32);
+    const long long warps = (long long)gridDim.x * NW;
     unsigned long long npairs = 0, nviol = 0, nover = 0, ndeg = 0;
     double sum = 0.0;
     float mx = -1.0f;
     int ai = 0x7fffffff, aj = 0x7fffffff;
     const double lo = cc.lo, span = (double)cc.hi - (double)cc.lo;
-    for (long long q = (long long)blockIdx.x * (RT / 32) + (tid >> 5); q < (long long)qlen;
-         q += warps) {
+    for (long long q = (long long)blockIdx.x * NW + warp; q < (long long)qlen; q += warps) {
         const int2 pr = queue[q];
-        const float *xi = X + (int64_t)pr.x * ldx, *xj = X + (int64_t)pr.y * ldx;
-        const float *yi = Y + (int64_t)pr.x * ldy, *yj = Y + (int64_t)pr.y * ldy;
-        DF ax{0.0f, 0.0f}, ay{0.0f, 0.0f};
-        for (int k = lane; k < d; k += 32) add_sq_diff(ax, xi[k], xj[k]);
-        for (int k = lane; k < m; k += 32) add_sq_diff(ay, yi[k], yj[k]);
+        DF ax = sq_dist_lanes(X + (int64_t)pr.x * ldx, X + (int64_t)pr.y * ldx, d, lane);
+        DF ay = sq_dist_lanes(Y + (int64_t)pr.x * ldy, Y + (int64_t)pr.y * ldy, m, lane);
         ax = warp_sum(ax);
         ay = warp_sum(ay);
         if (lane == 0) {
@@ -109,7 +124,7 @@ __global__ void __launch_bounds__(RT) recompute_kernel(const float *__restrict__
                 } else {
                     int b = (int)floor((delta - lo) / span * (double)kBins);
                     b = min(max(b, 0), kBins - 1);
-                    s_hist[b * RT + tid] += 1u;
+                    s_hist[b * NW + warp] += 1u;
                 }
                 const float df = (float)delta;
                 if (better_max(df, pr.x, pr.y, mx, ai, aj)) { mx = df; ai = pr.x; aj = pr.y; }
@@ -117,45 +132,90 @@ __global__ void __launch_bounds__(RT) recompute_kernel(const float *__restrict__
         }
     }
     __syncthreads();
-    write_partial<RT>(partials + blockIdx.x, s_hist, npairs, nviol, nover, 0ull, ndeg, sum, 0.0,
-                      mx, 0.0f, ai, aj);
+    write_partial<RT, NW>(partials + blockIdx.x, s_hist, npairs, nviol, nover, 0ull, ndeg, sum, 0.0,
+                          mx, 0.0f, ai, aj);
 }
 
-__global__ void finalize_kernel(const CertPartial *__restrict__ fast, int nfast,
-                                const CertPartial *__restrict__ rec, int nrec,
-                                const unsigned long long *__restrict__ qcount,
-                                const unsigned *__restrict__ flags, const int *__restrict__ status,
-                                const int *__restrict__ stop_flag, CertDevResult *__restrict__ out) {
-    const int tid = threadIdx.x;  // 64 threads: one per bin
-    unsigned long long h = 0;
-    for (int c = 0; c < nfast; ++c) h += fast[c].hist[tid];
-    for (int c = 0; c < nrec; ++c) h += rec[c].hist[tid];
-    out->hist[tid] = h;
-    if (tid == 0) {
-        unsigned long long fp = 0, qd = 0, rp = 0, dg = 0, vi = 0, ov = 0;
-        double s = 0.0, bs = 0.0;
-        float mx = -1.0f, mxb = 0.0f;
-        int ai = 0x7fffffff, aj = 0x7fffffff;
-        for (int c = 0; c < nfast; ++c) {
-            const CertPartial &p = fast[c];
-            fp += p.pairs; qd += p.queued; vi += p.violations; ov += p.overflow;
-            s += p.sum; bs += p.bound_sum;
+// Merges the partials of both paths.  Every sum runs over a fixed assignment
+// of partials to threads and a fixed reduction tree, so the result does not
+// depend on scheduling.
+constexpr int FT = 1024;
+__global__ void __launch_bounds__(FT) finalize_kernel(const CertPartial *__restrict__ fast, int nfast,
+                                                      const CertPartial *__restrict__ rec, int nrec,
+                                                      const unsigned long long *__restrict__ qcount,
+                                                      const unsigned *__restrict__ flags,
+                                                      const int *__restrict__ status,
+                                                      const int *__restrict__ stop_flag,
+                                                      CertDevResult *__restrict__ out) {
+    constexpr int SL = FT / kBins;  // slices per bin
+    __shared__ unsigned long long s_h[SL][kBins];
+    __shared__ unsigned long long s_u[6][FT / 32];
+    __shared__ double s_d[2][FT / 32];
+    __shared__ float s_m[2][FT / 32];
+    __shared__ int s_i[2][FT / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int ntot = nfast + nrec;
+    {
+        const int bin = tid % kBins, slice = tid / kBins;
+        unsigned long long h = 0;
+        for (int c = slice; c < ntot; c += SL) h += c < nfast ? fast[c].hist[bin] : rec[c - nfast].hist[bin];
+        s_h[slice][bin] = h;
+    }
+    unsigned long long u[6] = {0, 0, 0, 0, 0, 0};  // fast pairs, queued, recomputed, degenerate, violations, overflow
+    double s = 0.0, bs = 0.0;
+    float mx = -1.0f, mxb = 0.0f;
+    int ai = 0x7fffffff, aj = 0x7fffffff;
+    for (int c = tid; c < ntot; c += FT) {
+        const bool f = c < nfast;
+        const CertPartial &p = f ? fast[c] : rec[c - nfast];
+        if (f) {
+            u[0] += p.pairs; u[1] += p.queued;
+            bs += p.bound_sum;
             mxb = fmaxf(mxb, p.max_bound);
-            if (better_max(p.max, p.argmax_i, p.argmax_j, mx, ai, aj)) {
-                mx = p.max; ai = p.argmax_i; aj = p.argmax_j;
-            }
+        } else {
+            u[2] += p.pairs; u[3] += p.degenerate;
         }
-        for (int c = 0; c < nrec; ++c) {
-            const CertPartial &p = rec[c];
-            rp += p.pairs; dg += p.degenerate; vi += p.violations; ov += p.overflow;
-            s += p.sum;
-            if (better_max(p.max, p.argmax_i, p.argmax_j, mx, ai, aj)) {
-                mx = p.max; ai = p.argmax_i; aj = p.argmax_j;
-            }
+        u[4] += p.violations; u[5] += p.overflow;
+        s += p.sum;
+        if (better_max(p.max, p.argmax_i, p.argmax_j, mx, ai, aj)) { mx = p.max; ai = p.argmax_i; aj = p.argmax_j; }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) u[q] += __shfl_xor_sync(0xffffffffu, u[q], o);
+        s += __shfl_xor_sync(0xffffffffu, s, o);
+        bs += __shfl_xor_sync(0xffffffffu, bs, o);
+        mxb = fmaxf(mxb, __shfl_xor_sync(0xffffffffu, mxb, o));
+        const float om = __shfl_xor_sync(0xffffffffu, mx, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, ai, o);
+        const int oj = __shfl_xor_sync(0xffffffffu, aj, o);
+        if (better_max(om, oi, oj, mx, ai, aj)) { mx = om; ai = oi; aj = oj; }
+    }
+    if (lane == 0) {
+#pragma unroll
+        for (int q = 0; q < 6; ++q) s_u[q][warp] = u[q];
+        s_d[0][warp] = s; s_d[1][warp] = bs;
+        s_m[0][warp] = mx; s_m[1][warp] = mxb; s_i[0][warp] = ai; s_i[1][warp] = aj;
+    }
+    __syncthreads();
+    if (tid < kBins) {
+        unsigned long long h = 0;
+        for (int sl = 0; sl < SL; ++sl) h += s_h[sl][tid];
+        out->hist[tid] = h;
+    }
+    if (tid == 0) {
+        unsigned long long t[6] = {0, 0, 0, 0, 0, 0};
+        double d0 = 0.0, d1 = 0.0;
+        float m = -1.0f, mb = 0.0f;
+        int bi = 0x7fffffff, bj = 0x7fffffff;
+        for (int w = 0; w < FT / 32; ++w) {
+            for (int q = 0; q < 6; ++q) t[q] += s_u[q][w];
+            d0 += s_d[0][w]; d1 += s_d[1][w];
+            mb = fmaxf(mb, s_m[1][w]);
+            if (better_max(s_m[0][w], s_i[0][w], s_i[1][w], m, bi, bj)) { m = s_m[0][w]; bi = s_i[0][w]; bj = s_i[1][w]; }
         }
-        out->fast_pairs = fp; out->queued = qd; out->recomputed = rp; out->degenerate = dg;
-        out->violations = vi; out->overflow = ov; out->sum = s; out->bound_sum = bs;
-        out->max = mx; out->max_bound = mxb; out->argmax_i = ai; out->argmax_j = aj;
+        out->fast_pairs = t[0]; out->queued = t[1]; out->recomputed = t[2]; out->degenerate = t[3];
+        out->violations = t[4]; out->overflow = t[5]; out->sum = d0; out->bound_sum = d1;
+        out->max = m; out->max_bound = mb; out->argmax_i = bi; out->argmax_j = bj;
         out->flags = *flags;
         out->status = status ? *status : 0;
         out->stopped = stop_flag ? *stop_flag : 0;
@@ -165,26 +225,20 @@ __global__ void finalize_kernel(const CertPartial *__restrict__ fast, int nfast,
 
 }  // namespace
 
-void recompute_init() {
-    set_max_dyn_smem((const void *)recompute_kernel, (int)((size_t)kBins * RT * sizeof(unsigned)));
-}
+void recompute_init() {}
 
 void launch_recompute(const float *X, int64_t ldx, int d, const float *Y, int64_t ldy, int m,
                       const int2 *queue, const unsigned long long *qcount,
                       unsigned long long qcap, CertConst cc, CertPartial *partials, int grid,
                       cudaStream_t st) {
-    const size_t smem = (size_t)kBins * RT * sizeof(unsigned);
-    set_max_dyn_smem((const void *)recompute_kernel, (int)smem);
-    recompute_kernel<<<grid, RT, smem, st>>>(X, ldx, d, Y, ldy, m, queue, qcount, qcap, cc,
-                                            partials);
+    recompute_kernel<<<grid, RT, 0, st>>>(X, ldx, d, Y, ldy, m, queue, qcount, qcap, cc, partials);
     ADAGIO_CHECK_LAUNCH();
 }
 
 void launch_finalize(const CertPartial *fast, int nfast, const CertPartial *rec, int nrec,
                      const unsigned long long *qcount, const unsigned *flags, const int *status,
                      const int *stop_flag, CertDevResult *out, cudaStream_t st) {
-    finalize_kernel<<<1, kBins, 0, st>>>(fast, nfast, rec, nrec, qcount, flags, status, stop_flag,
-                                         out);
+    finalize_kernel<<<1, FT, 0, st>>>(fast, nfast, rec, nrec, qcount, flags, status, stop_flag, out);
     ADAGIO_CHECK_LAUNCH();
 }
 
