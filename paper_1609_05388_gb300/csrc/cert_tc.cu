@@ -45,13 +45,16 @@ namespace {
 constexpr int kEpiWarps = 8;                                // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;               // producer, MMA, epilogue
 constexpr int kStages = 3;
-constexpr int kSlots = 4;                                   // TMEM chunk accumulators
+constexpr int kSlots = 2;                                   // TMEM chunk accumulators
 constexpr int kTile = 128;
 constexpr int kKStep = 64;                                  // fp16 elements per stage row
 constexpr int kEpiCols = 64;                                // columns per epilogue warp
 constexpr uint32_t kPlaneBytes = kTile * kKStep * 2;        // 16 KB
 constexpr uint32_t kStageBytes = 4 * kPlaneBytes;           // 64 KB
-constexpr uint32_t kTmemCols = kSlots * kTile;              // 512
+constexpr uint32_t kStageCol = kSlots * kTile;              // finished Gram sums (gx | gy)
+constexpr uint32_t kTmemCols = kStageCol + 2 * kTile;       // 512
+static_assert(kTmemCols == 512, "TMEM holds 512 columns");
+constexpr int kPiece = 16;                                  // columns classified per step
 constexpr int kHistFlushTiles = 1000;                       // u16 counters: <= 64 per tile
 // per-thread histogram: two 16-bit bin counters per 32-bit word
 constexpr int kHistWords = kBins / 2;
@@ -81,9 +84,12 @@ struct SmemLayout {
     static constexpr uint32_t bars = hist + kHistWords * 32 * kEpiWarps * 4;
     static constexpr uint32_t cmd = bars + 256;                               // int [16]
     static constexpr uint32_t tmem_ptr = cmd + 64;
-    static constexpr uint32_t total = tmem_ptr + 16;
+    static constexpr uint32_t totals = tmem_ptr + 16;                         // WarpTotals [8]
+    static constexpr uint32_t total = totals + 64 * kEpiWarps;
 };
 constexpr size_t kSmemBytes = SmemLayout::total + 1024;   // + alignment slack
+static_assert(kSmemBytes <= 232448, "tile kernel exceeds the 227 KB shared-memory limit");
+static_assert(SmemLayout::totals % 8 == 0, "per-warp totals need 8-byte alignment");
 
 // ------------------------------------------------------------------ PTX glue
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -178,18 +184,45 @@ __device__ __forceinline__ void tc_commit(uint32_t bar) {
                  : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+// 16 consecutive TMEM columns of this warp's lane quarter into registers.
+// The wait is part of the same statement, so no use of the registers can be
+// scheduled before the asynchronous load has completed.
+__device__ __forceinline__ void tmem_ld16_wait(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
 }
 
-__device__ __forceinline__ void tmem_wait_ld() {
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+// Two 16-column pieces (at ta and tb) with one wait.
+__device__ __forceinline__ void tmem_ld16x2_wait(uint32_t ta, uint32_t tb, uint32_t (&a)[16],
+                                                 uint32_t (&b)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%32];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]), "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15])
+        : "r"(ta), "r"(tb)
+        : "memory");
+}
+
+// 16 registers into 16 consecutive TMEM columns of this warp's lane quarter.
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
+        :
+        : "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_wait_st() {
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 // Folds this warp's 32 per-thread counters of every bin into its partial
@@ -216,51 +249,89 @@ __device__ __forceinline__ void fold_hist(uint32_t *s_hist, int ew, CertPartial 
     __syncwarp();
 }
 
-// Fast classification of one pair from its Gram entries (Eq. 2), branch-free
-// (every pair of the unrolled tile row takes the same instruction path, so
-// the compiler interleaves independent pairs), two MUFU operations per pair.
-// With p = dx2 dy2 and s = sqrt(p):
-//   rho = sqrt(dy2 / dx2) = dy2 / s,   delta = |rho - 1| = |dy2 - dx2| / (dx2 + s)
-// (the second form has no cancellation).  The Gram error bounds are
-// ex = q4x_i q4x_j + cx (n2x_i + n2x_j), likewise ey, and the distortion error
-// is at most B = 0.55 rho (ex / dx2 + ey / dy2) + 1e-6 delta + 1e-9 (the last
-// terms cover the approximate reciprocal square root and reciprocal).
-// queue = the fast result cannot be used: the Gram values are too
-// ill-conditioned to bound (or not finite), B exceeds the maximum's
-// tolerance, or B > 1e-6 and a histogram edge or eps lies within B of delta.
-struct PairOut {
-    float delta, bound, t;
-    bool queue;
-};
-
 struct EpiConst {
     float m2sx, m2sy;      // -2 / scale^2 of the split planes
-    float cx, cy;
-    float inv_w, t0;       // t = delta * inv_w + t0 = (delta - lo) / w
-    float tmin;            // lowest real histogram edge index (1 when lo <= 0)
+    float cx, cy;          // bound coefficients of (n2_i + n2_j) per side
+    float inv_w, t0, w;    // t = delta * inv_w + t0 = (delta - lo) / w
     float eps;
 };
 
-__device__ __forceinline__ PairOut fast_pair(float gx, float gy, const float4 &ri, const float4 &rj,
-                                             const EpiConst &k) {
-    PairOut o;
-    const float sx = ri.x + rj.x, sy = ri.y + rj.y;
-    const float dx2 = fmaf(k.m2sx, gx, sx), dy2 = fmaf(k.m2sy, gy, sy);
-    const float ex = fmaf(ri.z, rj.z, k.cx * sx), ey = fmaf(ri.w, rj.w, k.cy * sy);
-    const bool cond = (dx2 > 8.0f * ex) & (dy2 > 8.0f * ey);
-    const float pp = dx2 * dy2;
-    const float rs = rsqrtf(pp);
-    const float sq = pp * rs;                       // sqrt(dx2 dy2)
-    o.delta = __fdividef(fabsf(dy2 - dx2), dx2 + sq);
-    const float rho = dy2 * rs;
-    const float inv_p = rs * rs;                    // 1 / (dx2 dy2)
-    o.bound = fmaf(0.55f * rho * inv_p, fmaf(ex, dy2, ey * dx2), fmaf(1e-6f, o.delta, 1e-9f));
-    o.t = fmaf(o.delta, k.inv_w, k.t0);
-    const float tn = rintf(o.t);
-    const bool near_edge = (fabsf(o.t - tn) < o.bound * k.inv_w) & (tn >= k.tmin) & (tn <= (float)kBins);
-    const bool near_eps = fabsf(o.delta - k.eps) < o.bound;
-    o.queue = !cond | !(o.bound <= kMaxTol) | ((o.bound > kExempt) & (near_edge | near_eps));
-    return o;
+// Statistics one epilogue thread keeps over the pairs of one tile row.
+struct RowAcc {
+    float sum, bsum, mxb, mx;
+    int viol, over, certain, arg;
+};
+
+// Per-warp running totals of the epilogue, in shared memory (lane 0 owns them).
+struct WarpTotals {
+    unsigned long long violations, overflow, queued;
+    double sum, bound_sum;
+    float max, max_bound;
+    int argmax_i, argmax_j;
+};
+
+static_assert(sizeof(WarpTotals) <= 64, "per-warp totals exceed their shared-memory slot");
+
+// Classifies the kPiece pairs (i, j0 + c0 + c) of one tile row from their Gram
+// entries (Eq. 2), without data-dependent branches, so the compiler
+// interleaves the independent pairs.  With p = dx2 dy2 and r = 1/sqrt(p):
+//   delta = |sqrt(dy2 / dx2) - 1| = |dy2 - dx2| / (dx2 + p r)   (no cancellation)
+// The Gram error bounds are ex = q4x_i q4x_j + cx (n2x_i + n2x_j), likewise ey,
+// and the distortion error is at most
+//   B = 0.55 rho (ex / dx2 + ey / dy2) + 1e-6 delta + 1e-9,  rho = dy2 r,
+// written as 0.55 dy2 r^3 (ex dy2 + ey dx2) + ...; the last two terms cover
+// the approximate reciprocal square root and reciprocal.  The fast value is
+// used when the Gram values are well enough conditioned to bound
+// (dx2 > 8 ex and dy2 > 8 ey) and
+//   B <= min(1e-5, max(1e-6, distance of delta to the nearest bin edge or eps)),
+// i.e. B is within the maximum's tolerance, and either B <= 1e-6 or no edge
+// and not eps lies within B of delta; every other pair is flagged in qmask for
+// the exact recompute.  A NaN Gram entry (how the caller marks a column that
+// is not a real pair) fails the test: the pair is flagged and adds nothing to
+// the statistics, and the caller clears its qmask bit.
+template <bool DUMP>
+__device__ __forceinline__ void classify_piece(const float (&gx)[kPiece], const float (&gy)[kPiece],
+                                               const float4 ri, const float4 *__restrict__ rsj,
+                                               int c0, const EpiConst &k, uint32_t *hrow, RowAcc &a,
+                                               unsigned long long &qmask, float4 *dump_row) {
+#pragma unroll
+    for (int c = 0; c < kPiece; ++c) {
+        const float4 rj = __ldg(rsj + c);
+        const float sx = ri.x + rj.x, sy = ri.y + rj.y;
+        const float dx2 = fmaf(k.m2sx, gx[c], sx), dy2 = fmaf(k.m2sy, gy[c], sy);
+        const float ex = fmaf(ri.z, rj.z, k.cx * sx), ey = fmaf(ri.w, rj.w, k.cy * sy);
+        if (DUMP) dump_row[c] = make_float4(dx2, dy2, ex, ey);
+        const float pp = dx2 * dy2;
+        const float r = rsqrtf(pp);
+        const float delta = __fdividef(fabsf(dy2 - dx2), fmaf(pp, r, dx2));
+        const float B = fmaf((0.55f * dy2) * (r * r * r), fmaf(ex, dy2, ey * dx2),
+                             fmaf(1e-6f, delta, 1e-9f));
+        const float t = fmaf(delta, k.inv_w, k.t0);
+        // distance to the nearest real edge: edges lie at integer t in [0, 64]
+        const float tc = fminf(fmaxf(t, -0.5f), (float)kBins + 0.5f);
+        const float dedge = fabsf(tc - rintf(tc)) * k.w;
+        const float lim = fminf(kMaxTol, fmaxf(kExempt, fminf(dedge, fabsf(delta - k.eps))));
+        const float cond = fminf(fmaf(-8.0f, ex, dx2), fmaf(-8.0f, ey, dy2));
+        const bool ok = (cond > 0.0f) & (B <= lim);
+        qmask |= ok ? 0ull : (1ull << (c0 + c));
+        const bool in_range = (t >= 0.0f) & (t < (float)kBins);
+        const bool binned = ok & in_range;
+        const int bin = (int)t;
+        // pairs not counted in a bin add 0 (to bin 0's word)
+        atomicAdd(hrow + (binned ? (bin >> 1) : 0) * (32 * kEpiWarps),
+                  binned ? (1u << ((bin & 1) << 4)) : 0u);
+        const bool viol = ok & (delta > k.eps);
+        a.over += (ok & !in_range) ? 1 : 0;
+        a.viol += viol ? 1 : 0;
+        a.certain += (viol & (delta - B > k.eps)) ? 1 : 0;
+        const float bok = ok ? B : 0.0f;
+        a.sum += ok ? delta : 0.0f;
+        a.bsum += bok;
+        a.mxb = fmaxf(a.mxb, bok);
+        const bool better = ok & (delta > a.mx);
+        a.mx = better ? delta : a.mx;
+        a.arg = better ? c0 + c : a.arg;
+    }
 }
 
 // ---------------------------------------------------------------- the kernel
@@ -462,10 +533,6 @@ __global__ void __launch_bounds__(kThreads, 1)
         CertPartial *mine = p.partials + (size_t)blockIdx.x * kEpiWarps + ew;
         int slot = 0;
         uint32_t sphase = 0;
-        unsigned long long nviol = 0, nqueued = 0, nover = 0;
-        double sum = 0.0, bsum = 0.0;
-        float mx = -1.0f, mxb_all = 0.0f;
-        int ai = 0x7fffffff, aj = 0x7fffffff;
         EpiConst k;
         {
             const float sx = *p.scale_x, sy = *p.scale_y;
@@ -475,10 +542,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             k.cy = p.cy;
             k.inv_w = p.cc.inv_w;
             k.t0 = -p.cc.lo * p.cc.inv_w;
-            k.tmin = p.cc.lo_is_floor ? 1.0f : 0.0f;
+            k.w = p.cc.w;
             k.eps = p.cc.eps;
         }
-        const float lo = p.cc.lo, hi_edge = p.cc.hi, eps = p.cc.eps;
+        WarpTotals *wt = reinterpret_cast<WarpTotals *>(smem + SmemLayout::totals) + ew;
+        if (lane == 0) {
+            wt->violations = wt->overflow = wt->queued = 0;
+            wt->sum = wt->bound_sum = 0.0;
+            wt->max = -1.0f;
+            wt->max_bound = 0.0f;
+            wt->argmax_i = wt->argmax_j = 0x7fffffff;
+        }
         uint32_t *hrow = s_hist + ew * 32 + lane;  // bins 2w, 2w+1 at hrow[w * 256]
         int tiles_since_flush = 0;
         long long t = blockIdx.x;               // the producer's static tile sequence
@@ -502,10 +576,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const uint32_t ta = tmem_base + lane_addr + (uint32_t)(slot * kTile + h * kEpiCols);
                 const bool is_y = ks < p.ky_steps;
 #pragma unroll
-                for (int qd = 0; qd < 4; ++qd) {
+                for (int qd = 0; qd < kEpiCols / 16; ++qd) {
                     uint32_t v[16];
-                    tmem_ld16(ta + qd * 16, v);
-                    tmem_wait_ld();
+                    tmem_ld16_wait(ta + qd * 16, v);
                     if (is_y) {
 #pragma unroll
                         for (int c = 0; c < 16; ++c) gy[qd * 16 + c] += __uint_as_float(v[c]);
@@ -522,95 +595,118 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             if (!ok) break;
-            // ---- classify the 64 pairs of this thread (no data-dependent branch)
+            // ---- park the finished sums in this warp's staging columns, so the
+            // classification below holds only one 16-column piece in registers
+            // (the compiler can then interleave many independent pairs)
+            const uint32_t sx_addr = tmem_base + lane_addr + kStageCol + (uint32_t)(h * kEpiCols);
+            const uint32_t sy_addr = sx_addr + kTile;
+#pragma unroll
+            for (int qd = 0; qd < kEpiCols / 16; ++qd) {
+                uint32_t vx[16], vy[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                    vx[c] = __float_as_uint(gx[qd * 16 + c]);
+                    vy[c] = __float_as_uint(gy[qd * 16 + c]);
+                }
+                tmem_st16(sx_addr + qd * 16, vx);
+                tmem_st16(sy_addr + qd * 16, vy);
+            }
+            tmem_wait_st();
+            // ---- classify the 64 pairs of this thread
             const uint32_t packed = p.sched[t];
             const int I = (int)(packed >> 16), J = (int)(packed & 0xFFFF);
             const int i = I * kTile + r;
             const float4 ri = __ldg(p.rs + i);
             const int j0 = J * kTile + h * kEpiCols;
-            const bool full = (I < J) && (J * kTile + kTile <= p.n);  // every pair valid
-            float tsum = 0.0f, tbsum = 0.0f, tmx = -1.0f, tmxb = 0.0f, tmdb = -1.0f;
-            int tviol = 0, tover = 0, targ = 0;
-            unsigned long long qmask = 0ull;
-#pragma unroll
-            for (int c = 0; c < kEpiCols; ++c) {
-                const int j = j0 + c;
-                const float4 rj = __ldg(p.rs + j);
-                const bool valid = full | ((i < j) & (j < p.n));
-                const PairOut o = fast_pair(gx[c], gy[c], ri, rj, k);
-                if (DUMP && p.dump && t < p.dump_tiles) {
-                    float4 w;
-                    w.x = fmaf(k.m2sx, gx[c], ri.x + rj.x);
-                    w.y = fmaf(k.m2sy, gy[c], ri.y + rj.y);
-                    w.z = fmaf(ri.z, rj.z, p.cx * (ri.x + rj.x));
-                    w.w = fmaf(ri.w, rj.w, p.cy * (ri.y + rj.y));
-                    p.dump[(size_t)t * kTile * kTile + r * kTile + h * kEpiCols + c] = w;
+            RowAcc acc{0.0f, 0.0f, 0.0f, -1.0f, 0, 0, 0, 0};
+            unsigned long long qmask = 0ull, vmask = ~0ull;
+            const bool full = (I < J) && (J * kTile + kTile <= p.n);
+            if (!full) {
+                // diagonal or ragged tile: columns that are not pairs i < j < n
+                // get a NaN Gram entry and their queue bit is cleared below
+                for (int c = 0; c < kEpiCols; ++c) {
+                    const int j = j0 + c;
+                    if (!((i < j) & (j < p.n))) vmask &= ~(1ull << c);
                 }
-                const bool okp = valid & !o.queue;
-                qmask |= (valid & o.queue) ? (1ull << c) : 0ull;
-                const bool in_range = (o.delta >= lo) & (o.delta < hi_edge);
-                // pairs not counted in a bin add 0 (to bin 0's word)
-                const int bin = (okp & in_range) ? min((int)o.t, kBins - 1) : 0;
-                const uint32_t inc = (okp & in_range) ? ((bin & 1) ? 0x10000u : 1u) : 0u;
-                atomicAdd(hrow + (bin >> 1) * (32 * kEpiWarps), inc);
-                tover += (okp & !in_range) ? 1 : 0;
-                tviol += (okp & (o.delta > eps)) ? 1 : 0;
-                tsum += okp ? o.delta : 0.0f;
-                tbsum += okp ? o.bound : 0.0f;
-                tmxb = fmaxf(tmxb, okp ? o.bound : 0.0f);
-                tmdb = fmaxf(tmdb, okp ? o.delta - o.bound : -1.0f);
-                const bool better = okp & (o.delta > tmx);
-                tmx = better ? o.delta : tmx;
-                targ = better ? c : targ;
             }
+            const bool dump = DUMP && p.dump && t < p.dump_tiles;
+#pragma unroll 1
+            for (int c0 = 0; c0 < kEpiCols; c0 += kPiece) {
+                uint32_t ux[kPiece], uy[kPiece];
+                tmem_ld16x2_wait(sx_addr + c0, sy_addr + c0, ux, uy);
+                float px[kPiece], py[kPiece];
+#pragma unroll
+                for (int c = 0; c < kPiece; ++c) {
+                    const bool valid = (vmask >> (c0 + c)) & 1ull;
+                    px[c] = valid ? __uint_as_float(ux[c]) : __int_as_float(0x7fc00000);
+                    py[c] = __uint_as_float(uy[c]);
+                }
+                if (dump) {
+                    float4 *drow = p.dump + (size_t)t * kTile * kTile + r * kTile + h * kEpiCols + c0;
+                    classify_piece<DUMP>(px, py, ri, p.rs + j0 + c0, c0, k, hrow, acc, qmask, drow);
+                } else {
+                    classify_piece<false>(px, py, ri, p.rs + j0 + c0, c0, k, hrow, acc, qmask, nullptr);
+                }
+            }
+            qmask &= vmask;
             // push the queued pairs of this tile (rare), warp-aggregated
-            nqueued += __popcll(qmask);
+            int nq = __popcll(qmask);
             while (__any_sync(0xffffffffu, qmask != 0ull)) {
                 const bool has = qmask != 0ull;
                 const int c = has ? __ffsll((long long)qmask) - 1 : 0;
                 if (has) qmask &= qmask - 1;
                 queue_push(has, i, j0 + c, p.queue, p.qcount, p.qcap);
             }
-            nviol += (unsigned)tviol;
-            nover += (unsigned)tover;
-            sum += (double)tsum;
-            bsum += (double)tbsum;
-            mxb_all = fmaxf(mxb_all, tmxb);
-            if (tmx >= 0.0f && better_max(tmx, i, j0 + targ, mx, ai, aj)) {
-                mx = tmx;
-                ai = i;
-                aj = j0 + targ;
+            // fold this tile's statistics into the warp's partial (lane 0 owns it)
+            int aj_t = j0 + acc.arg, ai_t = i;
+            for (int o = 16; o > 0; o >>= 1) {
+                acc.viol += __shfl_xor_sync(0xffffffffu, acc.viol, o);
+                acc.over += __shfl_xor_sync(0xffffffffu, acc.over, o);
+                acc.certain += __shfl_xor_sync(0xffffffffu, acc.certain, o);
+                nq += __shfl_xor_sync(0xffffffffu, nq, o);
+                acc.sum += __shfl_xor_sync(0xffffffffu, acc.sum, o);
+                acc.bsum += __shfl_xor_sync(0xffffffffu, acc.bsum, o);
+                acc.mxb = fmaxf(acc.mxb, __shfl_xor_sync(0xffffffffu, acc.mxb, o));
+                const float om = __shfl_xor_sync(0xffffffffu, acc.mx, o);
+                const int oi = __shfl_xor_sync(0xffffffffu, ai_t, o);
+                const int oj = __shfl_xor_sync(0xffffffffu, aj_t, o);
+                if (better_max(om, oi, oj, acc.mx, ai_t, aj_t)) { acc.mx = om; ai_t = oi; aj_t = oj; }
             }
-            // a certain violation: delta - B > eps for some pair
-            if (p.stop_flag && tmdb > eps) atomicExch(p.stop_flag, 1);
+            if (lane == 0) {
+                wt->violations += (unsigned)acc.viol;
+                wt->overflow += (unsigned)acc.over;
+                wt->queued += (unsigned)nq;
+                wt->sum += (double)acc.sum;
+                wt->bound_sum += (double)acc.bsum;
+                wt->max_bound = fmaxf(wt->max_bound, acc.mxb);
+                if (acc.mx >= 0.0f && better_max(acc.mx, ai_t, aj_t, wt->max, wt->argmax_i, wt->argmax_j)) {
+                    wt->max = acc.mx;
+                    wt->argmax_i = ai_t;
+                    wt->argmax_j = aj_t;
+                }
+                // a certain violation: delta - B > eps for some pair
+                if (p.stop_flag && acc.certain > 0) atomicExch(p.stop_flag, 1);
+            }
             t += gridDim.x;
             if (++tiles_since_flush == kHistFlushTiles) {
                 tiles_since_flush = 0;
                 fold_hist(s_hist, ew, mine);
             }
         }
-        // ---- this warp's partial: histogram (with pairs and overflow) and
-        // the scalar statistics
+        // ---- this warp's partial: the rest of its histogram and its totals
         fold_hist(s_hist, ew, mine);
-        unsigned long long u[3] = {nviol, nqueued, nover};
-        for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-            for (int q = 0; q < 3; ++q) u[q] += __shfl_xor_sync(0xffffffffu, u[q], o);
-            sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
-            mxb_all = fmaxf(mxb_all, __shfl_xor_sync(0xffffffffu, mxb_all, o));
-            const float om = __shfl_xor_sync(0xffffffffu, mx, o);
-            const int oi = __shfl_xor_sync(0xffffffffu, ai, o);
-            const int oj = __shfl_xor_sync(0xffffffffu, aj, o);
-            if (better_max(om, oi, oj, mx, ai, aj)) { mx = om; ai = oi; aj = oj; }
-        }
         if (lane == 0) {
-            mine->violations = u[0]; mine->queued = u[1];
-            mine->overflow = u[2];
-            mine->pairs += u[2];   // fold_hist added the binned pairs
+            mine->violations = wt->violations;
+            mine->queued = wt->queued;
+            mine->overflow = wt->overflow;
+            mine->pairs += wt->overflow;  // fold_hist added the binned pairs
             mine->degenerate = 0;
-            mine->sum = sum; mine->bound_sum = bsum;
-            mine->max = mx; mine->max_bound = mxb_all; mine->argmax_i = ai; mine->argmax_j = aj;
+            mine->sum = wt->sum;
+            mine->bound_sum = wt->bound_sum;
+            mine->max = wt->max;
+            mine->max_bound = wt->max_bound;
+            mine->argmax_i = wt->argmax_i;
+            mine->argmax_j = wt->argmax_j;
         }
     }
 

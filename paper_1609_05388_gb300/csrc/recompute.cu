@@ -7,9 +7,14 @@
 // square exactly by an FMA-based TwoProduct, and the running sum is kept as
 // an unevaluated hi + lo pair (Dekker 1971; Knuth TAOCP vol. 2, 4.2.2).  The
 // relative error of the result is a few units of 2^-44, far below the 1e-6
-// classification threshold.  The distortion (Eq. 2) and its bin are then
-// evaluated in double precision.  A pair with ||x_i - x_j|| == 0 is counted
-// as degenerate.
+// classification threshold.  The distortion (Eq. 2) is then evaluated without
+// FP64 (slow on this GPU) in the cancellation-free form
+//     delta = |dy2 - dx2| / (dx2 + sqrt(dx2) sqrt(dy2))
+// with the difference dy2 - dx2 taken in double-float and one IEEE FP32
+// division and two square roots: its relative error is below 4 * 2^-24
+// (under 2.4e-7 absolute for delta <= 1), inside the 1e-6 band around the
+// bin edges and eps where the certificate allows a miscount.  A pair with
+// ||x_i - x_j|| == 0 is counted as degenerate.
 //
 // K10 merges the per-CTA partials of both paths in a fixed order, so the
 // result does not depend on scheduling (apart from the order of the queue).
@@ -54,6 +59,14 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
     r.hi = __fadd_rn(s, e);
     r.lo = __fsub_rn(e, __fsub_rn(r.hi, s));
     return r;
+}
+
+// a - b in double-float
+__device__ __forceinline__ DF df_sub(DF a, DF b) {
+    DF nb;
+    nb.hi = -b.hi;
+    nb.lo = -b.lo;
+    return df_add(a, nb);
 }
 
 __device__ __forceinline__ DF warp_sum(DF v) {
@@ -102,7 +115,6 @@ __global__ void __launch_bounds__(RT) recompute_kernel(const float *__restrict__
     double sum = 0.0;
     float mx = -1.0f;
     int ai = 0x7fffffff, aj = 0x7fffffff;
-    const double lo = cc.lo, span = (double)cc.hi - (double)cc.lo;
     for (long long q = (long long)blockIdx.x * NW + warp; q < (long long)qlen; q += warps) {
         const int2 pr = queue[q];
         DF ax = sq_dist_lanes(X + (int64_t)pr.x * ldx, X + (int64_t)pr.y * ldx, d, lane);
@@ -110,24 +122,26 @@ __global__ void __launch_bounds__(RT) recompute_kernel(const float *__restrict__
         ax = warp_sum(ax);
         ay = warp_sum(ay);
         if (lane == 0) {
-            const double dx2 = (double)ax.hi + (double)ax.lo;
-            const double dy2 = (double)ay.hi + (double)ay.lo;
-            if (dx2 == 0.0) {
+            // the squares of exact differences sum to zero only if every
+            // difference is zero
+            if (ax.hi == 0.0f) {
                 ++ndeg;
             } else {
-                const double delta = fabs(sqrt(dy2 / dx2) - 1.0);
+                const DF dd = df_sub(ay, ax);
+                const float dx2 = __fadd_rn(ax.hi, ax.lo), dy2 = __fadd_rn(ay.hi, ay.lo);
+                const float den = __fmaf_rn(__fsqrt_rn(dx2), __fsqrt_rn(dy2), dx2);
+                const float delta = __fdiv_rn(fabsf(__fadd_rn(dd.hi, dd.lo)), den);
                 ++npairs;
-                sum += delta;
-                nviol += delta > (double)cc.eps;
-                if (delta < lo || delta >= (double)cc.hi) {
+                sum += (double)delta;
+                nviol += delta > cc.eps;
+                if (delta < cc.lo || delta >= cc.hi) {
                     ++nover;
                 } else {
-                    int b = (int)floor((delta - lo) / span * (double)kBins);
+                    int b = (int)floorf((delta - cc.lo) * cc.inv_w);
                     b = min(max(b, 0), kBins - 1);
                     s_hist[b * NW + warp] += 1u;
                 }
-                const float df = (float)delta;
-                if (better_max(df, pr.x, pr.y, mx, ai, aj)) { mx = df; ai = pr.x; aj = pr.y; }
+                if (better_max(delta, pr.x, pr.y, mx, ai, aj)) { mx = delta; ai = pr.x; aj = pr.y; }
             }
         }
     }
