@@ -54,7 +54,8 @@ constexpr uint32_t kStageBytes = 4 * kPlaneBytes;           // 64 KB
 constexpr uint32_t kStageCol = kSlots * kTile;              // finished Gram sums (gx | gy)
 constexpr uint32_t kTmemCols = kStageCol + 2 * kTile;       // 512
 static_assert(kTmemCols == 512, "TMEM holds 512 columns");
-constexpr int kPiece = 16;                                  // columns classified per step
+constexpr int kPiece = 8;                                   // columns classified per step
+constexpr int kPieces = kEpiCols / kPiece;
 constexpr int kHistFlushTiles = 1000;                       // u16 counters: <= 64 per tile
 // per-thread histogram: two 16-bit bin counters per 32-bit word
 constexpr int kHistWords = kBins / 2;
@@ -207,6 +208,20 @@ __device__ __forceinline__ void tmem_ld16x2_wait(uint32_t ta, uint32_t tb, uint3
         "{%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n\t"
         "tcgen05.wait::ld.sync.aligned;"
         : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]), "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15])
+        : "r"(ta), "r"(tb)
+        : "memory");
+}
+
+// Two 8-column pieces (at ta and tb) with one wait.
+__device__ __forceinline__ void tmem_ld8x2_wait(uint32_t ta, uint32_t tb, uint32_t (&a)[8],
+                                                uint32_t (&b)[8]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x8.b32 "
+        "{%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7])
         : "r"(ta), "r"(tb)
         : "memory");
 }
@@ -423,8 +438,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     const uint32_t bar = bar_full + 8 * stage;
                     mbar_arrive_expect_tx(bar, kStageBytes);
                     const uint32_t dst = sbase + SmemLayout::stages + stage * kStageBytes;
-                    const bool is_y = ks < p.ky_steps;
-                    const int k0 = (is_y ? ks : ks - p.ky_steps) * kKStep;
+                    const bool is_y = ks >= p.kx_steps;
+                    const int k0 = (is_y ? ks - p.kx_steps : ks) * kKStep;
                     const CUtensorMap *mh = is_y ? &map_yh : &map_xh;
                     const CUtensorMap *ml = is_y ? &map_yl : &map_xl;
                     tma_load_2d(dst, mh, k0, I * kTile, bar);
@@ -523,13 +538,21 @@ __global__ void __launch_bounds__(kThreads, 1)
     } else {
         // --------------------------------------------------------- epilogue
         // Warp e owns TMEM lane quarter (warp % 4), i.e. tile row r, and the
-        // column half h of the tile.  Warps work independently: each keeps
-        // running sums of its 64 pairs in registers and its own partial slot.
+        // column half h of the tile.  The K chunks of a tile come X first, then
+        // Y.  The X chunks are summed in registers (gx); the Y chunks are summed
+        // in this warp's TMEM running columns (gy, read + add + write back).  At
+        // the end of a tile gx is parked in the TMEM staging columns.  The
+        // classification of a tile is software-pipelined into the next one: it
+        // runs piece by piece between the next tile's X-chunk drains, while the
+        // MMA warp computes that tile, and is finished before the next tile's Y
+        // chunks overwrite the running columns.
         const int ew = warp - 2;                 // 0..7
         const int quarter = warp & 3;
         const int h = ew >> 2;                   // column half
         const int r = quarter * 32 + lane;       // tile row of this thread
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
+        const uint32_t gx_stage = tmem_base + lane_addr + kStageCol + (uint32_t)(h * kEpiCols);
+        const uint32_t gy_run = gx_stage + kTile;
         CertPartial *mine = p.partials + (size_t)blockIdx.x * kEpiWarps + ew;
         int slot = 0;
         uint32_t sphase = 0;
@@ -555,110 +578,48 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         uint32_t *hrow = s_hist + ew * 32 + lane;  // bins 2w, 2w+1 at hrow[w * 256]
         int tiles_since_flush = 0;
-        long long t = blockIdx.x;               // the producer's static tile sequence
-        bool ok = true;
-        while (ok) {
-            float gx[kEpiCols], gy[kEpiCols];
+        // the tile waiting for (or in) classification
+        bool pend = false;
+        int pend_pieces = 0;
+        long long pend_t = 0;
+        int pend_i = 0, pend_j0 = 0;
+        float4 pend_ri = make_float4(0.f, 0.f, 0.f, 0.f);
+        unsigned long long pend_vmask = 0ull, qmask = 0ull;
+        RowAcc acc{0.0f, 0.0f, 0.0f, -1.0f, 0, 0, 0, 0};
+
+        // classifies the next 8-column piece of the pending tile
+        auto classify_next = [&]() {
+            const int c0 = pend_pieces * kPiece;
+            uint32_t ux[kPiece], uy[kPiece];
+            tmem_ld8x2_wait(gx_stage + c0, gy_run + c0, ux, uy);
+            float px[kPiece], py[kPiece];
 #pragma unroll
-            for (int c = 0; c < kEpiCols; ++c) gx[c] = gy[c] = 0.0f;
-            for (int ks = 0; ks < ksteps; ++ks) {
-                ok = warp_wait(bar_sfull + 8 * slot, sphase, p.status, 3);
-                if (!ok) break;
-                tc_fence_after();
-                if (ks == 0) {
-                    int cmdv = 0;
-                    if (lane == 0) cmdv = s_cmd[kStages + slot];
-                    if (__shfl_sync(0xffffffffu, cmdv, 0) < 0) {
-                        ok = false;
-                        break;
-                    }
-                }
-                const uint32_t ta = tmem_base + lane_addr + (uint32_t)(slot * kTile + h * kEpiCols);
-                const bool is_y = ks < p.ky_steps;
-#pragma unroll
-                for (int qd = 0; qd < kEpiCols / 16; ++qd) {
-                    uint32_t v[16];
-                    tmem_ld16_wait(ta + qd * 16, v);
-                    if (is_y) {
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) gy[qd * 16 + c] += __uint_as_float(v[c]);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) gx[qd * 16 + c] += __uint_as_float(v[c]);
-                    }
-                }
-                tc_fence_before();
-                mbar_arrive(bar_sempty + 8 * slot);
-                if (++slot == kSlots) {
-                    slot = 0;
-                    sphase ^= 1;
-                }
+            for (int c = 0; c < kPiece; ++c) {
+                const bool valid = (pend_vmask >> (c0 + c)) & 1ull;
+                px[c] = valid ? __uint_as_float(ux[c]) : __int_as_float(0x7fc00000);
+                py[c] = __uint_as_float(uy[c]);
             }
-            if (!ok) break;
-            // ---- park the finished sums in this warp's staging columns, so the
-            // classification below holds only one 16-column piece in registers
-            // (the compiler can then interleave many independent pairs)
-            const uint32_t sx_addr = tmem_base + lane_addr + kStageCol + (uint32_t)(h * kEpiCols);
-            const uint32_t sy_addr = sx_addr + kTile;
-#pragma unroll
-            for (int qd = 0; qd < kEpiCols / 16; ++qd) {
-                uint32_t vx[16], vy[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                    vx[c] = __float_as_uint(gx[qd * 16 + c]);
-                    vy[c] = __float_as_uint(gy[qd * 16 + c]);
-                }
-                tmem_st16(sx_addr + qd * 16, vx);
-                tmem_st16(sy_addr + qd * 16, vy);
+            if (DUMP && p.dump && pend_t < p.dump_tiles) {
+                float4 *drow = p.dump + (size_t)pend_t * kTile * kTile + r * kTile + h * kEpiCols + c0;
+                classify_piece<DUMP>(px, py, pend_ri, p.rs + pend_j0 + c0, c0, k, hrow, acc, qmask, drow);
+            } else {
+                classify_piece<false>(px, py, pend_ri, p.rs + pend_j0 + c0, c0, k, hrow, acc, qmask,
+                                      nullptr);
             }
-            tmem_wait_st();
-            // ---- classify the 64 pairs of this thread
-            const uint32_t packed = p.sched[t];
-            const int I = (int)(packed >> 16), J = (int)(packed & 0xFFFF);
-            const int i = I * kTile + r;
-            const float4 ri = __ldg(p.rs + i);
-            const int j0 = J * kTile + h * kEpiCols;
-            RowAcc acc{0.0f, 0.0f, 0.0f, -1.0f, 0, 0, 0, 0};
-            unsigned long long qmask = 0ull, vmask = ~0ull;
-            const bool full = (I < J) && (J * kTile + kTile <= p.n);
-            if (!full) {
-                // diagonal or ragged tile: columns that are not pairs i < j < n
-                // get a NaN Gram entry and their queue bit is cleared below
-                for (int c = 0; c < kEpiCols; ++c) {
-                    const int j = j0 + c;
-                    if (!((i < j) & (j < p.n))) vmask &= ~(1ull << c);
-                }
-            }
-            const bool dump = DUMP && p.dump && t < p.dump_tiles;
-#pragma unroll 1
-            for (int c0 = 0; c0 < kEpiCols; c0 += kPiece) {
-                uint32_t ux[kPiece], uy[kPiece];
-                tmem_ld16x2_wait(sx_addr + c0, sy_addr + c0, ux, uy);
-                float px[kPiece], py[kPiece];
-#pragma unroll
-                for (int c = 0; c < kPiece; ++c) {
-                    const bool valid = (vmask >> (c0 + c)) & 1ull;
-                    px[c] = valid ? __uint_as_float(ux[c]) : __int_as_float(0x7fc00000);
-                    py[c] = __uint_as_float(uy[c]);
-                }
-                if (dump) {
-                    float4 *drow = p.dump + (size_t)t * kTile * kTile + r * kTile + h * kEpiCols + c0;
-                    classify_piece<DUMP>(px, py, ri, p.rs + j0 + c0, c0, k, hrow, acc, qmask, drow);
-                } else {
-                    classify_piece<false>(px, py, ri, p.rs + j0 + c0, c0, k, hrow, acc, qmask, nullptr);
-                }
-            }
-            qmask &= vmask;
-            // push the queued pairs of this tile (rare), warp-aggregated
+            ++pend_pieces;
+        };
+        // queue pushes and warp totals of the fully classified pending tile
+        auto finish_pending = [&]() {
+            while (pend_pieces < kPieces) classify_next();
+            qmask &= pend_vmask;
             int nq = __popcll(qmask);
             while (__any_sync(0xffffffffu, qmask != 0ull)) {
                 const bool has = qmask != 0ull;
                 const int c = has ? __ffsll((long long)qmask) - 1 : 0;
                 if (has) qmask &= qmask - 1;
-                queue_push(has, i, j0 + c, p.queue, p.qcount, p.qcap);
+                queue_push(has, pend_i, pend_j0 + c, p.queue, p.qcount, p.qcap);
             }
-            // fold this tile's statistics into the warp's partial (lane 0 owns it)
-            int aj_t = j0 + acc.arg, ai_t = i;
+            int aj_t = pend_j0 + acc.arg, ai_t = pend_i;
             for (int o = 16; o > 0; o >>= 1) {
                 acc.viol += __shfl_xor_sync(0xffffffffu, acc.viol, o);
                 acc.over += __shfl_xor_sync(0xffffffffu, acc.over, o);
@@ -687,12 +648,108 @@ __global__ void __launch_bounds__(kThreads, 1)
                 // a certain violation: delta - B > eps for some pair
                 if (p.stop_flag && acc.certain > 0) atomicExch(p.stop_flag, 1);
             }
-            t += gridDim.x;
+            pend = false;
             if (++tiles_since_flush == kHistFlushTiles) {
                 tiles_since_flush = 0;
                 fold_hist(s_hist, ew, mine);
             }
+        };
+
+        long long t = blockIdx.x;               // the producer's static tile sequence
+        bool ok = true;
+        while (ok) {
+            float gx[kEpiCols];
+#pragma unroll
+            for (int c = 0; c < kEpiCols; ++c) gx[c] = 0.0f;
+            bool stop = false;
+            for (int ks = 0; ks < ksteps; ++ks) {
+                ok = warp_wait(bar_sfull + 8 * slot, sphase, p.status, 3);
+                if (!ok) break;
+                tc_fence_after();
+                if (ks == 0) {
+                    int cmdv = 0;
+                    if (lane == 0) cmdv = s_cmd[kStages + slot];
+                    if (__shfl_sync(0xffffffffu, cmdv, 0) < 0) {
+                        stop = true;
+                        break;
+                    }
+                }
+                const uint32_t ta = tmem_base + lane_addr + (uint32_t)(slot * kTile + h * kEpiCols);
+                if (ks < p.kx_steps) {
+                    // X chunk: registers
+#pragma unroll
+                    for (int qd = 0; qd < kEpiCols / 16; ++qd) {
+                        uint32_t v[16];
+                        tmem_ld16_wait(ta + qd * 16, v);
+#pragma unroll
+                        for (int c = 0; c < 16; ++c) gx[qd * 16 + c] += __uint_as_float(v[c]);
+                    }
+                } else {
+                    // Y chunk: the running columns (the first Y chunk starts them)
+                    if (ks == p.kx_steps && pend) finish_pending();
+                    const bool first = ks == p.kx_steps;
+#pragma unroll
+                    for (int qd = 0; qd < kEpiCols / 16; ++qd) {
+                        uint32_t v[16], w[16];
+                        if (first) {
+                            tmem_ld16_wait(ta + qd * 16, v);
+                        } else {
+                            tmem_ld16x2_wait(ta + qd * 16, gy_run + qd * 16, v, w);
+#pragma unroll
+                            for (int c = 0; c < 16; ++c)
+                                v[c] = __float_as_uint(__uint_as_float(v[c]) + __uint_as_float(w[c]));
+                        }
+                        tmem_st16(gy_run + qd * 16, v);
+                    }
+                    tmem_wait_st();
+                }
+                tc_fence_before();
+                mbar_arrive(bar_sempty + 8 * slot);
+                if (++slot == kSlots) {
+                    slot = 0;
+                    sphase ^= 1;
+                }
+                // one piece of the previous tile between X-chunk drains
+                if (ks < p.kx_steps && pend && pend_pieces < kPieces) classify_next();
+            }
+            if (!ok || stop) break;
+            // this tile's Y chunks have started the running columns, so the
+            // previous tile is finished (kx_steps >= 1 always precedes them)
+            // ---- park gx in the staging columns; the tile is now pending
+#pragma unroll
+            for (int qd = 0; qd < kEpiCols / 16; ++qd) {
+                uint32_t vx[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) vx[c] = __float_as_uint(gx[qd * 16 + c]);
+                tmem_st16(gx_stage + qd * 16, vx);
+            }
+            tmem_wait_st();
+            const uint32_t packed = p.sched[t];
+            const int I = (int)(packed >> 16), J = (int)(packed & 0xFFFF);
+            pend = true;
+            pend_pieces = 0;
+            pend_t = t;
+            pend_i = I * kTile + r;
+            pend_ri = __ldg(p.rs + pend_i);
+            pend_j0 = J * kTile + h * kEpiCols;
+            // the 64 column statistics the classification reads, one lane per
+            // pair of rows: in L1 by the time the next tile's drains begin
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.rs + pend_j0 + 2 * lane));
+            pend_vmask = ~0ull;
+            if (!((I < J) && (J * kTile + kTile <= p.n))) {
+                // diagonal or ragged tile: columns that are not pairs i < j < n
+                // get a NaN Gram entry and their queue bit is cleared
+                for (int c = 0; c < kEpiCols; ++c) {
+                    const int j = pend_j0 + c;
+                    if (!((pend_i < j) & (j < p.n))) pend_vmask &= ~(1ull << c);
+                }
+            }
+            qmask = 0ull;
+            acc = RowAcc{0.0f, 0.0f, 0.0f, -1.0f, 0, 0, 0, 0};
+            t += gridDim.x;
         }
+        // the last tile (its sums are complete in TMEM)
+        if (ok && pend) finish_pending();
         // ---- this warp's partial: the rest of its histogram and its totals
         fold_hist(s_hist, ew, mine);
         if (lane == 0) {
