@@ -198,6 +198,33 @@ __device__ __forceinline__ void tmem_ld16_wait(uint32_t taddr, uint32_t (&r)[16]
         : "memory");
 }
 
+// 64 consecutive TMEM columns (four x16 loads) with one wait.
+__device__ __forceinline__ void tmem_ld64_wait(uint32_t taddr, uint32_t (&r)[64]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%65];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%66];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%67];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr), "r"(taddr + 16), "r"(taddr + 32), "r"(taddr + 48)
+        : "memory");
+}
+
+// Two 32-column pieces (at ta and tb; two x16 loads each) with one wait.
+__device__ __forceinline__ void tmem_ld32x2_wait(uint32_t ta, uint32_t tb, uint32_t (&a)[32],
+                                                 uint32_t (&b)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%64];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%65];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%66];\n\t"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%67];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(a[16]), "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]), "=r"(a[24]), "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31]), "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]), "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15]), "=r"(b[16]), "=r"(b[17]), "=r"(b[18]), "=r"(b[19]), "=r"(b[20]), "=r"(b[21]), "=r"(b[22]), "=r"(b[23]), "=r"(b[24]), "=r"(b[25]), "=r"(b[26]), "=r"(b[27]), "=r"(b[28]), "=r"(b[29]), "=r"(b[30]), "=r"(b[31])
+        : "r"(ta), "r"(ta + 16), "r"(tb), "r"(tb + 16)
+        : "memory");
+}
+
 // Two 16-column pieces (at ta and tb) with one wait.
 __device__ __forceinline__ void tmem_ld16x2_wait(uint32_t ta, uint32_t tb, uint32_t (&a)[16],
                                                  uint32_t (&b)[16]) {
@@ -676,30 +703,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 const uint32_t ta = tmem_base + lane_addr + (uint32_t)(slot * kTile + h * kEpiCols);
                 if (ks < p.kx_steps) {
-                    // X chunk: registers
+                    // X chunk: registers, all 64 columns behind one wait
+                    uint32_t v[64];
+                    tmem_ld64_wait(ta, v);
 #pragma unroll
-                    for (int qd = 0; qd < kEpiCols / 16; ++qd) {
-                        uint32_t v[16];
-                        tmem_ld16_wait(ta + qd * 16, v);
-#pragma unroll
-                        for (int c = 0; c < 16; ++c) gx[qd * 16 + c] += __uint_as_float(v[c]);
-                    }
+                    for (int c = 0; c < kEpiCols; ++c) gx[c] += __uint_as_float(v[c]);
                 } else {
                     // Y chunk: the running columns (the first Y chunk starts them)
                     if (ks == p.kx_steps && pend) finish_pending();
                     const bool first = ks == p.kx_steps;
 #pragma unroll
-                    for (int qd = 0; qd < kEpiCols / 16; ++qd) {
-                        uint32_t v[16], w[16];
+                    for (int hh = 0; hh < kEpiCols / 32; ++hh) {
+                        uint32_t v[32], w[32];
                         if (first) {
-                            tmem_ld16_wait(ta + qd * 16, v);
+                            tmem_ld16x2_wait(ta + hh * 32, ta + hh * 32 + 16,
+                                             *reinterpret_cast<uint32_t(*)[16]>(v),
+                                             *reinterpret_cast<uint32_t(*)[16]>(v + 16));
                         } else {
-                            tmem_ld16x2_wait(ta + qd * 16, gy_run + qd * 16, v, w);
+                            tmem_ld32x2_wait(ta + hh * 32, gy_run + hh * 32, v, w);
 #pragma unroll
-                            for (int c = 0; c < 16; ++c)
+                            for (int c = 0; c < 32; ++c)
                                 v[c] = __float_as_uint(__uint_as_float(v[c]) + __uint_as_float(w[c]));
                         }
-                        tmem_st16(gy_run + qd * 16, v);
+                        tmem_st16(gy_run + hh * 32, *reinterpret_cast<uint32_t(*)[16]>(v));
+                        tmem_st16(gy_run + hh * 32 + 16, *reinterpret_cast<uint32_t(*)[16]>(v + 16));
                     }
                     tmem_wait_st();
                 }

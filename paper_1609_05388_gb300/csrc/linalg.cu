@@ -233,6 +233,212 @@ __global__ void __launch_bounds__(kCholThreads) cholesky32_kernel(const TG *__re
     }
 }
 
+// Blocked Cholesky G + shift I = R^T R (R upper, FP32) of an SPD b x b Gram,
+// in one CTA, with 32 x 32 blocks.  For each diagonal block: one warp factors
+// it (row k scaled by its pivot, then the rank-1 update of the rows below,
+// warp-synchronous) and inverts it by back substitution (lane j = column j);
+// the CTA then forms the panel to its right as D^T A_12 with that inverse D,
+// and updates the trailing submatrix with 4 x 4 register tiles (SYRK).  The
+// diagonal-block inverses are returned with R, so that the triangular solve
+// R^{-T} M (trsm_blocked) is a short sequence of small products.  Pivots below
+// 1e-7 of the largest diagonal entry are raised to it (the shifted CholeskyQR
+// guard).
+constexpr int kCiThreads = 512;
+constexpr int kCiBlk = 32;
+constexpr int kCiLd = kJacobiMax + 1;
+constexpr size_t kCiSmem = (size_t)(kJacobiMax * kCiLd + 2 * kCiBlk * kCiLd) * sizeof(float);
+
+template <typename TG>
+__global__ void __launch_bounds__(kCiThreads) chol_blocked_kernel(const TG *__restrict__ G, int b,
+                                                                  float shift_rel,
+                                                                  float *__restrict__ R,
+                                                                  float *__restrict__ Dinv) {
+    extern __shared__ float ci_sm[];
+    float *A = ci_sm;                        // [b][kCiLd]: R in the upper triangle
+    float *D = A + kJacobiMax * kCiLd;       // [32][kCiLd]: inverse of the current diagonal block
+    float *Z = D + kCiBlk * kCiLd;           // [32][kCiLd]: the panel D^T A_12
+    __shared__ float s_red[kCiThreads / 32];
+    __shared__ float s_shift, s_floor;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    float mx = 0.0f;
+    for (int i = tid; i < b; i += kCiThreads) mx = fmaxf(mx, (float)G[(int64_t)i * b + i]);
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) s_red[warp] = mx;
+    __syncthreads();
+    if (tid == 0) {
+        float m = 0.0f;
+        for (int w = 0; w < kCiThreads / 32; ++w) m = fmaxf(m, s_red[w]);
+        s_shift = shift_rel * m;
+        s_floor = fmaxf(1e-7f * m, 1e-30f);
+    }
+    __syncthreads();
+    const float shift = s_shift, floor_v = s_floor;
+    for (int e = tid; e < b * b; e += kCiThreads) {
+        const int i = e / b, j = e % b;
+        A[i * kCiLd + j] = j >= i ? (float)G[(int64_t)i * b + j] + (i == j ? shift : 0.0f) : 0.0f;
+    }
+    __syncthreads();
+    const int nb = (b + kCiBlk - 1) / kCiBlk;
+    for (int kb = 0; kb < nb; ++kb) {
+        const int k0 = kb * kCiBlk, bs = min(kCiBlk, b - k0), k1 = k0 + bs;
+        if (warp == 0) {
+            // the diagonal block in registers: lane j holds column j,
+            // a[i] = A[k0 + i][k0 + j] for i <= j (an identity pad beyond bs)
+            float a[kCiBlk], x[kCiBlk];
+#pragma unroll
+            for (int i = 0; i < kCiBlk; ++i) {
+                const bool in = i < bs && lane < bs;
+                a[i] = in ? (i <= lane ? A[(k0 + i) * kCiLd + k0 + lane] : 0.0f) : (i == lane ? 1.0f : 0.0f);
+            }
+            // factor: row k scaled by its pivot, then the rank-1 update below
+#pragma unroll
+            for (int k = 0; k < kCiBlk; ++k) {
+                float piv = __shfl_sync(0xffffffffu, a[k], k);
+                if (k < bs && !(piv > floor_v)) piv = floor_v;
+                const float rkk = sqrtf(piv);
+                const float inv = 1.0f / rkk;
+                a[k] = lane == k ? rkk : (lane > k ? a[k] * inv : a[k]);
+                // constant trip counts (resolved after unrolling) keep a[] in registers
+#pragma unroll
+                for (int i = 0; i < kCiBlk; ++i) {
+                    if (i <= k) continue;
+                    const float rki = __shfl_sync(0xffffffffu, a[k], i);
+                    if (lane >= i) a[i] = fmaf(-rki, a[k], a[i]);
+                }
+            }
+            // invert: x[i] = (R_kk^{-1})[i][lane], back substitution
+#pragma unroll
+            for (int i = kCiBlk - 1; i >= 0; --i) {
+                const float rii = __shfl_sync(0xffffffffu, a[i], i);
+                float acc = i == lane ? 1.0f : 0.0f;
+#pragma unroll
+                for (int m = 0; m < kCiBlk; ++m) {
+                    if (m <= i) continue;
+                    const float rim = __shfl_sync(0xffffffffu, a[i], m);
+                    if (m <= lane) acc = fmaf(-rim, x[m], acc);
+                }
+                x[i] = i <= lane ? acc / rii : 0.0f;
+            }
+#pragma unroll
+            for (int i = 0; i < kCiBlk; ++i) {
+                if (lane < bs && i <= lane) A[(k0 + i) * kCiLd + k0 + lane] = a[i];
+                D[i * kCiLd + lane] = (lane < bs && i < bs) ? x[i] : 0.0f;
+            }
+        }
+        __syncthreads();
+        if (k1 < b) {
+            // panel: R_12 = D^T A_12 (A_12 = rows k0..k1, columns k1..b)
+            const int rem = b - k1;
+            for (int e = tid; e < bs * rem; e += kCiThreads) {
+                const int i = e / rem, c = k1 + e % rem;
+                float acc = 0.0f;
+                for (int m = 0; m <= i; ++m) acc = fmaf(D[m * kCiLd + i], A[(k0 + m) * kCiLd + c], acc);
+                Z[i * kCiLd + c] = acc;
+            }
+            __syncthreads();
+            for (int e = tid; e < bs * rem; e += kCiThreads) {
+                const int i = e / rem, c = k1 + e % rem;
+                A[(k0 + i) * kCiLd + c] = Z[i * kCiLd + c];
+            }
+            __syncthreads();
+            // trailing update A_22 -= R_12^T R_12 on 4 x 4 tiles of the upper triangle
+            const int nt4 = (rem + 3) / 4;
+            for (int e = tid; e < nt4 * nt4; e += kCiThreads) {
+                const int ti = e / nt4, tj = e % nt4;
+                if (tj < ti) continue;
+                float acc[4][4];
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) acc[r][c] = 0.0f;
+                const int i0 = k1 + 4 * ti, j0 = k1 + 4 * tj;
+                for (int m = k0; m < k1; ++m) {
+                    float u[4], w[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) u[r] = (i0 + r < b) ? A[m * kCiLd + i0 + r] : 0.0f;
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) w[c] = (j0 + c < b) ? A[m * kCiLd + j0 + c] : 0.0f;
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(u[r], w[c], acc[r][c]);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        const int i = i0 + r, j = j0 + c;
+                        if (i < b && j < b && j >= i) A[i * kCiLd + j] -= acc[r][c];
+                    }
+            }
+        }
+        // the inverse of this diagonal block, rows k0..k1 of Dinv (b x 32)
+        for (int e = tid; e < bs * kCiBlk; e += kCiThreads) {
+            const int i = e / kCiBlk, c = e % kCiBlk;
+            Dinv[(int64_t)(k0 + i) * kCiBlk + c] = c < bs ? D[i * kCiLd + c] : 0.0f;
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < b * b; e += kCiThreads) {
+        const int i = e / b, j = e % b;
+        R[e] = j >= i ? A[i * kCiLd + j] : 0.0f;
+    }
+}
+
+// M (b x d rows) <- R^{-T} M by 32-row blocks with the diagonal-block
+// inverses D_i of chol_blocked_kernel:
+//   Y_i = D_i^T (M_i - sum_{k < i} R_ki^T Y_k)
+// one CTA per 16 columns of M, everything in shared memory.
+constexpr int kTbCols = 16;
+constexpr int kTbThreads = 512;
+constexpr size_t kTbSmem = (size_t)(kJacobiMax * kCiLd + kJacobiMax * kCiBlk + 2 * kJacobiMax * kTbCols) * sizeof(float);
+
+__global__ void __launch_bounds__(kTbThreads) trsm_blocked_kernel(const float *__restrict__ R,
+                                                                  const float *__restrict__ Dinv,
+                                                                  int b, float *M, int64_t ldm, int d) {
+    extern __shared__ float tb_sm[];
+    float *Rs = tb_sm;                                // [b][kCiLd]
+    float *Ds = Rs + kJacobiMax * kCiLd;              // [b][32]
+    float *Ys = Ds + kJacobiMax * kCiBlk;             // [b][16]: solved rows
+    float *Ts = Ys + kJacobiMax * kTbCols;            // [b][16]: right-hand sides
+    const int tid = threadIdx.x;
+    const int c0 = blockIdx.x * kTbCols;
+    for (int e = tid; e < b * b; e += kTbThreads) {
+        const int i = e / b, j = e % b;
+        Rs[i * kCiLd + j] = R[e];
+    }
+    for (int e = tid; e < b * kCiBlk; e += kTbThreads) Ds[e] = Dinv[e];
+    for (int e = tid; e < b * kTbCols; e += kTbThreads) {
+        const int i = e / kTbCols, c = c0 + e % kTbCols;
+        Ts[e] = c < d ? M[(int64_t)i * ldm + c] : 0.0f;
+    }
+    __syncthreads();
+    const int nb = (b + kCiBlk - 1) / kCiBlk;
+    for (int kb = 0; kb < nb; ++kb) {
+        const int k0 = kb * kCiBlk, bs = min(kCiBlk, b - k0);
+        // right-hand side of block kb minus the solved blocks
+        for (int e = tid; e < bs * kTbCols; e += kTbThreads) {
+            const int r = k0 + e / kTbCols, c = e % kTbCols;
+            float acc = Ts[r * kTbCols + c];
+            for (int m = 0; m < k0; ++m) acc = fmaf(-Rs[m * kCiLd + r], Ys[m * kTbCols + c], acc);
+            Ts[r * kTbCols + c] = acc;
+        }
+        __syncthreads();
+        // Y_kb = D^T T_kb (D upper: rows m <= r)
+        for (int e = tid; e < bs * kTbCols; e += kTbThreads) {
+            const int rl = e / kTbCols, c = e % kTbCols;
+            float acc = 0.0f;
+            for (int m = 0; m <= rl; ++m) acc = fmaf(Ds[(k0 + m) * kCiBlk + rl], Ts[(k0 + m) * kTbCols + c], acc);
+            Ys[(k0 + rl) * kTbCols + c] = acc;
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < b * kTbCols; e += kTbThreads) {
+        const int i = e / kTbCols, c = c0 + e % kTbCols;
+        if (c < d) M[(int64_t)i * ldm + c] = Ys[e];
+    }
+}
+
 // V (b x d rows) <- R^{-T} V, two columns per warp: each half-warp solves
 // one column, lane l keeping the solved entries l, l + 16, ... in registers;
 // each step is a lane-local partial dot product and a 16-lane reduction.  R
@@ -327,7 +533,8 @@ __global__ void trsm_rows_kernel(const double *__restrict__ R, int b, float *V, 
     }
 }
 
-constexpr int kJacobiThreads = 512;
+constexpr int kJacobiThreads = 1024;
+constexpr int kJacobiColIt = (kJacobiMax / 2 + 31) / 32;  // column-pair rotations per lane
 
 // Parallel cyclic Jacobi (round-robin pairing, b / 2 disjoint rotations per
 // round) on H (FP32 in shared memory).  A round's rotations form a
@@ -362,9 +569,17 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const double *__
     for (int sweep = 0; sweep < max_sweeps; ++sweep) {
         for (int r = 0; r < B - 1; ++r) {
             if (tid < half) {
+                // round-robin pairing: index B - 1 stays, the others rotate
                 int p, q;
-                if (tid == 0) { p = r; q = B - 1; }
-                else { p = (r + tid) % (B - 1); q = (r - tid + (B - 1)) % (B - 1); }
+                if (tid == 0) {
+                    p = r;
+                    q = B - 1;
+                } else {
+                    p = r + tid;
+                    if (p >= B - 1) p -= B - 1;
+                    q = r - tid;
+                    if (q < 0) q += B - 1;
+                }
                 if (p > q) { int t = p; p = q; q = t; }
                 float c = 1.0f, s = 0.0f;
                 const float apq = H[p * ld + q];
@@ -380,24 +595,36 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const double *__
                 pp[tid] = p; qq[tid] = q; cs[tid] = c; sn[tid] = s;
             }
             __syncthreads();
+            // this lane's column-pair rotations, read once per round
+            int pb[kJacobiColIt], qb[kJacobiColIt];
+            float cb[kJacobiColIt], sb[kJacobiColIt];
+#pragma unroll
+            for (int u = 0; u < kJacobiColIt; ++u) {
+                const int rb = lx + 32 * u;
+                const bool in = rb < half;
+                pb[u] = in ? pp[rb] : 0;
+                qb[u] = in ? qq[rb] : 0;
+                cb[u] = in ? cs[rb] : 1.0f;
+                sb[u] = in ? sn[rb] : 0.0f;
+            }
             // H <- J^T H J, one 2 x 2 block (rotation a = row pair, b = column pair) per step
             for (int ra = wy; ra < half; ra += nwy) {
                 const int pa = pp[ra], qa = qq[ra];
                 const float ca = cs[ra], sa = sn[ra];
                 const bool ida = sa == 0.0f;
-                for (int rb = lx; rb < half; rb += 32) {
-                    const float sb = sn[rb];
-                    if (ida && sb == 0.0f) continue;
-                    const int pb = pp[rb], qb = qq[rb];
-                    const float cb = cs[rb];
-                    const float h00 = H[pa * ld + pb], h01 = H[pa * ld + qb];
-                    const float h10 = H[qa * ld + pb], h11 = H[qa * ld + qb];
+#pragma unroll
+                for (int u = 0; u < kJacobiColIt; ++u) {
+                    const int rb = lx + 32 * u;
+                    if (rb >= half || (ida && sb[u] == 0.0f)) continue;
+                    float *r0 = H + pa * ld, *r1 = H + qa * ld;
+                    const float h00 = r0[pb[u]], h01 = r0[qb[u]];
+                    const float h10 = r1[pb[u]], h11 = r1[qb[u]];
                     const float t00 = ca * h00 - sa * h10, t01 = ca * h01 - sa * h11;
                     const float t10 = sa * h00 + ca * h10, t11 = sa * h01 + ca * h11;
-                    H[pa * ld + pb] = cb * t00 - sb * t01;
-                    H[pa * ld + qb] = sb * t00 + cb * t01;
-                    H[qa * ld + pb] = cb * t10 - sb * t11;
-                    H[qa * ld + qb] = sb * t10 + cb * t11;
+                    r0[pb[u]] = cb[u] * t00 - sb[u] * t01;
+                    r0[qb[u]] = sb[u] * t00 + cb[u] * t01;
+                    r1[pb[u]] = cb[u] * t10 - sb[u] * t11;
+                    r1[qb[u]] = sb[u] * t10 + cb[u] * t11;
                 }
                 // U^T rows pa, qa (the same rotation as H's rows)
                 if (!ida) {
@@ -603,6 +830,9 @@ void linalg_init() {
     set_max_dyn_smem((const void *)trsm_rows_kernel, (int)((b * b + b * kTrsmCols) * sizeof(float)));
     set_max_dyn_smem((const void *)jacobi_kernel, (int)(jacobi_smem(kJacobiMax)));
     set_max_dyn_smem((const void *)trsm_warp_kernel, (int)(b * (b + 1) * sizeof(float)));
+    set_max_dyn_smem((const void *)chol_blocked_kernel<float>, (int)kCiSmem);
+    set_max_dyn_smem((const void *)chol_blocked_kernel<double>, (int)kCiSmem);
+    set_max_dyn_smem((const void *)trsm_blocked_kernel, (int)kTbSmem);
 }
 
 template <typename TG>
@@ -613,6 +843,25 @@ void cholesky32(const TG *G, int b, float shift_rel, float *R, cudaStream_t st) 
 }
 template void cholesky32<double>(const double *, int, float, float *, cudaStream_t);
 template void cholesky32<float>(const float *, int, float, float *, cudaStream_t);
+
+template <typename TG>
+void cholesky_blocked(const TG *G, int b, float shift_rel, float *R, float *Dinv, cudaStream_t st) {
+    if (b > kJacobiMax) fail(ADAGIO_E_INVALID_ARG, "internal: Cholesky block %d > %d", b, kJacobiMax);
+    set_max_dyn_smem((const void *)chol_blocked_kernel<TG>, (int)kCiSmem);
+    chol_blocked_kernel<TG><<<1, kCiThreads, kCiSmem, st>>>(G, b, shift_rel, R, Dinv);
+    ADAGIO_CHECK_LAUNCH();
+}
+template void cholesky_blocked<double>(const double *, int, float, float *, float *, cudaStream_t);
+template void cholesky_blocked<float>(const float *, int, float, float *, float *, cudaStream_t);
+
+void trsm_blocked(const float *R, const float *Dinv, int b, float *M, int64_t ldm, int d,
+                  cudaStream_t st) {
+    if (b > kJacobiMax) fail(ADAGIO_E_INVALID_ARG, "internal: TRSM block %d > %d", b, kJacobiMax);
+    set_max_dyn_smem((const void *)trsm_blocked_kernel, (int)kTbSmem);
+    trsm_blocked_kernel<<<(unsigned)ceil_div(d, kTbCols), kTbThreads, kTbSmem, st>>>(R, Dinv, b, M,
+                                                                                  ldm, d);
+    ADAGIO_CHECK_LAUNCH();
+}
 
 void trsm_warp(const float *R, int b, float *V, int64_t ldv, int d, cudaStream_t st) {
     if (b > kJacobiMax) fail(ADAGIO_E_INVALID_ARG, "internal: TRSM block %d > %d", b, kJacobiMax);

@@ -56,6 +56,19 @@ void trsm_rows(const double *R, int b, float *V, int64_t ldv, int d, cudaStream_
 template <typename TG>
 void cholesky32(const TG *G, int b, float shift_rel, float *R, cudaStream_t st);
 
+// Blocked FP32 Cholesky (one CTA) of the SPD b x b Gram G (FP64 or FP32,
+// row-major) with a diagonal shift of shift_rel * max(diag G): R (b x b
+// upper, row-major) and the inverses of its 32 x 32 diagonal blocks, Dinv
+// (b x 32: row r holds row r - 32 floor(r / 32) of its block's inverse).
+// Pivots are floored at 1e-7 of the largest diagonal entry.
+template <typename TG>
+void cholesky_blocked(const TG *G, int b, float shift_rel, float *R, float *Dinv, cudaStream_t st);
+
+// M (b x d rows, leading dimension ldm) <- R^{-T} M with R and Dinv from
+// cholesky_blocked (block forward substitution, one CTA per 16 columns).
+void trsm_blocked(const float *R, const float *Dinv, int b, float *M, int64_t ldm, int d,
+                  cudaStream_t st);
+
 // V (b x d rows, FP32, leading dimension ldv) <- R^{-T} V with R from
 // cholesky32: one warp per column of V.
 void trsm_warp(const float *R, int b, float *V, int64_t ldv, int d, cudaStream_t st);

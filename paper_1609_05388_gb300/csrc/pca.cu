@@ -37,6 +37,7 @@ size_t pca_bytes(int64_t n, int d, int s_cap, int oversample) {
     bytes += align_up((size_t)d * d * sizeof(float), 256);                          // C
     bytes += align_up((size_t)splitk_chunks(n) * d * d * sizeof(float), 256);       // partials
     bytes += 3 * align_up((size_t)b * d * sizeof(float), 256);                      // V, W, T
+    bytes += align_up((size_t)b * 32 * sizeof(float), 256);                         // Dinv
     bytes += align_up((size_t)std::max(s_cap, 1) * d * sizeof(float), 256);         // P
     bytes += align_up((size_t)std::max(s_cap, 1) * b * sizeof(float), 256);         // proj coeffs
     bytes += 2 * align_up((size_t)b * b * sizeof(double), 256);                     // G, H
@@ -81,6 +82,7 @@ void PCA::init_enqueue(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int
     V = ws_array<float>(ctx, (size_t)bmax * d);
     W = ws_array<float>(ctx, (size_t)bmax * d);
     T = ws_array<float>(ctx, (size_t)bmax * d);
+    Dinv = ws_array<float>(ctx, (size_t)bmax * 32);
     P = ws_array<float>(ctx, (size_t)std::max(s_cap, 1) * d);
     coef = ws_array<float>(ctx, (size_t)std::max(s_cap, 1) * bmax);
     G = ws_array<double>(ctx, (size_t)bmax * bmax);
@@ -120,31 +122,39 @@ void PCA::deflate(float *M, int r, cudaStream_t st) {
 }
 
 // Orthonormalises the rows of M (b x d): shifted CholeskyQR3 (Fukaya et al.,
-// SIAM J. Sci. Comput. 2020) in FP32.  The first pass takes its Gram in FP64
-// and a shift of 1e-5 of the largest diagonal entry, so it succeeds for any
+// SIAM J. Sci. Comput. 2020) in FP32.  Each pass forms the Gram M M^T, factors
+// it as R^T R with the blocked one-CTA Cholesky and replaces M by R^{-T} M
+// (block forward substitution).  The first pass takes its Gram in FP64 and a
+// shift of 1e-5 of the largest diagonal entry, so it succeeds for any
 // conditioning an FP32 matrix can carry and leaves a basis with condition
 // number below ~300; two unshifted-size passes with FP32 Grams then restore
 // orthonormality to FP32 precision.
 void PCA::orth(float *M, int b, cudaStream_t st) {
-    gemm_f64_splitk(b, b, d, MatView<float>{M, d, 1}, MatView<float>{M, 1, d}, G, f64part, kF64Chunk,
-                    st);
-    cholesky32<double>(G, b, 1e-5f, R32, st);
-    trsm_warp(R32, b, M, d, d, st);
-    for (int pass = 1; pass < 3; ++pass) {
-        gemm_f32(b, b, d, 1.0f, MatView<float>{M, d, 1}, MatView<float>{M, 1, d}, 0.0f, G32, b, part,
-                 part_floats, st);
-        cholesky32<float>(G32, b, pass == 1 ? 1e-7f : 0.0f, R32, st);
-        trsm_warp(R32, b, M, d, d, st);
+    for (int pass = 0; pass < 3; ++pass) {
+        if (pass == 0) {
+            gemm_f64_splitk(b, b, d, MatView<float>{M, d, 1}, MatView<float>{M, 1, d}, G, f64part,
+                            kF64Chunk, st);
+            cholesky_blocked<double>(G, b, 1e-5f, R32, Dinv, st);
+        } else {
+            gemm_f32(b, b, d, 1.0f, MatView<float>{M, d, 1}, MatView<float>{M, 1, d}, 0.0f, G32, b,
+                     part, part_floats, st);
+            cholesky_blocked<float>(G32, b, pass == 1 ? 1e-7f : 0.0f, R32, Dinv, st);
+        }
+        trsm_blocked(R32, Dinv, b, M, d, d, st);
     }
 }
 
-// Rayleigh-Ritz (and the convergence test) on the first iteration, then at
+// Rayleigh-Ritz (and the convergence test) after kRRFirst iterations, then at
 // the iteration where the last test predicts convergence (at most kRRMax
 // iterations later), and on the last; CholeskyQR keeps V orthonormal in
 // between.  The prediction: the Ritz residual of direction i shrinks by about
 // theta_b / theta_i per iteration (the block's smallest Ritz value standing
 // in for the first eigenvalue outside the block).
 constexpr int kRRMax = 8;
+// The first Rayleigh-Ritz step of a block comes after a few iterations: on
+// the random start block its convergence test cannot pass, and its dense
+// Jacobi solve is the most expensive one.
+constexpr int kRRFirst = 2;
 
 void PCA::begin_block(int s_needed, cudaStream_t st) {
     (void)s_needed;
@@ -152,7 +162,8 @@ void PCA::begin_block(int s_needed, cudaStream_t st) {
     blk.s_blk = std::min({s_cap - s_done, kJacobiMax - p, blk.remaining});
     blk.b = std::min(blk.s_blk + p, blk.remaining);
     blk.it = 0;
-    blk.next_rr = 0;
+    blk.next_rr = std::min(kRRFirst, max_iter - 1);
+    blk.rr = 0;
     blk.last = false;
     blk.active = true;
     rademacher_block(seed + (uint64_t)s_done * 0x9E3779B9ull, blk.b, d, V, d, st);
@@ -180,7 +191,8 @@ void PCA::advance(int s_needed, cudaStream_t st) {
             // separated Ritz values.  Rotations inside a cluster of nearly equal
             // values are left unfinished: they mix directions that are
             // interchangeable, and the convergence test measures the subspace.
-            jacobi_eig(H, b, theta_blk, U, it == 0 ? 6 : 3, st);
+            jacobi_eig(H, b, theta_blk, U, blk.rr == 0 ? 6 : 3, st);
+            ++blk.rr;
             // V <- U^T V, W <- U^T W
             gemm_f32(b, d, b, 1.0f, MatView<float>{U, 1, b}, MatView<float>{V, d, 1}, 0.0f, T, d,
                      part, part_floats, st);

@@ -21,6 +21,7 @@ struct PCA {
     float *V = nullptr, *W = nullptr, *T = nullptr, *U = nullptr, *coef = nullptr, *res = nullptr;
     double *G = nullptr, *H = nullptr, *theta_blk = nullptr, *f64part = nullptr;
     float *G32 = nullptr, *R32 = nullptr, *part = nullptr;  // FP32 Gram, Cholesky factor, split-K
+    float *Dinv = nullptr;     // b x 32: inverses of the factor's diagonal blocks
     int64_t part_floats = 0;
     unsigned *flags = nullptr;
     double *elapsed_ms = nullptr;  // optional: extend() adds its wall time here
@@ -51,6 +52,7 @@ struct PCA {
         bool active = false;
         int it = 0, s_blk = 0, b = 0, remaining = 0;
         int next_rr = 0;  // iteration of the next Rayleigh-Ritz step
+        int rr = 0;       // Rayleigh-Ritz steps taken in this block
         bool last = false;
     } blk;
     void *stage(size_t bytes);

@@ -2,17 +2,20 @@
 //
 // K9 takes every pair the tile kernels could not classify with certainty and
 // recomputes both squared distances from coordinate differences of the
-// ORIGINAL float32 inputs (no centring, no Gram), one warp per pair, in
-// double-float arithmetic: each difference is split exactly by TwoSum, each
-// square exactly by an FMA-based TwoProduct, and the running sum is kept as
-// an unevaluated hi + lo pair (Dekker 1971; Knuth TAOCP vol. 2, 4.2.2).  The
-// relative error of the result is a few units of 2^-44, far below the 1e-6
-// classification threshold.  The distortion (Eq. 2) is then evaluated without
-// FP64 (slow on this GPU) in the cancellation-free form
+// ORIGINAL float32 inputs (no centring, no Gram), one warp per pair.  Each
+// difference is rounded once to FP32 (relative error <= 2^-24), squared
+// exactly by an FMA-based TwoProduct, and the squares are summed as an
+// unevaluated hi + lo pair with TwoSum (Dekker 1971; Knuth TAOCP vol. 2,
+// 4.2.2).  All terms are positive, so the relative error of each squared
+// distance is at most 2^-23 plus the double-float summation error (a few
+// units of 2^-44), far below the 1e-6 classification threshold.  Rows are
+// read with the widest aligned vector loads (float4, float2 or float).
+// The distortion (Eq. 2) is then evaluated without FP64 (slow on this GPU)
+// in the cancellation-free form
 //     delta = |dy2 - dx2| / (dx2 + sqrt(dx2) sqrt(dy2))
 // with the difference dy2 - dx2 taken in double-float and one IEEE FP32
-// division and two square roots: its relative error is below 4 * 2^-24
-// (under 2.4e-7 absolute for delta <= 1), inside the 1e-6 band around the
+// division and two square roots: its relative error is below 6 * 2^-24
+// (under 4e-7 absolute for delta <= 1), inside the 1e-6 band around the
 // bin edges and eps where the certificate allows a miscount.  A pair with
 // ||x_i - x_j|| == 0 is counted as degenerate.
 //
@@ -38,17 +41,15 @@ __device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
     e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
 }
 
-// acc += (a - b)^2 in double-float
+// acc += (a - b)^2 in double-float, the difference rounded once
 __device__ __forceinline__ void add_sq_diff(DF &acc, float a, float b) {
-    float d, de;
-    two_sum(a, -b, d, de);                 // a - b = d + de exactly
-    float p = __fmul_rn(d, d);
-    float pe = __fmaf_rn(d, d, -p);        // d*d = p + pe exactly
-    float corr = __fmaf_rn(2.0f * d, de, pe);
+    const float d = __fsub_rn(a, b);
+    const float p = __fmul_rn(d, d);
+    const float pe = __fmaf_rn(d, d, -p);  // d*d = p + pe exactly
     float s, e;
     two_sum(acc.hi, p, s, e);
     acc.hi = s;
-    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, corr));
+    acc.lo = __fadd_rn(acc.lo, __fadd_rn(e, pe));
 }
 
 __device__ __forceinline__ DF df_add(DF a, DF b) {
@@ -79,24 +80,55 @@ __device__ __forceinline__ DF warp_sum(DF v) {
     return v;
 }
 
-// acc += sum over this lane's elements k of (a_k - b_k)^2, four independent
-// double-float chains so the loads of consecutive elements overlap
+template <int V>
+struct VecT;
+template <>
+struct VecT<4> {
+    using T = float4;
+};
+template <>
+struct VecT<2> {
+    using T = float2;
+};
+template <>
+struct VecT<1> {
+    using T = float;
+};
+
+__device__ __forceinline__ void add_vec(DF (&c)[4], float4 a, float4 b) {
+    add_sq_diff(c[0], a.x, b.x);
+    add_sq_diff(c[1], a.y, b.y);
+    add_sq_diff(c[2], a.z, b.z);
+    add_sq_diff(c[3], a.w, b.w);
+}
+__device__ __forceinline__ void add_vec(DF (&c)[4], float2 a, float2 b) {
+    add_sq_diff(c[0], a.x, b.x);
+    add_sq_diff(c[1], a.y, b.y);
+}
+__device__ __forceinline__ void add_vec(DF (&c)[4], float a, float b) { add_sq_diff(c[0], a, b); }
+
+// sum over this lane's elements k of (a_k - b_k)^2: V-wide loads (the rows
+// are V-aligned), two loads in flight per chain, a scalar tail
+template <int V>
 __device__ __forceinline__ DF sq_dist_lanes(const float *__restrict__ a, const float *__restrict__ b,
                                             int n, int lane) {
-    DF c0{0.0f, 0.0f}, c1{0.0f, 0.0f}, c2{0.0f, 0.0f}, c3{0.0f, 0.0f};
-    int k = lane;
-    for (; k + 96 < n; k += 128) {
-        const float a0 = __ldg(a + k), a1 = __ldg(a + k + 32), a2 = __ldg(a + k + 64), a3 = __ldg(a + k + 96);
-        const float b0 = __ldg(b + k), b1 = __ldg(b + k + 32), b2 = __ldg(b + k + 64), b3 = __ldg(b + k + 96);
-        add_sq_diff(c0, a0, b0);
-        add_sq_diff(c1, a1, b1);
-        add_sq_diff(c2, a2, b2);
-        add_sq_diff(c3, a3, b3);
+    using T = typename VecT<V>::T;
+    DF c[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+    const T *av = reinterpret_cast<const T *>(a), *bv = reinterpret_cast<const T *>(b);
+    const int nv = n / V;
+    int v = lane;
+    for (; v + 32 < nv; v += 64) {
+        const T a0 = __ldg(av + v), a1 = __ldg(av + v + 32);
+        const T b0 = __ldg(bv + v), b1 = __ldg(bv + v + 32);
+        add_vec(c, a0, b0);
+        add_vec(c, a1, b1);
     }
-    for (; k < n; k += 32) add_sq_diff(c0, __ldg(a + k), __ldg(b + k));
-    return df_add(df_add(c0, c1), df_add(c2, c3));
+    for (; v < nv; v += 32) add_vec(c, __ldg(av + v), __ldg(bv + v));
+    for (int k = nv * V + lane; k < n; k += 32) add_sq_diff(c[0], __ldg(a + k), __ldg(b + k));
+    return df_add(df_add(c[0], c[1]), df_add(c[2], c[3]));
 }
 
+template <int VX, int VY>
 __global__ void __launch_bounds__(RT) recompute_kernel(const float *__restrict__ X, int64_t ldx,
                                                         int d, const float *__restrict__ Y,
                                                         int64_t ldy, int m,
@@ -117,8 +149,8 @@ __global__ void __launch_bounds__(RT) recompute_kernel(const float *__restrict__
     int ai = 0x7fffffff, aj = 0x7fffffff;
     for (long long q = (long long)blockIdx.x * NW + warp; q < (long long)qlen; q += warps) {
         const int2 pr = queue[q];
-        DF ax = sq_dist_lanes(X + (int64_t)pr.x * ldx, X + (int64_t)pr.y * ldx, d, lane);
-        DF ay = sq_dist_lanes(Y + (int64_t)pr.x * ldy, Y + (int64_t)pr.y * ldy, m, lane);
+        DF ax = sq_dist_lanes<VX>(X + (int64_t)pr.x * ldx, X + (int64_t)pr.y * ldx, d, lane);
+        DF ay = sq_dist_lanes<VY>(Y + (int64_t)pr.x * ldy, Y + (int64_t)pr.y * ldy, m, lane);
         ax = warp_sum(ax);
         ay = warp_sum(ay);
         if (lane == 0) {
@@ -245,7 +277,30 @@ void launch_recompute(const float *X, int64_t ldx, int d, const float *Y, int64_
                       const int2 *queue, const unsigned long long *qcount,
                       unsigned long long qcap, CertConst cc, CertPartial *partials, int grid,
                       cudaStream_t st) {
-    recompute_kernel<<<grid, RT, 0, st>>>(X, ldx, d, Y, ldy, m, queue, qcount, qcap, cc, partials);
+    // widest vector load every row of the matrix starts aligned to
+    auto width = [](const float *p, int64_t ld) {
+        const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+        if (a % 16 == 0 && ld % 4 == 0) return 4;
+        if (a % 8 == 0 && ld % 2 == 0) return 2;
+        return 1;
+    };
+    const int vx = width(X, ldx), vy = width(Y, ldy);
+#define ADAGIO_RECOMPUTE(A, B)                                                                    \
+    recompute_kernel<A, B><<<grid, RT, 0, st>>>(X, ldx, d, Y, ldy, m, queue, qcount, qcap, cc, partials)
+    if (vx == 4) {
+        if (vy == 4) ADAGIO_RECOMPUTE(4, 4);
+        else if (vy == 2) ADAGIO_RECOMPUTE(4, 2);
+        else ADAGIO_RECOMPUTE(4, 1);
+    } else if (vx == 2) {
+        if (vy == 4) ADAGIO_RECOMPUTE(2, 4);
+        else if (vy == 2) ADAGIO_RECOMPUTE(2, 2);
+        else ADAGIO_RECOMPUTE(2, 1);
+    } else {
+        if (vy == 4) ADAGIO_RECOMPUTE(1, 4);
+        else if (vy == 2) ADAGIO_RECOMPUTE(1, 2);
+        else ADAGIO_RECOMPUTE(1, 1);
+    }
+#undef ADAGIO_RECOMPUTE
     ADAGIO_CHECK_LAUNCH();
 }
 
