@@ -51,7 +51,7 @@ static int partial_slots(adagio_ctx *ctx, int64_t n, int precision) {
     return cert_tc_ctas(ctx, n) * 8;                          // one slot per epilogue warp
 }
 
-static int recompute_grid(adagio_ctx *ctx) { return ctx->num_sms * 8; }
+static int recompute_grid(adagio_ctx *ctx) { return ctx->num_sms * 3; }  // resident: 3 x 256 threads / SM
 
 size_t cert_prep_x_bytes(int64_t n, int d, int precision) {
     const bool tc = precision != ADAGIO_PREC_FP32;

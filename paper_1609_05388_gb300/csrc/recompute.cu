@@ -129,7 +129,7 @@ __device__ __forceinline__ DF sq_dist_lanes(const float *__restrict__ a, const f
 }
 
 template <int VX, int VY>
-__global__ void __launch_bounds__(RT) recompute_kernel(const float *__restrict__ X, int64_t ldx,
+__global__ void __launch_bounds__(RT, 3) recompute_kernel(const float *__restrict__ X, int64_t ldx,
                                                         int d, const float *__restrict__ Y,
                                                         int64_t ldy, int m,
                                                         const int2 *__restrict__ queue,
