@@ -39,9 +39,9 @@ PCA_TOL = 1e-4
 WORKLOAD = "mnist_like 60000x784 (10 clusters, rank-50, ~80% zeros, k/255), eps=0.1"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one tile-kernel
-# launch on this workload (m = 422) from one ncu capture of the full launch
+# launch on this workload from one ncu capture of the full launch
 # (profiles/cert_tc_mnist.md), or None once the kernel has changed since.
-TRAFFIC_BYTES = 8211860736 + 37117184
+TRAFFIC_BYTES = None
 
 
 def parse():
@@ -321,6 +321,17 @@ def main():
                  "traffic": TRAFFIC_BYTES, "kernel_ms": tile_ms,
                  "algorithmic_flops_per_launch": flops,
                  "queued_pairs": cst["queued"]})
+    if prec != lib.PREC_FP32:
+        # tensor-pipe work actually issued: three products per K term over
+        # the padded K (multiples of 64) and the full 128 x 128 tiles
+        T = -(-n // 256) * 2
+        tiles = T * (T + 1) // 2
+        kpad = -(-d // 64) * 64 + -(-m // 64) * 64
+        executed = tiles * 128 * 128 * 2.0 * kpad * 3
+        roof["executed_tflops"] = executed / (tile_ms / 1e3) / 1e12
+        roof["executed_frac"] = roof["executed_tflops"] / peak
+        roof["tile_kernel"] = {1: "single CTA per 128x128 tile", 2: "CTA pair per 256x128 tile"}[
+            ctx.tile_kernel_for(n)]
 
     # end to end through the C ABI with host buffers (copies inside the call)
     torch.cuda.synchronize()

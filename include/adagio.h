@@ -185,8 +185,13 @@ int adagio_distortion_noalloc(adagio_ctx *ctx, const float *X, int64_t n, int d,
 /* ------------------------------------------------------------------- embed */
 /*
  * Y = X A^T: row i of Y is f(x_i) = A x_i (Algorithm 1's output for every w).
- *  A  m x d (lda), X  n x d (ldx), Y  n x m (ldy), written in full.
- * Errors: INVALID_ARG, CUDA, WORKSPACE (host arrays need staging).
+ *  A  m x d (lda), X  n x d (ldx), Y  n x m (ldy), written in full; n <= 2^30.
+ * Computed on tcgen05 tensor cores from per-row power-of-two FP16 splits of X
+ * and A (hi + lo, three products per term), FP32 accumulation: about 1e-7
+ * relative to |A| |x| per entry.
+ * Errors: INVALID_ARG, CUDA, WORKSPACE (host arrays need staging), TIMEOUT
+ * (reported when Y is a host array; a device-array call does not synchronise,
+ * and a later synchronising call on the context reports it).
  */
 int adagio_embed(adagio_ctx *ctx, const float *A, int m, int d, int64_t lda,
                  const float *X, int64_t n, int64_t ldx, float *Y, int64_t ldy,
@@ -387,6 +392,28 @@ int adagio_last_fit_stats(const adagio_ctx *ctx, adagio_fit_stats *out);
 
 int adagio_set_timing(adagio_ctx *ctx, int enable);
 int adagio_last_cert_stats(const adagio_ctx *ctx, adagio_cert_stats *out);
+
+/*
+ * Tile kernel of the split-precision certificates (the all-pairs step of
+ * Eq. 2 and Eq. 3; the classification of every pair does not depend on it):
+ *   variant ADAGIO_TILES_AUTO    default: one CTA per tile
+ *           ADAGIO_TILES_SINGLE  one CTA per 128 x 128 tile
+ *           ADAGIO_TILES_PAIR    a cluster of two CTAs per 256 x 128 tile
+ *                                (SINGLE where such clusters cannot be
+ *                                resident on the device)
+ *   chunk_steps  64-wide K steps summed in one tensor-core accumulator before
+ *                the FP32 register sum: 0 (default) or 1, or 2 (half the
+ *                accumulator drains, a wider error bound and so more pairs
+ *                for the exact recompute)
+ * Returns ADAGIO_E_INVALID_ARG for any other value.  Adopted by the next call.
+ */
+#define ADAGIO_TILES_AUTO 0
+#define ADAGIO_TILES_SINGLE 1
+#define ADAGIO_TILES_PAIR 2
+int adagio_set_tile_kernel(adagio_ctx *ctx, int variant, int chunk_steps);
+/* The tile kernel that certifies n points on ctx (1 = single, 2 = pair);
+ * queries the device on first use.  Negative on error. */
+int adagio_tile_kernel_for(adagio_ctx *ctx, int64_t n);
 
 /*
  * Error-model check of the certificate's fast path.  Runs the certificate of

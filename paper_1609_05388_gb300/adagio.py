@@ -29,6 +29,10 @@ E_UNSUPPORTED = -8
 PREC_FP32 = 0
 PREC_FP16X3 = 1
 PREC_BF16X3 = 2
+# tile kernels of the split-precision certificate (adagio_set_tile_kernel)
+TILES_AUTO = 0
+TILES_SINGLE = 1
+TILES_PAIR = 2
 JL_RADEMACHER = 0
 JL_GAUSSIAN = 1
 HIST_BINS = 64
@@ -146,6 +150,8 @@ def _load() -> ctypes.CDLL:
                                      ctypes.POINTER(FitOptsStruct), i32, vp]),
         "adagio_last_batch_stats": (i32, [vp, ctypes.POINTER(BatchStatsStruct)]),
         "adagio_set_timing": (i32, [vp, i32]),
+        "adagio_set_tile_kernel": (i32, [vp, i32, i32]),
+        "adagio_tile_kernel_for": (i32, [vp, i64]),
         "adagio_last_cert_stats": (i32, [vp, ctypes.POINTER(CertStatsStruct)]),
         "adagio_launch_count": (ctypes.c_uint64, []),
         "adagio_last_fit_stats": (i32, [vp, ctypes.POINTER(FitStatsStruct)]),
@@ -186,7 +192,8 @@ def exported_symbols() -> list[str]:
                         "adagio_mlp_get_params", "adagio_mlp_forward", "adagio_mlp_grad",
                         "adagio_mlp_train_step", "adagio_predict_m", "adagio_features",
                         "adagio_mlp_save", "adagio_mlp_load", "adagio_fit_batched",
-                        "adagio_last_batch_stats") if hasattr(LIB, n)]
+                        "adagio_last_batch_stats", "adagio_set_tile_kernel",
+                        "adagio_tile_kernel_for") if hasattr(LIB, n)]
 
 
 def launch_count() -> int:
@@ -284,6 +291,17 @@ class Context:
 
     def set_timing(self, enable: bool = True):
         self._check(LIB.adagio_set_timing(self.h, 1 if enable else 0))
+
+    def set_tile_kernel(self, variant: int, chunk_steps: int = 0):
+        """Tile kernel of split-precision certificates (TILES_AUTO, TILES_SINGLE or TILES_PAIR)
+        and the 64-wide K steps per tensor-core accumulator chunk (0 = default)."""
+        self._check(LIB.adagio_set_tile_kernel(self.h, int(variant), int(chunk_steps)))
+
+    def tile_kernel_for(self, n: int) -> int:
+        """The tile kernel (TILES_SINGLE or TILES_PAIR) that certifies n points."""
+        rc = LIB.adagio_tile_kernel_for(self.h, int(n))
+        self._check(min(rc, 0))
+        return rc
 
     def last_fit_stats(self) -> dict:
         st = FitStatsStruct()

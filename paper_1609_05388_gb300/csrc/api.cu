@@ -6,6 +6,7 @@
 #include "jl.cuh"
 #include "linalg.cuh"
 #include "pca.cuh"
+#include "tcgemm.cuh"
 #include "api_guard.cuh"
 
 #include <algorithm>
@@ -36,6 +37,13 @@ static void check_precision(int precision) {
 }
 
 extern "C" {
+
+int adagio_tile_kernel_for(adagio_ctx *ctx, int64_t n) {
+    API_BEGIN(ctx)
+    ADAGIO_REQUIRE(n >= 2, "n must be at least 2");
+    return tc_variant(ctx, n);
+    API_END(ctx)
+}
 
 int adagio_distortion(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
                       const float *Y, int m, int64_t ldy, double eps, double hist_lo,
@@ -97,7 +105,8 @@ int adagio_debug_tile_bounds(adagio_ctx *ctx, const float *X, int64_t n, int d, 
         ADAGIO_CUDA(cudaMemcpyAsync(out, dump, dump_bytes, cudaMemcpyDeviceToHost, st));
         ADAGIO_CUDA(cudaStreamSynchronize(st));
     }
-    for (long long t = 0; t < tiles; ++t) tile_coords(precision, T, t, &tile_ij[2 * t], &tile_ij[2 * t + 1]);
+    for (long long t = 0; t < tiles; ++t)
+        tile_coords(ctx, precision, n, t, &tile_ij[2 * t], &tile_ij[2 * t + 1]);
     return rc;
     API_END(ctx)
 }
@@ -109,20 +118,25 @@ int adagio_embed(adagio_ctx *ctx, const float *A, int m, int d, int64_t lda, con
     ADAGIO_REQUIRE(n >= 1 && d >= 1 && m >= 1, "sizes must be positive");
     ADAGIO_REQUIRE(lda >= d && ldx >= d && ldy >= m, "leading dimensions too small");
     cudaStream_t st = (cudaStream_t)stream;
+    ADAGIO_REQUIRE(n <= (1ll << 30), "n must be at most 2^30");
     const bool y_dev = is_device_ptr(Y, ctx->device);
+    // tensor cores: per-row FP16 split planes of X and A, three products
     size_t need = staging_bytes(ctx, A, m, d) + staging_bytes(ctx, X, n, d) +
-                  (y_dev ? 0 : align_up((size_t)n * m * sizeof(float), 256)) + 4096;
+                  (y_dev ? 0 : align_up((size_t)n * m * sizeof(float), 256)) +
+                  embed_planes_bytes(ctx, n, d, m) + 4096;
     ws_reserve(ctx, need);
     int64_t la, lx;
     const float *dA = stage_input(ctx, A, m, d, lda, &la, st);
     const float *dX = stage_input(ctx, X, n, d, ldx, &lx, st);
     float *dY = y_dev ? Y : ws_array<float>(ctx, (size_t)n * m);
     const int64_t ly = y_dev ? ldy : m;
-    embed_gemm(dX, lx, n, d, dA, la, m, dY, ly, st);
+    EmbedPlanes ep;
+    embed_planes_init(ctx, dX, n, d, lx, m, ep, st);
+    embed_planes_run(ctx, ep, dA, m, la, dY, ly, st);
     if (!y_dev) {
         ADAGIO_CUDA(cudaMemcpy2DAsync(Y, (size_t)ldy * sizeof(float), dY, (size_t)m * sizeof(float),
                                       (size_t)m * sizeof(float), (size_t)n, cudaMemcpyDeviceToHost, st));
-        ADAGIO_CUDA(cudaStreamSynchronize(st));
+        check_device_status(ctx, st);
     }
     return ADAGIO_OK;
     API_END(ctx)
@@ -158,11 +172,12 @@ int adagio_pca(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx, i
     adagio_fit_opts o;
     if (opts) o = *opts; else adagio_default_fit_opts(&o);
     cudaStream_t st = (cudaStream_t)stream;
-    ws_reserve(ctx, staging_bytes(ctx, X, n, d) + pca_bytes(n, d, s, o.oversample) + 4096);
+    ws_reserve(ctx, staging_bytes(ctx, X, n, d) + pca_bytes(ctx, n, d, s, o.oversample, o.precision != ADAGIO_PREC_FP32) + 4096);
     int64_t lx;
     const float *dX = stage_input(ctx, X, n, d, ldx, &lx, st);
     PCA pca;
-    pca.init(ctx, dX, n, d, lx, s, o.seed, o.max_iter, o.tol, o.oversample, st);
+    pca.init(ctx, dX, n, d, lx, s, o.seed, o.max_iter, o.tol, o.oversample,
+             o.precision != ADAGIO_PREC_FP32, st);
     pca.extend(s, st);
     if (is_device_ptr(P, ctx->device)) {
         copy_rows(pca.P, d, P, ldp, s, d, st);

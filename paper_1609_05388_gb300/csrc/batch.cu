@@ -22,6 +22,7 @@
 #include "linalg.cuh"
 #include "pca.cuh"
 #include "search.cuh"
+#include "tcgemm.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -44,6 +45,7 @@ struct Inst {
     int cap = 0, s_cap = 0, k_cap = 0, fixed_s = -1;
     PCA pca;
     float *S = nullptr, *A = nullptr, *Abest = nullptr, *T = nullptr, *Y = nullptr;
+    EmbedPlanes ep;                  // X split once for every probe's embedding
     float *feats = nullptr;
     PrepMat px;
     unsigned *xflags = nullptr;
@@ -133,12 +135,13 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
             I.k_cap = p.m - I.s_cap;
             if (p.feats) I.s_cap = std::max(I.s_cap, std::min(64, d));
         }
-        ws_fixed += pca_bytes(p.n, d, I.s_cap, o.oversample);
+        ws_fixed += pca_bytes(ctx, p.n, d, I.s_cap, o.oversample, o.precision != ADAGIO_PREC_FP32);
         ws_fixed += align_up((size_t)std::max(I.k_cap, 1) * d * sizeof(float), 256);
         ws_fixed += 2 * align_up((size_t)std::max(I.cap, 1) * d * sizeof(float), 256);
         ws_fixed += align_up((size_t)std::max(I.k_cap, 1) * std::max(I.s_cap, 1) * sizeof(float), 256);
         ws_fixed += align_up((size_t)p.n * std::max(I.cap, 1) * sizeof(float), 256);
         ws_fixed += cert_prep_x_bytes(p.n, d, o.precision) + cert_job_bytes(ctx, p.n, I.cap, o.precision);
+        ws_fixed += align_up(embed_planes_bytes(ctx, p.n, d, I.cap), 256);
         ws_fixed += 3 * 256 + align_up(68 * sizeof(float), 256);
         ws_round += prep_bytes(p.n, std::max(I.cap, 1), !tc, tc);
         // a batch re-reserves its queues on every call: start at 1/64 of the
@@ -175,6 +178,7 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
     for (auto &e : ev) ADAGIO_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     cert_init();
     linalg_init();
+    tc_gemm_init();
     for (int i = 0; i < count; ++i) {
         Inst &I = in[i];
         I.sidx = 1 + i % nstreams;
@@ -183,7 +187,7 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
         I.pca.hbuf = hb + hslot * i + align_up(sizeof(CertDevResult), 64);
         I.hx = reinterpret_cast<unsigned *>(hb + hslot * i + align_up(sizeof(CertDevResult), 64) +
                                             align_up(pca_host_bytes(), 64));
-        if (tc) tc_prepare(ctx, (int)((I.pub->n + kTileRows - 1) / kTileRows));
+        if (tc) tc_prepare(ctx, I.pub->n);
     }
     int *hpred = reinterpret_cast<int *>(hb + hslot * count + 64);
     float *feats_all = ws_array<float>(ctx, (size_t)count * 68);
@@ -256,12 +260,13 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
         for (Inst &I : in) {
             const adagio_instance &p = *I.pub;
             I.pca.init_enqueue(ctx, p.X, p.n, p.d, p.ldx, I.s_cap, o.seed, o.max_iter, o.tol,
-                               o.oversample, I.st);
+                               o.oversample, o.precision != ADAGIO_PREC_FP32, I.st);
             I.S = ws_array<float>(ctx, (size_t)std::max(I.k_cap, 1) * p.d);
             I.A = ws_array<float>(ctx, (size_t)std::max(I.cap, 1) * p.d);
             I.Abest = ws_array<float>(ctx, (size_t)std::max(I.cap, 1) * p.d);
             I.T = ws_array<float>(ctx, (size_t)std::max(I.k_cap, 1) * std::max(I.s_cap, 1));
             I.Y = ws_array<float>(ctx, (size_t)p.n * std::max(I.cap, 1));
+            embed_planes_init(ctx, p.X, p.n, p.d, p.ldx, I.cap, I.ep, I.st);
             I.xflags = ws_array<unsigned>(ctx, 1);
             ADAGIO_CUDA(cudaMemsetAsync(I.xflags, 0, sizeof(unsigned), I.st));
             cert_prepare_x(ctx, p.X, p.ldx, p.n, p.d, o.precision, I.px, I.xflags, I.st);
@@ -301,7 +306,7 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
         const int s = I.split_s(r), k = r - s;
         if (k > 0) jl_matrix(o.seed, k, p.d, o.jl_dist, I.S, p.d, I.st);
         assemble(I.pca.P, s, p.d, I.S, k, p.d, p.d, I.A, p.d, I.T, I.st);
-        embed_gemm(p.X, p.ldx, p.n, p.d, I.A, p.d, r, I.Y, r, I.st);
+        embed_planes_run(ctx, I.ep, I.A, r, p.d, I.Y, r, I.st);
         I.job.Y = I.Y;
         I.job.ldy = r;
         I.job.m = r;
@@ -464,7 +469,7 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
         ADAGIO_CUDA(cudaEventRecord(ev[s], ctx->batch_streams[s]));
         ADAGIO_CUDA(cudaStreamWaitEvent(user, ev[s], 0));
     }
-    ADAGIO_CUDA(cudaStreamSynchronize(user));
+    check_device_status(ctx, user);  // synchronises
     bs.total_ms = std::chrono::duration<double, std::milli>(clk::now() - t0).count();
     ctx->last_batch = bs;
     return ADAGIO_OK;

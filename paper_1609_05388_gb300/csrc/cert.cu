@@ -63,7 +63,7 @@ size_t cert_job_bytes(adagio_ctx *ctx, int64_t n, int m, int precision) {
     size_t b = prep_bytes(n, m, !tc, tc);
     b += align_up(sizeof(CertPartial) * (partial_slots(ctx, n, precision) + recompute_grid(ctx)), 256);
     b += 4 * 256 + align_up(sizeof(CertDevResult), 256);
-    if (tc) b += align_up((size_t)((n + 127) / 128 * 128) * sizeof(float4), 256);
+    if (tc) b += align_up((size_t)pad_rows(n) * sizeof(float4), 256);
     return b + 1024;
 }
 
@@ -88,7 +88,7 @@ void cert_job_setup(adagio_ctx *ctx, CertJob &job, int2 *queue, unsigned long lo
     job.rparts = ws_array<CertPartial>(ctx, job.rgrid);
     job.dres = ws_array<CertDevResult>(ctx, 1);
     const bool tc = job.opt.precision != ADAGIO_PREC_FP32;
-    const int64_t n_pad = (job.n + kTileRows - 1) / kTileRows * kTileRows;
+    const int64_t n_pad = pad_rows(job.n);
     job.rs_xy = tc ? ws_array<float4>(ctx, (size_t)n_pad) : nullptr;
     job.queue = queue;
     job.qcap = qcap;
@@ -188,7 +188,7 @@ int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_
     const bool tc = opt.precision != ADAGIO_PREC_FP32;
     const unsigned long long pairs = (unsigned long long)n * (unsigned long long)(n - 1) / 2;
     if (!ctx->qbuf_fixed) cert_ensure_queue(ctx, cert_queue_capacity(pairs));
-    if (tc) tc_prepare(ctx, (int)((n + kTileRows - 1) / kTileRows));
+    if (tc) tc_prepare(ctx, n);
     const size_t mark = ctx->ws.off;
     for (int attempt = 0; attempt < 2; ++attempt) {
         ctx->ws.off = mark;
@@ -235,7 +235,7 @@ int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_
         }
         cs.queued = h->qlen;
         cs.grid = job.nparts;
-        const int64_t T = (n + kTileRows - 1) / kTileRows;
+        const int64_t T = pad_rows(n) / kTileRows;
         cs.tiles = T * (T + 1) / 2;
         const int rc = cert_job_collect(job, *h, out, stopped);
         if (rc == ADAGIO_E_QUEUE_OVERFLOW) {
@@ -253,7 +253,8 @@ int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_
     return ADAGIO_E_QUEUE_OVERFLOW;
 }
 
-void tile_coords(int precision, int T, long long t, int *I, int *J) {
+void tile_coords(adagio_ctx *ctx, int precision, int64_t n, long long t, int *I, int *J) {
+    const int T = (int)(pad_rows(n) / kTileRows);
     if (precision == ADAGIO_PREC_FP32) {
         // row-major upper triangle (the SIMT kernel's order)
         int i = 0;
@@ -262,7 +263,7 @@ void tile_coords(int precision, int T, long long t, int *I, int *J) {
         *I = i;
         *J = i + (int)(t - off);
     } else {
-        tc_tile_coords(T, t, I, J);
+        tc_tile_coords(ctx, n, t, I, J);
     }
 }
 

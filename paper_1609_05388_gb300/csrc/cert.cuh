@@ -47,7 +47,12 @@ void cert_simt_init();
 void recompute_init();
 // every certificate kernel's attributes, set once (call before a capture)
 void cert_init();
-void tc_tile_coords(int T, long long t, int *I, int *J);
+// 128-row block coordinates of 128 x 128 tile unit u of the tensor-core kernel
+void tc_tile_coords(adagio_ctx *ctx, int64_t n, long long u, int *I, int *J);
+// tensor-core tile kernel for n points: 1 = one CTA per tile, 2 = CTA pairs
+int tc_variant(adagio_ctx *ctx, int64_t n);
+// K steps per TMEM accumulator chunk of the tensor-core kernel (1 or 2)
+int tc_chunk_steps(adagio_ctx *ctx);
 
 // Exact recompute of the queued pairs from the original (uncentred) inputs.
 void launch_recompute(const float *X, int64_t ldx, int d, const float *Y, int64_t ldy, int m,
@@ -73,9 +78,9 @@ struct CertOptions {
     long long dump_tiles = 0;
 };
 
-// Tile coordinates of the t-th tile pair the tile kernel of `precision`
-// visits (host side, for diagnostics).
-void tile_coords(int precision, int T, long long t, int *I, int *J);
+// 128-row block coordinates of the t-th 128 x 128 tile the tile kernel of
+// `precision` visits for n points (host side, for diagnostics).
+void tile_coords(adagio_ctx *ctx, int precision, int64_t n, long long t, int *I, int *J);
 int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_t ldy, int64_t n,
             int d, int m, const CertOptions &opt, adagio_cert *out, cudaStream_t st,
             bool *stopped = nullptr, const PrepMat *px_ready = nullptr);
@@ -117,8 +122,8 @@ void cert_job_enqueue(adagio_ctx *ctx, CertJob &job, cudaStream_t st, cudaEvent_
 int cert_job_collect(const CertJob &job, const CertDevResult &h, adagio_cert *out, bool *stopped);
 unsigned long long cert_queue_capacity(unsigned long long pairs);
 void cert_ensure_queue(adagio_ctx *ctx, unsigned long long cap);
-// tensor path: makes the tile schedule of T tile rows resident (call before capture)
-void tc_prepare(adagio_ctx *ctx, int T);
+// tensor path: makes the tile schedule for n points resident (call before capture)
+void tc_prepare(adagio_ctx *ctx, int64_t n);
 
 
 }  // namespace adagio

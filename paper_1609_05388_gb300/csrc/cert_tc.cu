@@ -1,56 +1,70 @@
 // K8 (tensor-core path): all-pairs distortion tiles on tcgen05.
 //
-// One persistent CTA per SM walks 128 x 128 tiles (I, J), I <= J, of the
-// pair matrix in the band order of the schedule table (bands of 8 tile rows,
-// so the I-tiles of a band stay in L2 while the J-tiles stream).  For every
-// tile it forms
+// Persistent CTAs walk tiles (I, J), I <= J, of the pair matrix in the band
+// order of the schedule table (bands of tile rows, so the I-tiles of a band
+// stay in L2 while the J-tiles stream).  For every tile they form
 //     Gy = Yc[I] Yc[J]^T   and   Gx = Xc[I] Xc[J]^T
 // from 2-term split planes (hi + lo, FP16 or BF16, power-of-two scaled) with
 // three products hi.hi + hi.lo + lo.hi per K chunk, accumulated in FP32 in
-// tensor memory chunk by chunk, and hands the sums to the epilogue (cert_common.cuh),
-// which classifies every pair (Eq. 2), accumulates max / histogram / counts
-// and queues the pairs that need the exact recompute.
+// tensor memory chunk by chunk, and hand the sums to the epilogue
+// (cert_common.cuh), which classifies every pair (Eq. 2), accumulates max /
+// histogram / counts and queues the pairs that need the exact recompute.
 //
-// Roles (320 threads):
+// Two variants share the code:
+//   single  one CTA per 128 x 128 tile (tcgen05 cta_group::1, M = N = 128)
+//   pair    a cluster of two CTAs per 256 x 128 tile (cta_group::2, M = 256,
+//           N = 128): each CTA loads its own 128 rows of the I block and half
+//           of the 128 J rows, the leader CTA issues the MMAs for both, and
+//           each CTA's tensor memory receives its own 128 x 128 quarter-tile.
+//           Per multiply-add this moves 25 % fewer bytes through L2 and
+//           shared memory than the single variant (the MMA reads 6 KB of
+//           operands per 128 x 128 x 16 step instead of 8 KB).
+//
+// Roles (320 threads per CTA):
 //   warp 0      TMA producer: 4 planes (A hi/lo, B hi/lo) of 64 K-elements per
-//               stage, 3 stages of 64 KB, 128-byte swizzle
-//   warp 1      TMEM owner (512 columns = 4 chunk slots of 128) and MMA issuer:
-//               tcgen05.mma kind::f16, M = N = 128, K = 16.  Every 64-element K
-//               step goes to a fresh slot, cross products (hi.lo, lo.hi) first
-//               and the 4 hi.hi products last: the FP32 accumulator loses up to
-//               one unit in the last place per MMA (it truncates), so this
-//               bounds the full-size roundings to 4 per chunk
+//               stage, 128-byte swizzle
+//   warp 1      TMEM owner (512 columns = 2 chunk slots of 128 + 256 staging
+//               columns) and, in the single CTA or the pair's leader, MMA
+//               issuer: tcgen05.mma kind::f16, K = 16.  Every chunk of one
+//               (default) or two 64-element K steps goes to a fresh slot, the
+//               cross products (hi.lo, lo.hi) of its steps first and the hi.hi
+//               products last: the FP32 accumulator loses up to one unit in
+//               the last place per MMA (it truncates), so this bounds the
+//               full-size roundings to 4 per K step of the chunk
 //   warps 2..9  epilogue: two warps per TMEM lane quarter, 64 columns each;
 //               they drain every slot into register running sums (round to
 //               nearest) and classify their 64 pairs at the end of a tile,
 //               without data-dependent branches
-// The producer decides the tile sequence and sends it down the pipeline (a
-// tile index per first stage, -1 to stop, forwarded through a slot), so early
-// exit needs no CTA-wide barrier, and the epilogue warps never wait on one
-// another.  Every wait is bounded: on timeout the role records a status word
-// and leaves, the producer drains its in-flight copies, the MMA warp waits
-// for its last commit, and TMEM is freed.
+// The producer (in a pair, the leader's producer, which hands every decision
+// to the peer's producer through its shared memory) decides the tile
+// sequence and sends it down the pipeline (a tile index per first stage, -1
+// to stop, forwarded through a slot), so early exit needs no grid-wide
+// barrier, and the epilogue warps never wait on one another.  Every wait is
+// bounded: on timeout the role records a status word and leaves, the
+// producers drain their in-flight copies, the MMA warp waits for its last
+// commit, and TMEM is freed.
 #include <cuda.h>
 
 #include "internal.cuh"
 #include "cert.cuh"
+#include "tc_ptx.cuh"
 
-#include <mutex>
 #include <vector>
 
 namespace adagio {
+
+using namespace tc;
 
 namespace {
 
 constexpr int kEpiWarps = 8;                                // two per TMEM lane quarter
 constexpr int kThreads = 64 + 32 * kEpiWarps;               // producer, MMA, epilogue
-constexpr int kStages = 3;
 constexpr int kSlots = 2;                                   // TMEM chunk accumulators
 constexpr int kTile = 128;
 constexpr int kKStep = 64;                                  // fp16 elements per stage row
+constexpr int kMaxChunkSteps = 2;                           // K steps per TMEM chunk slot (at most)
 constexpr int kEpiCols = 64;                                // columns per epilogue warp
-constexpr uint32_t kPlaneBytes = kTile * kKStep * 2;        // 16 KB
-constexpr uint32_t kStageBytes = 4 * kPlaneBytes;           // 64 KB
+constexpr uint32_t kAPlane = kTile * kKStep * 2;            // 16 KB: 128 rows of one plane
 constexpr uint32_t kStageCol = kSlots * kTile;              // finished Gram sums (gx | gy)
 constexpr uint32_t kTmemCols = kStageCol + 2 * kTile;       // 512
 static_assert(kTmemCols == 512, "TMEM holds 512 columns");
@@ -59,15 +73,15 @@ constexpr int kPieces = kEpiCols / kPiece;
 constexpr int kHistFlushTiles = 1000;                       // u16 counters: <= 64 per tile
 // per-thread histogram: two 16-bit bin counters per 32-bit word
 constexpr int kHistWords = kBins / 2;
-constexpr long long kSpinLimit = 4000000000ll;              // clock64 cycles (~2 s)
 
 struct TcArgs {
     const float4 *rs;          // per row: (|xc|^2, |yc|^2, q4x, q4y)
     float cx, cy;              // bound coefficients of (n2_i + n2_j) per side
     const float *scale_x, *scale_y;
-    const uint32_t *sched;     // (I << 16) | J per tile pair
+    const uint32_t *sched;     // (I << 16) | J per tile (pair variant: I counts 256-row blocks)
     long long ntp;
     int n, kx_steps, ky_steps;
+    int csteps;                // K steps per chunk slot (1 or 2)
     uint32_t idesc;
     CertConst cc;
     CertPartial *partials;     // [gridDim.x * kEpiWarps], one slot per epilogue warp
@@ -75,197 +89,34 @@ struct TcArgs {
     unsigned long long *qcount, qcap;
     int *stop_flag;
     int *status;
-    float4 *dump;              // optional: (dx2, dy2, ex, ey) of tile pairs t < dump_tiles
+    float4 *dump;              // optional: (dx2, dy2, ex, ey) of 128 x 128 tile units u < dump_tiles
     long long dump_tiles;
 };
 
-struct SmemLayout {
+// Shared-memory layout of one CTA.  The pair variant loads half of the J rows
+// per CTA, so its stages are smaller and there are four of them.
+template <bool PAIR>
+struct Layout {
+    static constexpr int kStages = PAIR ? 4 : 3;
+    static constexpr int kBRows = PAIR ? kTile / 2 : kTile;                   // J rows loaded here
+    static constexpr uint32_t kBPlane = kBRows * kKStep * 2;
+    static constexpr uint32_t kStageBytes = 2 * kAPlane + 2 * kBPlane;
+    static constexpr uint32_t kTxBytes = PAIR ? 2 * kStageBytes : kStageBytes;  // per full barrier
     static constexpr uint32_t stages = 0;
     static constexpr uint32_t hist = kStages * kStageBytes;                  // u32 [32][256]
     static constexpr uint32_t bars = hist + kHistWords * 32 * kEpiWarps * 4;
     static constexpr uint32_t cmd = bars + 256;                               // int [16]
-    static constexpr uint32_t tmem_ptr = cmd + 64;
+    static constexpr uint32_t dec = cmd + 64;                                 // int [4]
+    static constexpr uint32_t tmem_ptr = dec + 16;
     static constexpr uint32_t totals = tmem_ptr + 16;                         // WarpTotals [8]
     static constexpr uint32_t total = totals + 64 * kEpiWarps;
+    static constexpr size_t smem = total + 1024;                              // + alignment slack
+    static_assert(smem <= 232448, "tile kernel exceeds the 227 KB shared-memory limit");
+    static_assert(totals % 8 == 0, "per-warp totals need 8-byte alignment");
+    static_assert(kStageBytes % 1024 == 0 && kBPlane % 1024 == 0, "stage buffers need 1 KB alignment");
+    static_assert((2 * kStages + 2 * kSlots + 5) * 8 <= 256, "barriers exceed their area");
+    static_assert(kStages >= kMaxChunkSteps + 1, "a chunk's stages and one more must fit");
 };
-constexpr size_t kSmemBytes = SmemLayout::total + 1024;   // + alignment slack
-static_assert(kSmemBytes <= 232448, "tile kernel exceeds the 227 KB shared-memory limit");
-static_assert(SmemLayout::totals % 8 == 0, "per-warp totals need 8-byte alignment");
-
-// ------------------------------------------------------------------ PTX glue
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred P1;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n\t"
-        "selp.b32 %0, 1, 0, P1;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the completion of the phase with the given parity.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int *status, int code) {
-    if (mbar_try_wait(bar, parity)) return true;
-    const long long t0 = clock64();
-    while (true) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (clock64() - t0 > kSpinLimit) {
-            atomicCAS(status, 0, code);
-            return false;
-        }
-    }
-}
-
-// Warp-uniform bounded wait: lane 0 waits, every lane gets the outcome.
-__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, int *status, int code) {
-    int ok = 0;
-    if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, status, code) ? 1 : 0;
-    return __shfl_sync(0xffffffffu, ok, 0) != 0;
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int x, int y,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// SW128 K-major shared-memory matrix descriptor (tcgen05 format): start
-// address >> 4, leading byte offset 16 (unused for swizzled K-major), stride
-// byte offset 1024 (one 8-row x 128-byte swizzle atom), version 1, 128B swizzle.
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)(16 >> 4) << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-
-__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
-                                       uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-
-// 16 consecutive TMEM columns of this warp's lane quarter into registers.
-// The wait is part of the same statement, so no use of the registers can be
-// scheduled before the asynchronous load has completed.
-__device__ __forceinline__ void tmem_ld16_wait(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr)
-        : "memory");
-}
-
-// 64 consecutive TMEM columns (four x16 loads) with one wait.
-__device__ __forceinline__ void tmem_ld64_wait(uint32_t taddr, uint32_t (&r)[64]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%64];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%65];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%66];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%67];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]), "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]), "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]), "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]), "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-        : "r"(taddr), "r"(taddr + 16), "r"(taddr + 32), "r"(taddr + 48)
-        : "memory");
-}
-
-// Two 32-column pieces (at ta and tb; two x16 loads each) with one wait.
-__device__ __forceinline__ void tmem_ld32x2_wait(uint32_t ta, uint32_t tb, uint32_t (&a)[32],
-                                                 uint32_t (&b)[32]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%64];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%65];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%32, %33, %34, %35, %36, %37, %38, %39, %40, %41, %42, %43, %44, %45, %46, %47}, [%66];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%48, %49, %50, %51, %52, %53, %54, %55, %56, %57, %58, %59, %60, %61, %62, %63}, [%67];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(a[16]), "=r"(a[17]), "=r"(a[18]), "=r"(a[19]), "=r"(a[20]), "=r"(a[21]), "=r"(a[22]), "=r"(a[23]), "=r"(a[24]), "=r"(a[25]), "=r"(a[26]), "=r"(a[27]), "=r"(a[28]), "=r"(a[29]), "=r"(a[30]), "=r"(a[31]), "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]), "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15]), "=r"(b[16]), "=r"(b[17]), "=r"(b[18]), "=r"(b[19]), "=r"(b[20]), "=r"(b[21]), "=r"(b[22]), "=r"(b[23]), "=r"(b[24]), "=r"(b[25]), "=r"(b[26]), "=r"(b[27]), "=r"(b[28]), "=r"(b[29]), "=r"(b[30]), "=r"(b[31])
-        : "r"(ta), "r"(ta + 16), "r"(tb), "r"(tb + 16)
-        : "memory");
-}
-
-// Two 16-column pieces (at ta and tb) with one wait.
-__device__ __forceinline__ void tmem_ld16x2_wait(uint32_t ta, uint32_t tb, uint32_t (&a)[16],
-                                                 uint32_t (&b)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%32];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%33];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]), "=r"(a[15]), "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7]), "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]), "=r"(b[14]), "=r"(b[15])
-        : "r"(ta), "r"(tb)
-        : "memory");
-}
-
-// Two 8-column pieces (at ta and tb) with one wait.
-__device__ __forceinline__ void tmem_ld8x2_wait(uint32_t ta, uint32_t tb, uint32_t (&a)[8],
-                                                uint32_t (&b)[8]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 "
-        "{%0, %1, %2, %3, %4, %5, %6, %7}, [%16];\n\t"
-        "tcgen05.ld.sync.aligned.32x32b.x8.b32 "
-        "{%8, %9, %10, %11, %12, %13, %14, %15}, [%17];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]), "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]), "=r"(b[7])
-        : "r"(ta), "r"(tb)
-        : "memory");
-}
-
-// 16 registers into 16 consecutive TMEM columns of this warp's lane quarter.
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&v)[16]) {
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};"
-        :
-        : "r"(taddr), "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]), "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-        : "memory");
-}
-
-__device__ __forceinline__ void tmem_wait_st() {
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-}
 
 // Folds this warp's 32 per-thread counters of every bin into its partial
 // (the bins and their total, part of `pairs`).
@@ -377,27 +228,40 @@ __device__ __forceinline__ void classify_piece(const float (&gx)[kPiece], const 
 }
 
 // ---------------------------------------------------------------- the kernel
-template <bool DUMP>
+template <bool DUMP, bool PAIR>
 __global__ void __launch_bounds__(kThreads, 1)
     cert_tc_kernel(const __grid_constant__ CUtensorMap map_xh, const __grid_constant__ CUtensorMap map_xl,
                    const __grid_constant__ CUtensorMap map_yh, const __grid_constant__ CUtensorMap map_yl,
+                   const __grid_constant__ CUtensorMap bmap_xh, const __grid_constant__ CUtensorMap bmap_xl,
+                   const __grid_constant__ CUtensorMap bmap_yh, const __grid_constant__ CUtensorMap bmap_yl,
                    TcArgs p) {
+    using L = Layout<PAIR>;
+    constexpr int kStages = L::kStages;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte alignment of the stage buffers (128-byte swizzle atoms), by
-    // an offset from the shared array so the address space stays known
+    // an offset from the shared array so the address space stays known; the
+    // offset is the same in both CTAs of a pair, which the MMA relies on
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
     const uint32_t sbase = smem_u32(smem);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // identity: the pair's two CTAs share a tile sequence; rank 0 leads
+    const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
+    const bool leader = rank == 0;
+    const long long unit0 = PAIR ? (long long)cluster_id_x() : (long long)blockIdx.x;
+    const long long ustride = PAIR ? (long long)ncluster_x() : (long long)gridDim.x;
 
-    uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem + SmemLayout::hist);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + SmemLayout::bars);
-    int *s_cmd = reinterpret_cast<int *>(smem + SmemLayout::cmd);  // [kStages] stage, [kStages + s] slot
-    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + SmemLayout::tmem_ptr);
+    uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem + L::hist);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::bars);
+    int *s_cmd = reinterpret_cast<int *>(smem + L::cmd);  // [kStages] stage, [kStages + s] slot
+    int *s_dec = reinterpret_cast<int *>(smem + L::dec);  // pair: the leader's decisions for the peer
+    uint32_t *s_tmem = reinterpret_cast<uint32_t *>(smem + L::tmem_ptr);
     const uint32_t bar_full = smem_u32(bars);                 // [kStages]
     const uint32_t bar_empty = bar_full + 8 * kStages;        // [kStages]
     const uint32_t bar_sfull = bar_empty + 8 * kStages;       // [kSlots]
     const uint32_t bar_sempty = bar_sfull + 8 * kSlots;       // [kSlots]
     const uint32_t bar_done = bar_sempty + 8 * kSlots;        // MMA drain
+    const uint32_t bar_dfull = bar_done + 8;                  // [2] pair: decision posted (peer)
+    const uint32_t bar_dempty = bar_dfull + 16;               // [2] pair: decision taken (leader)
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -406,73 +270,136 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int s = 0; s < kSlots; ++s) {
             mbar_init(bar_sfull + 8 * s, 1);
-            mbar_init(bar_sempty + 8 * s, 32 * kEpiWarps);
+            // one arrival per epilogue warp (of both CTAs of a pair)
+            mbar_init(bar_sempty + 8 * s, kEpiWarps * (PAIR ? 2 : 1));
         }
         mbar_init(bar_done, 1);
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(bar_dfull + 8 * q, 1);
+            mbar_init(bar_dempty + 8 * q, 1);
+        }
         for (int q = 0; q < 16; ++q) s_cmd[q] = 0;
+        for (int q = 0; q < 4; ++q) s_dec[q] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
     for (int e = threadIdx.x; e < kHistWords * 32 * kEpiWarps; e += kThreads) s_hist[e] = 0;
     if (warp == 1) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                         smem_u32(s_tmem)),
-                     "r"(kTmemCols)
-                     : "memory");
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        if (PAIR) {
+            // collective with the peer CTA's warp 1: the same columns in both
+            asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(s_tmem)),
+                         "r"(kTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+        } else {
+            asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                             smem_u32(s_tmem)),
+                         "r"(kTmemCols)
+                         : "memory");
+            asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        }
     }
     tc_fence_before();
-    __syncthreads();
+    // a pair: no CTA touches the other's barriers before both are initialised
+    if (PAIR)
+        cluster_sync();
+    else
+        __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *s_tmem;
     const int ksteps = p.ky_steps + p.kx_steps;
+    // chunks of up to p.csteps K steps: X chunks first, then Y chunks
+    const int cs = p.csteps;
+    const int xchunks = (p.kx_steps + cs - 1) / cs;
+    const int nchunks = xchunks + (p.ky_steps + cs - 1) / cs;
+    auto chunk_steps = [&](int c) {
+        return c < xchunks ? min(cs, p.kx_steps - c * cs) : min(cs, p.ky_steps - (c - xchunks) * cs);
+    };
 
     if (warp == 0) {
         // ------------------------------------------------------ TMA producer
+        // Both CTAs of a pair load the same stages of the same tiles: each its
+        // own 128 I rows and its half of the J rows; every copy completes on
+        // the leader's full barrier, which expects the bytes of both.
         int stage = 0;
         uint32_t phase = 0;
         bool ok = true;
         uint32_t issued_parity[kStages];
         bool issued[kStages];
         for (int s = 0; s < kStages; ++s) issued[s] = false, issued_parity[s] = 0;
-        long long t = blockIdx.x;
-        while (ok) {
-            bool stop = t >= p.ntp;
-            if (!stop && p.stop_flag) {
-                int f = 0;
-                if (lane == 0) f = *(volatile int *)p.stop_flag;
-                stop = __shfl_sync(0xffffffffu, f, 0) != 0;
+        const uint32_t full_tgt = PAIR ? mapa(bar_full, 0) : bar_full;
+        long long t = unit0;
+        for (long long k = 0; ok; ++k, t += ustride) {
+            bool stop;
+            const int q = (int)(k & 1);
+            const uint32_t use = (uint32_t)(k >> 1) & 1u;
+            if (leader) {
+                stop = t >= p.ntp;
+                if (!stop && p.stop_flag) {
+                    int f = 0;
+                    if (lane == 0) f = *(volatile int *)p.stop_flag;
+                    stop = __shfl_sync(0xffffffffu, f, 0) != 0;
+                }
+                if (PAIR) {
+                    // post the decision in the peer's shared memory (decision
+                    // slot q, once the peer has taken the one posted two tiles ago)
+                    ok = warp_wait<true>(bar_dempty + 8 * q, use ^ 1u, p.status, 1);
+                    if (!ok) break;
+                    if (lane == 0) {
+                        st_cluster_u32(mapa(smem_u32(s_dec + q), 1), stop ? 0xFFFFFFFFu : 1u);
+                        mbar_arrive_cluster(mapa(bar_dfull + 8 * q, 1));
+                    }
+                    __syncwarp();
+                }
+            } else {
+                ok = warp_wait<true>(bar_dfull + 8 * q, use, p.status, 1);
+                if (!ok) break;
+                int dec = 0;
+                if (lane == 0) {
+                    dec = ((volatile int *)s_dec)[q];
+                    mbar_arrive_cluster(mapa(bar_dempty + 8 * q, 0));
+                }
+                stop = __shfl_sync(0xffffffffu, dec, 0) < 0;
             }
             if (stop) {
-                if (lane == 0 && mbar_wait(bar_empty + 8 * stage, phase ^ 1, p.status, 1)) {
-                    s_cmd[stage] = -1;
-                    mbar_arrive(bar_full + 8 * stage);
+                if (leader) {
+                    if (lane == 0 && mbar_wait<PAIR>(bar_empty + 8 * stage, phase ^ 1, p.status, 1)) {
+                        s_cmd[stage] = -1;
+                        mbar_arrive(bar_full + 8 * stage);
+                    }
+                    // the empty wait proved the stage's last copy was consumed,
+                    // and the stop arrive moved its full barrier one phase on:
+                    // nothing of this stage is left to drain
+                    issued[stage] = false;
                 }
-                // the empty wait proved the stage's last copy was consumed, and
-                // the stop arrive moved its full barrier one phase on: nothing
-                // of this stage is left to drain
-                issued[stage] = false;
                 __syncwarp();
                 break;
             }
             const uint32_t packed = p.sched[t];
             const int I = (int)(packed >> 16), J = (int)(packed & 0xFFFF);
+            const int arow = PAIR ? I * 2 * kTile + (int)rank * kTile : I * kTile;
+            const int brow = J * kTile + (int)rank * L::kBRows;
             for (int ks = 0; ks < ksteps; ++ks) {
-                ok = warp_wait(bar_empty + 8 * stage, phase ^ 1, p.status, 1);
+                ok = warp_wait<PAIR>(bar_empty + 8 * stage, phase ^ 1, p.status, 1);
                 if (!ok) break;
                 if (lane == 0) {
-                    if (ks == 0) s_cmd[stage] = (int)t;
-                    const uint32_t bar = bar_full + 8 * stage;
-                    mbar_arrive_expect_tx(bar, kStageBytes);
-                    const uint32_t dst = sbase + SmemLayout::stages + stage * kStageBytes;
+                    if (leader) {
+                        if (ks == 0) s_cmd[stage] = (int)t;
+                        mbar_arrive_expect_tx(bar_full + 8 * stage, L::kTxBytes);
+                    }
+                    const uint32_t bar = full_tgt + 8 * stage;
+                    const uint32_t dst = sbase + L::stages + stage * L::kStageBytes;
                     const bool is_y = ks >= p.kx_steps;
                     const int k0 = (is_y ? ks - p.kx_steps : ks) * kKStep;
                     const CUtensorMap *mh = is_y ? &map_yh : &map_xh;
                     const CUtensorMap *ml = is_y ? &map_yl : &map_xl;
-                    tma_load_2d(dst, mh, k0, I * kTile, bar);
-                    tma_load_2d(dst + kPlaneBytes, ml, k0, I * kTile, bar);
-                    tma_load_2d(dst + 2 * kPlaneBytes, mh, k0, J * kTile, bar);
-                    tma_load_2d(dst + 3 * kPlaneBytes, ml, k0, J * kTile, bar);
+                    const CUtensorMap *bh = is_y ? &bmap_yh : &bmap_xh;
+                    const CUtensorMap *bl = is_y ? &bmap_yl : &bmap_xl;
+                    tma_load_2d<PAIR>(dst, mh, k0, arow, bar);
+                    tma_load_2d<PAIR>(dst + kAPlane, ml, k0, arow, bar);
+                    tma_load_2d<PAIR>(dst + 2 * kAPlane, bh, k0, brow, bar);
+                    tma_load_2d<PAIR>(dst + 2 * kAPlane + L::kBPlane, bl, k0, brow, bar);
                 }
                 __syncwarp();
                 issued[stage] = true;
@@ -482,86 +409,131 @@ __global__ void __launch_bounds__(kThreads, 1)
                     phase ^= 1;
                 }
             }
-            t += gridDim.x;
         }
-        // drain: every issued copy must have landed before the CTA can exit
+        // drain: every issued copy must have landed before the CTA can exit.
+        // The leader's full barriers count the copies of both CTAs; the peer
+        // waits until the MMA has consumed its last copies (every started
+        // tile is consumed whole).
         if (lane == 0)
             for (int s = 0; s < kStages; ++s)
-                if (issued[s]) mbar_wait(bar_full + 8 * s, issued_parity[s], p.status, 1);
+                if (issued[s]) {
+                    if (leader)
+                        mbar_wait<PAIR>(bar_full + 8 * s, issued_parity[s], p.status, 1);
+                    else
+                        mbar_wait<true>(bar_empty + 8 * s, issued_parity[s], p.status, 1);
+                }
         __syncwarp();
     } else if (warp == 1) {
         // ------------------------------------------------------- MMA issuer
-        // Every K step accumulates into a fresh TMEM slot (128 columns): first
-        // the 8 small cross-term products (hi.lo, lo.hi), then the 4 large
-        // hi.hi products, so only 4 FP32 accumulator roundings per chunk act
-        // on full-size partial sums.  The epilogue drains the slot.
-        int stage = 0, slot = 0;
-        uint32_t phase = 0, sphase = 0;
-        bool any = false;
-        bool ok = true;
-        while (ok) {
-            int t = -1;
-            ok = warp_wait(bar_full + 8 * stage, phase, p.status, 2);
-            if (!ok) break;
-            if (lane == 0) t = s_cmd[stage];
-            t = __shfl_sync(0xffffffffu, t, 0);
-            if (t < 0) {
-                // forward the stop to the epilogue through the next slot; the
-                // plain arrive releases the store of the stop word
-                if (lane == 0 && mbar_wait(bar_sempty + 8 * slot, sphase ^ 1, p.status, 2)) {
-                    s_cmd[kStages + slot] = -1;
-                    mbar_arrive(bar_sfull + 8 * slot);
+        // Every chunk of p.csteps K steps accumulates into a fresh TMEM slot
+        // (128 columns): first the small cross-term products (hi.lo, lo.hi) of
+        // its steps, then the large hi.hi products, so only 4 FP32
+        // accumulator roundings per K step act on full-size partial sums.  The
+        // epilogue drains the slot.  A chunk never mixes X and Y steps.  In a
+        // pair only the leader issues; the peer's warp 1 only holds TMEM.
+        if (leader) {
+            int stage = 0, slot = 0;
+            uint32_t phase = 0, sphase = 0;
+            bool any = false;
+            bool ok = true;
+            auto cross = [&](int st, uint32_t d, uint32_t accumulate_first) {
+                const uint32_t a0 = sbase + L::stages + st * L::kStageBytes;
+                const uint64_t ah = sw128_desc(a0), al = sw128_desc(a0 + kAPlane);
+                const uint64_t bh = sw128_desc(a0 + 2 * kAPlane);
+                const uint64_t bl = sw128_desc(a0 + 2 * kAPlane + L::kBPlane);
+#pragma unroll
+                for (int kk = 0; kk < kKStep / 16; ++kk) {
+                    const uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 elements = 32 bytes
+                    tc_mma<PAIR>(d, ah + off, bl + off, p.idesc, (kk == 0) ? accumulate_first : 1u);
+                    tc_mma<PAIR>(d, al + off, bh + off, p.idesc, 1u);
                 }
-                __syncwarp();
-                break;
-            }
-            for (int ks = 0; ks < ksteps; ++ks) {
-                if (ks > 0) {
-                    ok = warp_wait(bar_full + 8 * stage, phase, p.status, 2);
-                    if (!ok) break;
+            };
+            auto full_size = [&](int st, uint32_t d) {
+                const uint32_t a0 = sbase + L::stages + st * L::kStageBytes;
+                const uint64_t ah = sw128_desc(a0), bh = sw128_desc(a0 + 2 * kAPlane);
+#pragma unroll
+                for (int kk = 0; kk < kKStep / 16; ++kk) {
+                    const uint64_t off = (uint64_t)(kk * 32) >> 4;
+                    tc_mma<PAIR>(d, ah + off, bh + off, p.idesc, 1u);
                 }
-                ok = warp_wait(bar_sempty + 8 * slot, sphase ^ 1, p.status, 2);
+            };
+            while (ok) {
+                int t = -1;
+                ok = warp_wait<PAIR>(bar_full + 8 * stage, phase, p.status, 2);
                 if (!ok) break;
-                tc_fence_after();
-                if (lane == 0) {
+                if (lane == 0) t = s_cmd[stage];
+                t = __shfl_sync(0xffffffffu, t, 0);
+                if (t < 0) {
+                    // forward the stop to the epilogues through the next slot;
+                    // the plain (release) arrive publishes the stop word
+                    if (lane == 0 && mbar_wait<PAIR>(bar_sempty + 8 * slot, sphase ^ 1, p.status, 2)) {
+                        s_cmd[kStages + slot] = -1;
+                        if (PAIR) st_cluster_u32(mapa(smem_u32(s_cmd + kStages + slot), 1), 0xFFFFFFFFu);
+                        mbar_arrive(bar_sfull + 8 * slot);
+                        if (PAIR) mbar_arrive_cluster(mapa(bar_sfull + 8 * slot, 1));
+                    }
+                    __syncwarp();
+                    break;
+                }
+                for (int c = 0; c < nchunks; ++c) {
+                    const int nst = chunk_steps(c);
+                    if (c > 0) {
+                        ok = warp_wait<PAIR>(bar_full + 8 * stage, phase, p.status, 2);
+                        if (!ok) break;
+                    }
+                    ok = warp_wait<PAIR>(bar_sempty + 8 * slot, sphase ^ 1, p.status, 2);
+                    if (!ok) break;
+                    tc_fence_after();
                     const uint32_t d = tmem_base + (uint32_t)(slot * kTile);
-                    const uint32_t a0 = sbase + SmemLayout::stages + stage * kStageBytes;
-                    const uint64_t ah = sw128_desc(a0), al = sw128_desc(a0 + kPlaneBytes);
-                    const uint64_t bh = sw128_desc(a0 + 2 * kPlaneBytes);
-                    const uint64_t bl = sw128_desc(a0 + 3 * kPlaneBytes);
-#pragma unroll
-                    for (int kk = 0; kk < kKStep / 16; ++kk) {
-                        const uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 elements = 32 bytes
-                        tc_mma(d, ah + off, bl + off, p.idesc, kk == 0 ? 0u : 1u);
-                        tc_mma(d, al + off, bh + off, p.idesc, 1u);
+                    const int st0 = stage;
+                    int st1 = stage + 1;
+                    uint32_t ph1 = phase;
+                    if (st1 == kStages) {
+                        st1 = 0;
+                        ph1 ^= 1;
                     }
-#pragma unroll
-                    for (int kk = 0; kk < kKStep / 16; ++kk) {
-                        const uint64_t off = (uint64_t)(kk * 32) >> 4;
-                        tc_mma(d, ah + off, bh + off, p.idesc, 1u);
+                    if (lane == 0) {
+                        cross(st0, d, 0u);
+                        any = true;
                     }
-                    tc_commit(bar_empty + 8 * stage);
-                    tc_commit(bar_sfull + 8 * slot);
-                    any = true;
-                }
-                __syncwarp();
-                if (++stage == kStages) {
-                    stage = 0;
-                    phase ^= 1;
-                }
-                if (++slot == kSlots) {
-                    slot = 0;
-                    sphase ^= 1;
+                    __syncwarp();
+                    if (nst == 2) {
+                        ok = warp_wait<PAIR>(bar_full + 8 * st1, ph1, p.status, 2);
+                        if (!ok) break;
+                        tc_fence_after();
+                        if (lane == 0) cross(st1, d, 1u);
+                        __syncwarp();
+                    }
+                    if (lane == 0) {
+                        full_size(st0, d);
+                        tc_commit<PAIR>(bar_empty + 8 * st0);
+                        if (nst == 2) {
+                            full_size(st1, d);
+                            tc_commit<PAIR>(bar_empty + 8 * st1);
+                        }
+                        tc_commit<PAIR>(bar_sfull + 8 * slot);
+                        any = true;
+                    }
+                    __syncwarp();
+                    for (int q = 0; q < nst; ++q)
+                        if (++stage == kStages) {
+                            stage = 0;
+                            phase ^= 1;
+                        }
+                    if (++slot == kSlots) {
+                        slot = 0;
+                        sphase ^= 1;
+                    }
                 }
             }
+            // all issued MMAs must be complete before TMEM is released
+            any = __shfl_sync(0xffffffffu, any ? 1 : 0, 0) != 0;
+            if (lane == 0 && any) {
+                tc_commit_local<PAIR>(bar_done);
+                mbar_wait(bar_done, 0, p.status, 2);
+            }
+            __syncwarp();
         }
-        // all issued MMAs must be complete before TMEM is released
-        any = __shfl_sync(0xffffffffu, any ? 1 : 0, 0) != 0;
-        if (lane == 0 && any) {
-            tc_commit(bar_done);
-            mbar_wait(bar_done, 0, p.status, 2);
-        }
-        __syncwarp();
     } else {
         // --------------------------------------------------------- epilogue
         // Warp e owns TMEM lane quarter (warp % 4), i.e. tile row r, and the
@@ -580,6 +552,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
         const uint32_t gx_stage = tmem_base + lane_addr + kStageCol + (uint32_t)(h * kEpiCols);
         const uint32_t gy_run = gx_stage + kTile;
+        // the slot-drained barrier is the leader's
+        const uint32_t sempty_tgt = PAIR ? mapa(bar_sempty, 0) : bar_sempty;
         CertPartial *mine = p.partials + (size_t)blockIdx.x * kEpiWarps + ew;
         int slot = 0;
         uint32_t sphase = 0;
@@ -595,7 +569,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             k.w = p.cc.w;
             k.eps = p.cc.eps;
         }
-        WarpTotals *wt = reinterpret_cast<WarpTotals *>(smem + SmemLayout::totals) + ew;
+        WarpTotals *wt = reinterpret_cast<WarpTotals *>(smem + L::totals) + ew;
         if (lane == 0) {
             wt->violations = wt->overflow = wt->queued = 0;
             wt->sum = wt->bound_sum = 0.0;
@@ -608,7 +582,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // the tile waiting for (or in) classification
         bool pend = false;
         int pend_pieces = 0;
-        long long pend_t = 0;
+        long long pend_u = 0;
         int pend_i = 0, pend_j0 = 0;
         float4 pend_ri = make_float4(0.f, 0.f, 0.f, 0.f);
         unsigned long long pend_vmask = 0ull, qmask = 0ull;
@@ -626,8 +600,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 px[c] = valid ? __uint_as_float(ux[c]) : __int_as_float(0x7fc00000);
                 py[c] = __uint_as_float(uy[c]);
             }
-            if (DUMP && p.dump && pend_t < p.dump_tiles) {
-                float4 *drow = p.dump + (size_t)pend_t * kTile * kTile + r * kTile + h * kEpiCols + c0;
+            if (DUMP && p.dump && pend_u < p.dump_tiles) {
+                float4 *drow = p.dump + (size_t)pend_u * kTile * kTile + r * kTile + h * kEpiCols + c0;
                 classify_piece<DUMP>(px, py, pend_ri, p.rs + pend_j0 + c0, c0, k, hrow, acc, qmask, drow);
             } else {
                 classify_piece<false>(px, py, pend_ri, p.rs + pend_j0 + c0, c0, k, hrow, acc, qmask,
@@ -682,27 +656,27 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         };
 
-        long long t = blockIdx.x;               // the producer's static tile sequence
+        long long t = unit0;                    // the producer's static tile sequence
         bool ok = true;
         while (ok) {
             float gx[kEpiCols];
 #pragma unroll
             for (int c = 0; c < kEpiCols; ++c) gx[c] = 0.0f;
             bool stop = false;
-            for (int ks = 0; ks < ksteps; ++ks) {
-                ok = warp_wait(bar_sfull + 8 * slot, sphase, p.status, 3);
+            for (int c = 0; c < nchunks; ++c) {
+                ok = warp_wait<PAIR>(bar_sfull + 8 * slot, sphase, p.status, 3);
                 if (!ok) break;
                 tc_fence_after();
-                if (ks == 0) {
+                if (c == 0) {
                     int cmdv = 0;
-                    if (lane == 0) cmdv = s_cmd[kStages + slot];
+                    if (lane == 0) cmdv = ((volatile int *)s_cmd)[kStages + slot];
                     if (__shfl_sync(0xffffffffu, cmdv, 0) < 0) {
                         stop = true;
                         break;
                     }
                 }
                 const uint32_t ta = tmem_base + lane_addr + (uint32_t)(slot * kTile + h * kEpiCols);
-                if (ks < p.kx_steps) {
+                if (c < xchunks) {
                     // X chunk: registers, all 64 columns behind one wait
                     uint32_t v[64];
                     tmem_ld64_wait(ta, v);
@@ -710,8 +684,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int c = 0; c < kEpiCols; ++c) gx[c] += __uint_as_float(v[c]);
                 } else {
                     // Y chunk: the running columns (the first Y chunk starts them)
-                    if (ks == p.kx_steps && pend) finish_pending();
-                    const bool first = ks == p.kx_steps;
+                    if (c == xchunks && pend) finish_pending();
+                    const bool first = c == xchunks;
 #pragma unroll
                     for (int hh = 0; hh < kEpiCols / 32; ++hh) {
                         uint32_t v[32], w[32];
@@ -730,14 +704,25 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tmem_wait_st();
                 }
+                // the slot is drained: one arrival per warp on the (leader's) barrier
                 tc_fence_before();
-                mbar_arrive(bar_sempty + 8 * slot);
+                __syncwarp();
+                if (lane == 0) {
+                    if (PAIR)
+                        mbar_arrive_cluster(sempty_tgt + 8 * slot);
+                    else
+                        mbar_arrive(sempty_tgt + 8 * slot);
+                }
                 if (++slot == kSlots) {
                     slot = 0;
                     sphase ^= 1;
                 }
-                // one piece of the previous tile between X-chunk drains
-                if (ks < p.kx_steps && pend && pend_pieces < kPieces) classify_next();
+                // pieces of the previous tile between X-chunk drains, spread so
+                // that all of them are done by the last X chunk
+                if (c < xchunks && pend) {
+                    const int target = ((c + 1) * kPieces + xchunks - 1) / xchunks;
+                    while (pend_pieces < target) classify_next();
+                }
             }
             if (!ok || stop) break;
             // this tile's Y chunks have started the running columns, so the
@@ -753,19 +738,21 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_wait_st();
             const uint32_t packed = p.sched[t];
             const int I = (int)(packed >> 16), J = (int)(packed & 0xFFFF);
+            // this CTA's 128-row block of the tile
+            const int Ib = PAIR ? 2 * I + (int)rank : I;
             pend = true;
             pend_pieces = 0;
-            pend_t = t;
-            pend_i = I * kTile + r;
+            pend_u = PAIR ? 2 * t + (long long)rank : t;
+            pend_i = Ib * kTile + r;
             pend_ri = __ldg(p.rs + pend_i);
             pend_j0 = J * kTile + h * kEpiCols;
             // the 64 column statistics the classification reads, one lane per
             // pair of rows: in L1 by the time the next tile's drains begin
             asm volatile("prefetch.global.L1 [%0];" ::"l"(p.rs + pend_j0 + 2 * lane));
             pend_vmask = ~0ull;
-            if (!((I < J) && (J * kTile + kTile <= p.n))) {
-                // diagonal or ragged tile: columns that are not pairs i < j < n
-                // get a NaN Gram entry and their queue bit is cleared
+            if (!((Ib < J) && (J * kTile + kTile <= p.n))) {
+                // diagonal, below-diagonal or ragged tile: columns that are not
+                // pairs i < j < n get a NaN Gram entry and their queue bit is cleared
                 for (int c = 0; c < kEpiCols; ++c) {
                     const int j = pend_j0 + c;
                     if (!((pend_i < j) & (j < p.n))) pend_vmask &= ~(1ull << c);
@@ -773,7 +760,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             qmask = 0ull;
             acc = RowAcc{0.0f, 0.0f, 0.0f, -1.0f, 0, 0, 0, 0};
-            t += gridDim.x;
+            t += ustride;
         }
         // the last tile (its sums are complete in TMEM)
         if (ok && pend) finish_pending();
@@ -795,13 +782,23 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 
     tc_fence_before();
-    __syncthreads();
+    // a pair: both CTAs are done with each other's barriers and shared memory
+    if (PAIR)
+        cluster_sync();
+    else
+        __syncthreads();
     tc_fence_after();
     if (warp == 1) {
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                     "r"(kTmemCols)
-                     : "memory");
+        if (PAIR)
+            asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                         "r"(kTmemCols)
+                         : "memory");
+        else
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                         "r"(kTmemCols)
+                         : "memory");
     }
+    if (PAIR) cluster_sync();
 }
 
 __global__ void pack_row_stats(const RowStat *__restrict__ rx, const RowStat *__restrict__ ry,
@@ -810,44 +807,13 @@ __global__ void pack_row_stats(const RowStat *__restrict__ rx, const RowStat *__
     if (r < n_pad) out[r] = make_float4(rx[r].n2, ry[r].n2, rx[r].q4, ry[r].q4);
 }
 
-// ------------------------------------------------------------------ host side
-using EncodeFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                              const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                              const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                              CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-EncodeFn encode_fn() {
-    static EncodeFn fn = nullptr;
-    static std::once_flag once;
-    std::call_once(once, [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<EncodeFn>(p);
-    });
-    if (!fn) fail(ADAGIO_E_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    return fn;
-}
-
-CUtensorMap plane_map(const uint16_t *plane, int64_t rows, int cols, bool bf16) {
-    CUtensorMap m;
-    const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    const cuuint32_t box[2] = {(cuuint32_t)kKStep, (cuuint32_t)kTile};
-    const cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode_fn()(&m, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16,
-                             2, const_cast<uint16_t *>(plane), dims, strides, box, estr,
-                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) fail(ADAGIO_E_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
-    return m;
-}
-
-// Band order of the upper triangle: bands of kBand tile rows; in a band, J
-// runs left to right and I over the band's rows with I <= J.
+// Band orders of the upper triangle.  Single: bands of kBand tile rows; in a
+// band, J runs left to right and I over the band's rows with I <= J.  Pair:
+// tiles of 256 I rows x 128 J rows (I counts 256-row blocks), bands of
+// kBandPair such blocks (the same 1024 rows), J >= 2 I (the tiles that hold
+// pairs i < j).
 constexpr int kBand = 8;
+constexpr int kBandPair = 4;
 
 std::vector<uint32_t> band_schedule(int T) {
     std::vector<uint32_t> s;
@@ -860,16 +826,88 @@ std::vector<uint32_t> band_schedule(int T) {
     return s;
 }
 
+std::vector<uint32_t> band_schedule_pair(int T) {
+    const int T2 = T / 2;
+    std::vector<uint32_t> s;
+    s.reserve((size_t)T2 * (T2 + 1));
+    for (int b0 = 0; b0 < T2; b0 += kBandPair) {
+        const int b1 = std::min(T2, b0 + kBandPair);
+        for (int J = 2 * b0; J < T; ++J)
+            for (int I = b0; I < b1 && 2 * I <= J; ++I) s.push_back(((uint32_t)I << 16) | (uint32_t)J);
+    }
+    return s;
+}
+
 }  // namespace
 
-// Per-context cache of the device copy of the schedule.
-// The schedule of T tile rows, resident on the device for the context's
-// lifetime (built on first use: a synchronous upload, so callers that capture
-// graphs make it resident first with tc_prepare).
-static const uint32_t *schedule_for(adagio_ctx *ctx, int T) {
-    auto it = ctx->tc_sched.find(T);
-    if (it != ctx->tc_sched.end()) return it->second;
-    std::vector<uint32_t> s = band_schedule(T);
+// K steps per TMEM chunk slot: one by default (a tighter error bound, and so
+// fewer pairs for the exact recompute), two when the context asks for it
+int tc_chunk_steps(adagio_ctx *ctx) { return ctx->tc_chunk == 2 ? 2 : 1; }
+
+// 128-row tile blocks of a prepared matrix of n rows
+static int tile_blocks(int64_t n) { return (int)(pad_rows(n) / kTile); }
+
+// raises the kernels' dynamic shared-memory limit (once per device)
+void cert_tc_init() {
+    set_max_dyn_smem((const void *)cert_tc_kernel<true, false>, (int)Layout<false>::smem);
+    set_max_dyn_smem((const void *)cert_tc_kernel<false, false>, (int)Layout<false>::smem);
+    set_max_dyn_smem((const void *)cert_tc_kernel<true, true>, (int)Layout<true>::smem);
+    set_max_dyn_smem((const void *)cert_tc_kernel<false, true>, (int)Layout<true>::smem);
+}
+
+static cudaLaunchConfig_t pair_config(unsigned ctas, cudaStream_t st, cudaLaunchAttribute *at) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ctas);
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = Layout<true>::smem;
+    cfg.stream = st;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+// CTA pairs of the pair variant that can be resident at once (0: none; the
+// single variant is used), queried once per context
+static int pair_capacity(adagio_ctx *ctx) {
+    if (ctx->tc_pair_clusters >= 0) return ctx->tc_pair_clusters;
+    cert_tc_init();
+    cudaLaunchAttribute at[1];
+    cudaLaunchConfig_t cfg = pair_config((unsigned)(ctx->num_sms / 2 * 2), nullptr, at);
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, (const void *)cert_tc_kernel<false, true>, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        nc = 0;
+    }
+    ctx->tc_pair_clusters = std::max(0, std::min(nc, ctx->num_sms / 2));
+    return ctx->tc_pair_clusters;
+}
+
+// Which tile kernel certifies n points: 1 = single CTA per tile, 2 = CTA
+// pair.  The context's setting decides; automatic takes the single CTA,
+// which measured faster on the MNIST-shaped workload (its epilogue, not the
+// operand traffic the pair saves, limits the tile rate).
+int tc_variant(adagio_ctx *ctx, int64_t n) {
+    if (pad_rows(n) % (2 * kTile) != 0) return 1;
+    if (ctx->tc_variant != 2) return 1;
+    return pair_capacity(ctx) > 0 ? 2 : 1;
+}
+
+// Per-context cache of the device copy of a schedule, by tile-block count and
+// variant, resident for the context's lifetime (built on first use: a
+// synchronous upload, so callers that capture graphs make it resident first
+// with tc_prepare).
+static const uint32_t *schedule_for(adagio_ctx *ctx, int T, int variant, long long *count) {
+    const int key = T * 4 + variant;
+    auto it = ctx->tc_sched.find(key);
+    if (it != ctx->tc_sched.end()) {
+        *count = variant == 2 ? (long long)(T / 2) * (T / 2 + 1) : (long long)T * (T + 1) / 2;
+        return it->second;
+    }
+    std::vector<uint32_t> s = variant == 2 ? band_schedule_pair(T) : band_schedule(T);
     uint32_t *dev = nullptr;
     ADAGIO_CUDA(cudaMalloc(&dev, s.size() * sizeof(uint32_t)));
     cudaError_t e = cudaMemcpy(dev, s.data(), s.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
@@ -877,66 +915,89 @@ static const uint32_t *schedule_for(adagio_ctx *ctx, int T) {
         cudaFree(dev);
         ADAGIO_CUDA(e);
     }
-    ctx->tc_sched[T] = dev;
+    ctx->tc_sched[key] = dev;
+    *count = (long long)s.size();
     return dev;
 }
 
-void tc_prepare(adagio_ctx *ctx, int T) { (void)schedule_for(ctx, T); }
+void tc_prepare(adagio_ctx *ctx, int64_t n) {
+    long long c;
+    (void)schedule_for(ctx, tile_blocks(n), tc_variant(ctx, n), &c);
+}
 
 // CTAs of one certificate launch: one per SM (the shared-memory footprint
 // allows one), never more than there are tiles, so that small problems of a
 // batch leave SMs to the others
 int cert_tc_ctas(adagio_ctx *ctx, int64_t n) {
-    const long long T = (n + kTile - 1) / kTile;
+    const long long T = tile_blocks(n);
+    if (tc_variant(ctx, n) == 2) {
+        const long long tiles = (T / 2) * (T / 2 + 1);
+        return 2 * (int)std::min<long long>(pair_capacity(ctx), tiles);
+    }
     const long long tiles = T * (T + 1) / 2;
     return (int)std::min<long long>(ctx->num_sms, tiles);
 }
 
-void tc_tile_coords(int T, long long t, int *I, int *J) {
-    const std::vector<uint32_t> s = band_schedule(T);
-    const uint32_t v = s.at((size_t)t);
-    *I = (int)(v >> 16);
-    *J = (int)(v & 0xFFFF);
-}
-
-// raises the kernels' dynamic shared-memory limit (once per device)
-void cert_tc_init() {
-    set_max_dyn_smem((const void *)cert_tc_kernel<true>, (int)kSmemBytes);
-    set_max_dyn_smem((const void *)cert_tc_kernel<false>, (int)kSmemBytes);
+// 128-row block coordinates (I, J) of 128 x 128 tile unit u (the unit index
+// of the per-pair dump): the u-th tile of the single schedule, or CTA u % 2
+// of the (u / 2)-th tile of the pair schedule
+void tc_tile_coords(adagio_ctx *ctx, int64_t n, long long u, int *I, int *J) {
+    const int T = tile_blocks(n);
+    if (tc_variant(ctx, n) == 2) {
+        const std::vector<uint32_t> s = band_schedule_pair(T);
+        const uint32_t v = s.at((size_t)(u >> 1));
+        *I = 2 * (int)(v >> 16) + (int)(u & 1);
+        *J = (int)(v & 0xFFFF);
+    } else {
+        const std::vector<uint32_t> s = band_schedule(T);
+        const uint32_t v = s.at((size_t)u);
+        *I = (int)(v >> 16);
+        *J = (int)(v & 0xFFFF);
+    }
 }
 
 bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     const PrepMat &x = *L.x, &y = *L.y;
     if (!x.hi || !y.hi) return false;
     if (x.n_pad / kTile >= 65536) return false;
+    const int variant = tc_variant(L.ctx, x.n);
+    const bool pair = variant == 2;
+    if (pair && (x.n_pad % (2 * kTile) != 0 || y.n_pad != x.n_pad))
+        fail(ADAGIO_E_CUDA, "internal: pair tiles need rows padded to 256 (n_pad %lld)",
+             (long long)x.n_pad);
     const bool bf16 = precision == ADAGIO_PREC_BF16X3;
-    const CUtensorMap mxh = plane_map(x.hi, x.n_pad, x.Kp16, bf16);
-    const CUtensorMap mxl = plane_map(x.lo, x.n_pad, x.Kp16, bf16);
-    const CUtensorMap myh = plane_map(y.hi, y.n_pad, y.Kp16, bf16);
-    const CUtensorMap myl = plane_map(y.lo, y.n_pad, y.Kp16, bf16);
+    const int brows = pair ? Layout<true>::kBRows : Layout<false>::kBRows;
+    const CUtensorMap mxh = plane_map(x.hi, x.n_pad, x.Kp16, kKStep, kTile, bf16);
+    const CUtensorMap mxl = plane_map(x.lo, x.n_pad, x.Kp16, kKStep, kTile, bf16);
+    const CUtensorMap myh = plane_map(y.hi, y.n_pad, y.Kp16, kKStep, kTile, bf16);
+    const CUtensorMap myl = plane_map(y.lo, y.n_pad, y.Kp16, kKStep, kTile, bf16);
+    const CUtensorMap bxh = plane_map(x.hi, x.n_pad, x.Kp16, kKStep, brows, bf16);
+    const CUtensorMap bxl = plane_map(x.lo, x.n_pad, x.Kp16, kKStep, brows, bf16);
+    const CUtensorMap byh = plane_map(y.hi, y.n_pad, y.Kp16, kKStep, brows, bf16);
+    const CUtensorMap byl = plane_map(y.lo, y.n_pad, y.Kp16, kKStep, brows, bf16);
     TcArgs a;
     a.rs = reinterpret_cast<const float4 *>(L.rs_xy);
     pack_row_stats<<<(unsigned)ceil_div(x.n_pad, 256), 256, 0, st>>>(x.rs, y.rs, x.n_pad,
                                                                      (float4 *)L.rs_xy);
     ADAGIO_CHECK_LAUNCH();
     // ex = q4_i q4_j + (c_acc + c_r)(n2_i + n2_j) dominates the split model's
-    // q1 term, because 2 |a| |b| <= |a|^2 + |b|^2
-    a.cx = x.bm.cacc + L.cc.c_r;
-    a.cy = y.bm.cacc + L.cc.c_r;
+    // q1 term, because 2 |a| |b| <= |a|^2 + |b|^2; c_acc for this chunking
+    a.csteps = tc_chunk_steps(L.ctx);
+    a.cx = bound_model(precision, x.Kp16, a.csteps).cacc + L.cc.c_r;
+    a.cy = bound_model(precision, y.Kp16, a.csteps).cacc + L.cc.c_r;
     a.scale_x = x.scale;
     a.scale_y = y.scale;
     const int T = (int)(x.n_pad / kTile);
-    a.sched = schedule_for(L.ctx, T);
-    a.ntp = (long long)T * (T + 1) / 2;
+    a.sched = schedule_for(L.ctx, T, variant, &a.ntp);
     a.n = (int)x.n;
     a.kx_steps = x.Kp16 / kKStep;
     a.ky_steps = y.Kp16 / kKStep;
     // instruction descriptor, kind::f16: D = F32 (bits 4-5 = 1), A/B format
     // F16 = 0 / BF16 = 1 (bits 7-9, 10-12), K-major A and B, N >> 3 at bit
-    // 17, M >> 4 at bit 24
+    // 17, M >> 4 at bit 24 (M = 256 for the pair: 128 rows per CTA)
     const uint32_t fmt = bf16 ? 1u : 0u;
-    a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTile >> 3) << 17) |
-              ((uint32_t)(kTile >> 4) << 24);
+    const uint32_t M = pair ? 2 * kTile : kTile;
+    a.idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((uint32_t)(kTile >> 3) << 17) | ((M >> 4) << 24);
     a.cc = L.cc;
     a.partials = L.partials;
     a.queue = L.queue;
@@ -948,10 +1009,23 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     a.dump_tiles = L.dump_tiles;
     ADAGIO_CUDA(cudaMemsetAsync(L.partials, 0, sizeof(CertPartial) * L.grid, st));
     cert_tc_init();
-    if (L.dump)
-        cert_tc_kernel<true><<<L.grid / kEpiWarps, kThreads, kSmemBytes, st>>>(mxh, mxl, myh, myl, a);
-    else
-        cert_tc_kernel<false><<<L.grid / kEpiWarps, kThreads, kSmemBytes, st>>>(mxh, mxl, myh, myl, a);
+    const unsigned ctas = (unsigned)(L.grid / kEpiWarps);
+    if (pair) {
+        cudaLaunchAttribute at[1];
+        const cudaLaunchConfig_t cfg = pair_config(ctas, st, at);
+        if (L.dump)
+            ADAGIO_CUDA(cudaLaunchKernelEx(&cfg, cert_tc_kernel<true, true>, mxh, mxl, myh, myl, bxh, bxl,
+                                           byh, byl, a));
+        else
+            ADAGIO_CUDA(cudaLaunchKernelEx(&cfg, cert_tc_kernel<false, true>, mxh, mxl, myh, myl, bxh, bxl,
+                                           byh, byl, a));
+    } else {
+        const size_t sm = Layout<false>::smem;
+        if (L.dump)
+            cert_tc_kernel<true, false><<<ctas, kThreads, sm, st>>>(mxh, mxl, myh, myl, bxh, bxl, byh, byl, a);
+        else
+            cert_tc_kernel<false, false><<<ctas, kThreads, sm, st>>>(mxh, mxl, myh, myl, bxh, bxl, byh, byl, a);
+    }
     ADAGIO_CHECK_LAUNCH();
     return true;
 }

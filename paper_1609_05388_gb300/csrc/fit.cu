@@ -15,6 +15,7 @@
 #include "linalg.cuh"
 #include "pca.cuh"
 #include "search.cuh"
+#include "tcgemm.cuh"
 
 #include <algorithm>
 #include <chrono>
@@ -37,14 +38,44 @@ void assemble(const float *P, int s, int64_t ldp, const float *S, int k, int64_t
                                      MatView<float>{P, ldp, 1}, 1.0f, AS, lda, st);
 }
 
+size_t embed_planes_bytes(adagio_ctx *ctx, int64_t n, int d, int m_cap) {
+    const size_t planes = align_up((size_t)n * pad64(d) * sizeof(uint16_t), 256);
+    return 2 * planes + align_up((size_t)n * sizeof(float), 256) +
+           embed_tc_bytes(ctx, n, std::max(m_cap, 1), d) + 256;
+}
+
+void embed_planes_init(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx, int m_cap,
+                       EmbedPlanes &ep, cudaStream_t st) {
+    ADAGIO_REQUIRE(n <= (1ll << 30), "n must be at most 2^30");
+    const int Kd = pad64(d);
+    uint16_t *xh = ws_array<uint16_t>(ctx, (size_t)n * Kd), *xl = ws_array<uint16_t>(ctx, (size_t)n * Kd);
+    float *xs = ws_array<float>(ctx, (size_t)n);
+    split_rows(X, n, d, ldx, xh, xl, xs, st);
+    ep.Xp.hi = xh;
+    ep.Xp.lo = xl;
+    ep.Xp.rows = n;
+    ep.Xp.Kp = Kd;
+    ep.Xp.scale = xs;
+    ep.Xp.scale_stride = 1;
+    ep.n = n;
+    ep.d = d;
+    ep.scratch = ws_alloc(ctx, embed_tc_bytes(ctx, n, std::max(m_cap, 1), d));
+}
+
+void embed_planes_run(adagio_ctx *ctx, const EmbedPlanes &ep, const float *A, int m, int64_t lda,
+                      float *Y, int64_t ldy, cudaStream_t st) {
+    embed_tc(ctx, ep.Xp, ep.n, nullptr, A, m, ep.d, lda, Y, ldy, ep.scratch, st);
+}
+
 size_t fit_bytes(adagio_ctx *ctx, int64_t n, int d, int s_cap, int k_cap, int m_cap, int precision,
                  int oversample) {
-    size_t b = pca_bytes(n, d, s_cap, oversample);
+    size_t b = pca_bytes(ctx, n, d, s_cap, oversample, precision != ADAGIO_PREC_FP32);
     b += align_up((size_t)std::max(k_cap, 1) * d * sizeof(float), 256);          // S
     b += 2 * align_up((size_t)std::max(m_cap, 1) * d * sizeof(float), 256);      // A probe, A best
     b += align_up((size_t)std::max(k_cap, 1) * std::max(s_cap, 1) * sizeof(float), 256);  // T
     b += align_up((size_t)n * std::max(m_cap, 1) * sizeof(float), 256);          // Y
     b += certify_bytes(ctx, n, d, std::max(m_cap, 1), precision);
+    b += embed_planes_bytes(ctx, n, d, m_cap);
     return b + 65536;
 }
 
@@ -58,6 +89,7 @@ struct Prober {
     const adagio_fit_opts *o;
     PCA *pca;
     float *S, *A, *Abest, *T, *Y;
+    EmbedPlanes ep;            // X split once for every probe's embedding
     CertOptions copt;
     const PrepMat *px = nullptr;  // X prepared once for every probe's certificate
     int fixed_s;  // >= 0: every probe uses this many principal rows
@@ -82,9 +114,11 @@ struct Prober {
         assemble(pca->P, s, d, S, k, d, d, A, d, T, st);
     }
 
+    void embed(int r, cudaStream_t st) { embed_planes_run(ctx, ep, A, r, d, Y, r, st); }
+
     bool probe(int r, bool stop_early, cudaStream_t st) {
         build(r, st);
-        embed_gemm(X, ldx, n, d, A, d, r, Y, r, st);
+        embed(r, st);
         adagio_cert c;
         CertOptions co = copt;
         co.stop_early = stop_early;
@@ -133,7 +167,8 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
     const auto t_start = clk::now();
     double pca_ms = 0.0;
     PCA pca;
-    pca.init(ctx, X, n, d, ldx, s_cap, o->seed, o->max_iter, o->tol, o->oversample, st);
+    pca.init(ctx, X, n, d, ldx, s_cap, o->seed, o->max_iter, o->tol, o->oversample,
+             o->precision != ADAGIO_PREC_FP32, st);
     pca_ms += std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
     pca.elapsed_ms = &pca_ms;
     Prober pr{};
@@ -149,6 +184,7 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
     pr.Abest = ws_array<float>(ctx, (size_t)std::max(cap, 1) * d);
     pr.T = ws_array<float>(ctx, (size_t)std::max(k_cap, 1) * std::max(s_cap, 1));
     pr.Y = ws_array<float>(ctx, (size_t)n * std::max(cap, 1));
+    embed_planes_init(ctx, X, n, d, ldx, cap, pr.ep, st);
     const double eps = search ? o->eps : 0.1;
     pr.copt.eps = eps;
     pr.copt.precision = o->precision;
@@ -173,7 +209,7 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
     if (!search) {
         pr.build(cap, st);
         if (cert) {
-            embed_gemm(X, ldx, n, d, pr.A, d, cap, pr.Y, cap, st);
+            pr.embed(cap, st);
             certify(ctx, X, ldx, pr.Y, cap, n, d, cap, pr.copt, cert, st, nullptr, &px);
         }
         ADAGIO_CUDA(cudaMemcpyAsync(A_out, pr.A, sizeof(float) * (size_t)cap * d,
@@ -204,7 +240,7 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
         } else {
             // not certifiable at the cap: return the map at the cap and its full certificate
             pr.build(cap, st);
-            embed_gemm(X, ldx, n, d, pr.A, d, cap, pr.Y, cap, st);
+            pr.embed(cap, st);
             adagio_cert c;
             certify(ctx, X, ldx, pr.Y, cap, n, d, cap, pr.copt, &c, st, nullptr, &px);
             if (cert) *cert = c;
@@ -230,7 +266,7 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
         trace->pca_iterations = pca.iterations;
         trace->s_computed = pca.s_done;
     }
-    ADAGIO_CUDA(cudaStreamSynchronize(st));
+    check_device_status(ctx, st);  // synchronises
     ctx->last_fit.total_ms = std::chrono::duration<double, std::milli>(clk::now() - t_start).count();
     ctx->ws.off = mark;
     return status;

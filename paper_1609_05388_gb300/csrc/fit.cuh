@@ -3,6 +3,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "tcgemm.cuh"
 
 namespace adagio {
 
@@ -29,6 +30,22 @@ void assemble(const float *P, int s, int64_t ldp, const float *S, int k, int64_t
 
 size_t fit_bytes(adagio_ctx *ctx, int64_t n, int d, int s_cap, int k_cap, int m_cap, int precision,
                  int oversample);
+
+// The projection Y = X A^T (Algorithm 1) as adagio_embed computes it: per-row
+// FP16 split planes of the raw rows of X, made once and reused for every map
+// A (up to m_cap rows), and the tensor-core GEMM.  Every fit embeds this way,
+// so a returned certificate is the one of adagio_embed's Y, bit for bit.
+struct EmbedPlanes {
+    SplitPlanes Xp;
+    int64_t n = 0;
+    int d = 0;
+    void *scratch = nullptr;
+};
+size_t embed_planes_bytes(adagio_ctx *ctx, int64_t n, int d, int m_cap);
+void embed_planes_init(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx, int m_cap,
+                       EmbedPlanes &ep, cudaStream_t st);
+void embed_planes_run(adagio_ctx *ctx, const EmbedPlanes &ep, const float *A, int m, int64_t lda,
+                      float *Y, int64_t ldy, cudaStream_t st);
 
 // Fit on device data; A_out (device) gets m x d rows with leading dimension d.
 int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,

@@ -84,6 +84,14 @@ struct adagio_ctx {
     // tile schedules of the tensor-core certificate, by tile-row count T
     // (built once, resident for the context's lifetime)
     std::map<int, uint32_t *> tc_sched;
+    // tile kernel of the tensor-core certificate: 0 automatic, 1 one CTA per
+    // tile, 2 CTA pairs; and how many CTA pairs fit at once (-1: not queried)
+    int tc_variant = 0;
+    int tc_chunk = 0;  // K steps per TMEM chunk slot: 0 automatic (1), 1 or 2
+    int tc_pair_clusters = -1;
+    // device status word of the tensor-core GEMMs (nonzero: a bounded wait
+    // gave up); checked and cleared by the calls that synchronise
+    int *dev_status = nullptr;
     // streams and pinned host memory of batched fits (grown on demand)
     std::vector<cudaStream_t> batch_streams;
     void *batch_host = nullptr;
@@ -135,7 +143,12 @@ struct BoundModel {
     float c4;    // statistical product-error coefficient (times ||a||_4 ||b||_4)
     float cacc;  // accumulation coefficient (times ||a||_2 ||b||_2)
 };
-BoundModel bound_model(int precision, int K);
+// chunk_steps: 64-wide K steps per tensor-core accumulator chunk (1 or 2)
+BoundModel bound_model(int precision, int K, int chunk_steps = 1);
+
+// Synchronises st and fails with ADAGIO_E_TIMEOUT (clearing the word) when a
+// tensor-core GEMM enqueued on the context recorded a timeout.
+void check_device_status(adagio_ctx *ctx, cudaStream_t st);
 
 // Releases the dimension predictor held by a context (mlp.cu).
 void free_predictor(adagio_ctx *ctx);

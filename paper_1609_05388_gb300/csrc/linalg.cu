@@ -809,16 +809,6 @@ void gemm_tn_splitk(int M, int N, int64_t K, const float *A, int64_t lda, const 
     ADAGIO_CHECK_LAUNCH();
 }
 
-void embed_gemm(const float *X, int64_t ldx, int64_t n, int d, const float *A, int64_t lda, int m,
-                float *Y, int64_t ldy, cudaStream_t st) {
-    // row blocks of at most 2^20 rows keep every index in int range
-    for (int64_t r0 = 0; r0 < n; r0 += (1 << 20)) {
-        const int rows = (int)std::min<int64_t>(n - r0, 1 << 20);
-        gemm<float, float, float, float>(rows, m, d, 1.0f, MatView<float>{X + r0 * ldx, ldx, 1},
-                                         MatView<float>{A, 1, lda}, 0.0f, Y + r0 * ldy, ldy, st);
-    }
-}
-
 static size_t jacobi_smem(int b) {
     const size_t B = (size_t)((b + 1) & ~1);
     return (B * (B + 1) + B * ((B + 3) & ~(size_t)3)) * sizeof(float) + 16;

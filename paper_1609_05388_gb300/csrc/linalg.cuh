@@ -33,13 +33,9 @@ void gemm_f64_splitk(int M, int N, int K, MatView<float> A, MatView<float> B, do
                      double *partials, int kchunk, cudaStream_t st);
 constexpr int kF64Chunk = 32;
 
-// Y[n x m] = X[n x d] A[m x d]^T, both row-major (the embedding, Algorithm 1).
 // raises the shared-memory limits of the block kernels (Cholesky, TRSM,
 // Jacobi) to their largest block once, so later launches set no attribute
 void linalg_init();
-
-void embed_gemm(const float *X, int64_t ldx, int64_t n, int d, const float *A, int64_t lda, int m,
-                float *Y, int64_t ldy, cudaStream_t st);
 
 // Cholesky factorisation in place of an SPD b x b FP64 matrix (upper factor R,
 // G = R^T R), one CTA.  Pivots below `floor_rel * max diagonal` are raised

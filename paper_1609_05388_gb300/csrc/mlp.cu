@@ -485,11 +485,12 @@ int adagio_features(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t l
     const int s = std::min(64, d);
     const bool x_dev = is_device_ptr(X, ctx->device);
     ws_reserve(ctx, (x_dev ? 0 : align_up((size_t)n * d * sizeof(float), 256)) +
-                        pca_bytes(n, d, s, o.oversample) + 8192);
+                        pca_bytes(ctx, n, d, s, o.oversample, o.precision != ADAGIO_PREC_FP32) + 8192);
     int64_t lx;
     const float *dX = stage_input(ctx, X, n, d, ldx, &lx, st);
     PCA pca;
-    pca.init(ctx, dX, n, d, lx, s, o.seed, o.max_iter, o.tol, o.oversample, st);
+    pca.init(ctx, dX, n, d, lx, s, o.seed, o.max_iter, o.tol, o.oversample,
+             o.precision != ADAGIO_PREC_FP32, st);
     pca.extend(s, st);
     float *df = ws_array<float>(ctx, kIn);
     spectrum_features(pca.theta, pca.s_done, pca.C, d, n, eps, df, st);

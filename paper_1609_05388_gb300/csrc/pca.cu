@@ -31,11 +31,22 @@ static int64_t pca_part_floats(int d, int s_cap) {
     return (int64_t)8 * std::min(kJacobiMax, d) * std::max(d, std::max(s_cap, 1));
 }
 
-size_t pca_bytes(int64_t n, int d, int s_cap, int oversample) {
+size_t pca_bytes(adagio_ctx *ctx, int64_t n, int d, int s_cap, int oversample, bool tensor) {
     const int b = std::min(kJacobiMax, d);
-    size_t bytes = prep_bytes(n, d, true, false);
+    size_t bytes = prep_bytes(n, d, !tensor, false);
     bytes += align_up((size_t)d * d * sizeof(float), 256);                          // C
-    bytes += align_up((size_t)splitk_chunks(n) * d * d * sizeof(float), 256);       // partials
+    if (tensor) {
+        const int Kn = pad64(n), Kd = pad64(d);
+        bytes += 2 * align_up((size_t)d * Kn * sizeof(uint16_t), 256) + 256;       // X^T planes
+        bytes += align_up((size_t)tc_gemm_workspace(ctx, d, d, Kn, true) * sizeof(float), 256);
+        bytes += 2 * align_up((size_t)d * Kd * sizeof(uint16_t), 256);             // C planes
+        bytes += align_up((size_t)d * sizeof(float), 256);
+        bytes += 2 * align_up((size_t)b * Kd * sizeof(uint16_t), 256);             // V planes
+        bytes += align_up((size_t)b * sizeof(float), 256);
+        bytes += align_up((size_t)tc_gemm_workspace(ctx, b, d, Kd, false) * sizeof(float), 256);
+    } else {
+        bytes += align_up((size_t)splitk_chunks(n) * d * d * sizeof(float), 256);   // partials
+    }
     bytes += 3 * align_up((size_t)b * d * sizeof(float), 256);                      // V, W, T
     bytes += align_up((size_t)b * 32 * sizeof(float), 256);                         // Dinv
     bytes += align_up((size_t)std::max(s_cap, 1) * d * sizeof(float), 256);         // P
@@ -57,8 +68,9 @@ void *PCA::stage(size_t bytes) { return hbuf ? hbuf : host_stage(ctx, bytes); }
 
 void PCA::init_enqueue(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int64_t ldx,
                        int s_cap_, uint64_t seed_, int max_iter_, double tol_, int oversample_,
-                       cudaStream_t st) {
+                       bool tensor_, cudaStream_t st) {
     ctx = ctx_;
+    tensor = tensor_;
     n = n_;
     d = d_;
     s_cap = std::max(0, std::min(s_cap_, d_));
@@ -72,13 +84,45 @@ void PCA::init_enqueue(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int
     blk = Block{};
     flags = ws_array<unsigned>(ctx, 1);
     ADAGIO_CUDA(cudaMemsetAsync(flags, 0, sizeof(unsigned), st));
-    // centred FP32 copy (K0) and the covariance C = Xc^T Xc
+    // centring (K0) and the covariance C = Xc^T Xc: tensor cores from the
+    // transposed split planes of Xc, or FP32 SIMT from a centred copy
     PrepMat pm;
-    prep_matrix(ctx, X, n, d, ldx, ADAGIO_PREC_FP32, true, false, pm, flags, st);
+    prep_matrix(ctx, X, n, d, ldx, ADAGIO_PREC_FP32, !tensor, false, pm, flags, st);
     C = ws_array<float>(ctx, (size_t)d * d);
-    float *partials = ws_array<float>(ctx, (size_t)splitk_chunks(n) * d * d);
-    gemm_tn_splitk(d, d, n, pm.c32, pm.Kp32, pm.c32, pm.Kp32, C, d, partials, st);
     const int bmax = std::min(kJacobiMax, d);
+    if (tensor) {
+        const int Kn = pad64(n), Kd = pad64(d);
+        SplitPlanes XT;
+        uint16_t *xh = ws_array<uint16_t>(ctx, (size_t)d * Kn), *xl = ws_array<uint16_t>(ctx, (size_t)d * Kn);
+        float *xs = ws_array<float>(ctx, 1);
+        split_transpose_centred(X, n, d, ldx, pm.mu, pm.amax, xh, xl, xs, st);
+        XT.hi = xh;
+        XT.lo = xl;
+        XT.rows = d;
+        XT.Kp = Kn;
+        XT.scale = xs;
+        float *cpart = ws_array<float>(ctx, (size_t)std::max<int64_t>(1, tc_gemm_workspace(ctx, d, d, Kn, true)));
+        tc_gemm(ctx, XT, XT, d, d, nullptr, C, d, true, cpart, ctx->dev_status, st);
+        // planes of C (rows) and room for those of each block V
+        uint16_t *ch = ws_array<uint16_t>(ctx, (size_t)d * Kd), *cl = ws_array<uint16_t>(ctx, (size_t)d * Kd);
+        float *cs = ws_array<float>(ctx, d);
+        split_rows(C, d, d, d, ch, cl, cs, st);
+        Cp.hi = ch;
+        Cp.lo = cl;
+        Cp.rows = d;
+        Cp.Kp = Kd;
+        Cp.scale = cs;
+        Cp.scale_stride = 1;
+        Vp.hi = ws_array<uint16_t>(ctx, (size_t)bmax * Kd);
+        Vp.lo = ws_array<uint16_t>(ctx, (size_t)bmax * Kd);
+        Vp.scale = ws_array<float>(ctx, bmax);
+        Vp.Kp = Kd;
+        Vp.scale_stride = 1;
+        gpart = ws_array<float>(ctx, (size_t)std::max<int64_t>(1, tc_gemm_workspace(ctx, bmax, d, Kd, false)));
+    } else {
+        float *partials = ws_array<float>(ctx, (size_t)splitk_chunks(n) * d * d);
+        gemm_tn_splitk(d, d, n, pm.c32, pm.Kp32, pm.c32, pm.Kp32, C, d, partials, st);
+    }
     V = ws_array<float>(ctx, (size_t)bmax * d);
     W = ws_array<float>(ctx, (size_t)bmax * d);
     T = ws_array<float>(ctx, (size_t)bmax * d);
@@ -98,18 +142,53 @@ void PCA::init_enqueue(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int
     part = ws_array<float>(ctx, (size_t)part_floats);
     unsigned *hflag = reinterpret_cast<unsigned *>(stage(pca_host_bytes()));
     ADAGIO_CUDA(cudaMemcpyAsync(hflag, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+    copy_status(st);
+}
+
+// the tensor-core GEMMs' status word, copied beside the convergence data
+static constexpr size_t kStatusOff = (size_t)kJacobiMax * 12 + 64;
+
+void PCA::copy_status(cudaStream_t st) {
+    if (!tensor) return;
+    char *hs = reinterpret_cast<char *>(stage(pca_host_bytes()));
+    ADAGIO_CUDA(cudaMemcpyAsync(hs + kStatusOff, ctx->dev_status, sizeof(int), cudaMemcpyDeviceToHost, st));
+}
+
+void PCA::check_status() {
+    if (!tensor) return;
+    const int h = *reinterpret_cast<const int *>(reinterpret_cast<const char *>(stage(pca_host_bytes())) +
+                                                 kStatusOff);
+    if (h != 0) {
+        ADAGIO_CUDA(cudaMemset(ctx->dev_status, 0, sizeof(int)));
+        fail(ADAGIO_E_TIMEOUT, "tensor-core GEMM of the PCA gave up a bounded wait (status %d)", h);
+    }
 }
 
 void PCA::init_check() {
     const unsigned hflag = *reinterpret_cast<unsigned *>(stage(pca_host_bytes()));
     if (hflag & 1u) fail(ADAGIO_E_NONFINITE, "input holds NaN or Inf");
+    check_status();
 }
 
 void PCA::init(adagio_ctx *ctx_, const float *X, int64_t n_, int d_, int64_t ldx, int s_cap_,
-               uint64_t seed_, int max_iter_, double tol_, int oversample_, cudaStream_t st) {
-    init_enqueue(ctx_, X, n_, d_, ldx, s_cap_, seed_, max_iter_, tol_, oversample_, st);
+               uint64_t seed_, int max_iter_, double tol_, int oversample_, bool tensor_,
+               cudaStream_t st) {
+    init_enqueue(ctx_, X, n_, d_, ldx, s_cap_, seed_, max_iter_, tol_, oversample_, tensor_, st);
     ADAGIO_CUDA(cudaStreamSynchronize(st));
     init_check();
+}
+
+// out (b x d) = M C for the rows of M (C symmetric)
+void PCA::times_C(const float *M, int b, float *out, cudaStream_t st) {
+    if (tensor) {
+        Vp.rows = b;
+        split_rows(M, b, d, d, const_cast<uint16_t *>(Vp.hi), const_cast<uint16_t *>(Vp.lo),
+                   const_cast<float *>(Vp.scale), st);
+        tc_gemm(ctx, Vp, Cp, b, d, nullptr, out, d, false, gpart, ctx->dev_status, st);
+    } else {
+        gemm_f32(b, d, d, 1.0f, MatView<float>{const_cast<float *>(M), d, 1}, MatView<float>{C, d, 1},
+                 0.0f, out, d, part, part_floats, st);
+    }
 }
 
 // rows of M (r x d) <- M - (M P^T) P over the s_done finished directions
@@ -177,8 +256,7 @@ void PCA::advance(int s_needed, cudaStream_t st) {
     for (;;) {
         ++iterations;
         // W = V C (C symmetric)
-        gemm_f32(b, d, d, 1.0f, MatView<float>{V, d, 1}, MatView<float>{C, d, 1}, 0.0f, W, d, part,
-                 part_floats, st);
+        times_C(V, b, W, st);
         deflate(W, b, st);
         const int it = blk.it;
         blk.last = it == max_iter - 1 || b == blk.remaining;
@@ -207,6 +285,7 @@ void PCA::advance(int s_needed, cudaStream_t st) {
             ADAGIO_CUDA(cudaMemcpyAsync(hs, theta_blk, sizeof(double) * b, cudaMemcpyDeviceToHost, st));
             ADAGIO_CUDA(cudaMemcpyAsync(hs + (size_t)kJacobiMax * 8, res, sizeof(float) * s_blk,
                                         cudaMemcpyDeviceToHost, st));
+            copy_status(st);
             return;
         }
         // next iterate: V <- orth(W)
@@ -217,6 +296,7 @@ void PCA::advance(int s_needed, cudaStream_t st) {
 }
 
 void PCA::resolve(cudaStream_t st) {
+    check_status();
     const char *hs = reinterpret_cast<const char *>(stage(pca_host_bytes()));
     const double *hth = reinterpret_cast<const double *>(hs);
     const float *hres = reinterpret_cast<const float *>(hs + (size_t)kJacobiMax * 8);

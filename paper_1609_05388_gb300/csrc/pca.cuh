@@ -1,6 +1,7 @@
 #pragma once
 
 #include "internal.cuh"
+#include "tcgemm.cuh"
 
 #include <algorithm>
 
@@ -24,13 +25,18 @@ struct PCA {
     float *Dinv = nullptr;     // b x 32: inverses of the factor's diagonal blocks
     int64_t part_floats = 0;
     unsigned *flags = nullptr;
+    // tensor: the covariance and the products V C on tcgen05 from split
+    // planes (the split-precision fits); otherwise FP32 SIMT (the plain path)
+    bool tensor = false;
+    SplitPlanes Cp, Vp;        // tensor: planes of C and of the current block
+    float *gpart = nullptr;    // tensor: split-K partials of V C
     double *elapsed_ms = nullptr;  // optional: extend() adds its wall time here
     // pinned host buffer of at least pca_host_bytes() for the convergence
     // checks; null: the context's staging buffer at each use
     void *hbuf = nullptr;
 
     void init(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx, int s_cap,
-              uint64_t seed, int max_iter, double tol, int oversample, cudaStream_t st);
+              uint64_t seed, int max_iter, double tol, int oversample, bool tensor, cudaStream_t st);
     // make sure the first s_needed rows of P are computed (synchronises)
     void extend(int s_needed, cudaStream_t st);
 
@@ -41,7 +47,8 @@ struct PCA {
     // the host); resolve reads it after the caller synchronised the stream and
     // enqueues the next iteration or the acceptance of the block.
     void init_enqueue(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx, int s_cap,
-                      uint64_t seed, int max_iter, double tol, int oversample, cudaStream_t st);
+                      uint64_t seed, int max_iter, double tol, int oversample, bool tensor,
+                      cudaStream_t st);
     void init_check();
     bool needs(int s_needed) const { return s_done < std::min(s_needed, s_cap); }
     void advance(int s_needed, cudaStream_t st);
@@ -60,9 +67,13 @@ struct PCA {
     void accept_block(cudaStream_t st);
     void deflate(float *M, int r, cudaStream_t st);
     void orth(float *M, int b, cudaStream_t st);
+    void times_C(const float *M, int b, float *out, cudaStream_t st);  // out = M C
+    void copy_status(cudaStream_t st);
+    void check_status();
 };
 
-size_t pca_bytes(int64_t n, int d, int s_cap, int oversample);
+// tensor: the split-precision PCA (see PCA::tensor)
+size_t pca_bytes(adagio_ctx *ctx, int64_t n, int d, int s_cap, int oversample, bool tensor);
 size_t pca_host_bytes();
 
 }  // namespace adagio

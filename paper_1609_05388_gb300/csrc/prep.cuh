@@ -7,7 +7,10 @@
 
 namespace adagio {
 
-constexpr int kTileRows = 128;  // row padding of every prepared matrix
+constexpr int kTileRows = 128;  // tile height of the certificate kernels
+constexpr int kRowPad = 256;    // row padding of every prepared matrix (two tile heights)
+
+inline int64_t pad_rows(int64_t n) { return (n + kRowPad - 1) / kRowPad * kRowPad; }
 
 struct PrepMat {
     int64_t n = 0, n_pad = 0;
@@ -18,6 +21,7 @@ struct PrepMat {
     uint16_t *hi = nullptr;     // [n_pad][Kp16] split plane, high part
     uint16_t *lo = nullptr;     // [n_pad][Kp16] split plane, low part
     float *scale = nullptr;     // device scalar: power-of-two split scale
+    unsigned *amax = nullptr;   // device: max |x - mu| as float bits
     BoundModel bm{};
 };
 
@@ -29,7 +33,7 @@ void prep_matrix(adagio_ctx *ctx, const float *X, int64_t n, int K, int64_t ld, 
 
 // Workspace bytes prep_matrix needs.
 inline size_t prep_bytes(int64_t n, int K, bool want_c32, bool want_split) {
-    int64_t n_pad = (n + kTileRows - 1) / kTileRows * kTileRows;
+    int64_t n_pad = pad_rows(n);
     size_t Kp32 = align_up((size_t)K, 8), Kp16 = align_up((size_t)K, 64);
     size_t b = 0;
     b += align_up(K * sizeof(float), 256);

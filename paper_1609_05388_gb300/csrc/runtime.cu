@@ -94,6 +94,16 @@ bool is_device_ptr(const void *p, int device) {
     return false;
 }
 
+void check_device_status(adagio_ctx *ctx, cudaStream_t st) {
+    ADAGIO_CUDA(cudaStreamSynchronize(st));
+    int h = 0;
+    ADAGIO_CUDA(cudaMemcpy(&h, ctx->dev_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0) {
+        ADAGIO_CUDA(cudaMemset(ctx->dev_status, 0, sizeof(int)));
+        fail(ADAGIO_E_TIMEOUT, "tensor-core GEMM gave up a bounded wait (status %d)", h);
+    }
+}
+
 const float *stage_input(adagio_ctx *ctx, const float *p, int64_t rows, int cols, int64_t ld,
                          int64_t *ld_out, cudaStream_t st) {
     if (is_device_ptr(p, ctx->device)) {
@@ -148,10 +158,18 @@ int adagio_ctx_create(int device, size_t workspace_limit, adagio_ctx **out) {
                  device, prop.major, prop.minor);
         DeviceGuard g(device);
         ADAGIO_CUDA(cudaFree(nullptr));  // make sure the primary context exists
+        int *status = nullptr;
+        ADAGIO_CUDA(cudaMalloc(&status, 256));
+        cudaError_t e = cudaMemset(status, 0, 256);
+        if (e != cudaSuccess) {
+            cudaFree(status);
+            ADAGIO_CUDA(e);
+        }
         adagio_ctx *ctx = new adagio_ctx();
         ctx->device = device;
         ctx->num_sms = prop.multiProcessorCount;
         ctx->ws.limit = workspace_limit;
+        ctx->dev_status = status;
         *out = ctx;
         return ADAGIO_OK;
     } catch (const Error &e) {
@@ -178,6 +196,7 @@ int adagio_ctx_destroy(adagio_ctx *ctx) {
         for (auto &e : ctx->tc_sched) cudaFree(e.second);
         for (cudaStream_t s : ctx->batch_streams) cudaStreamDestroy(s);
         if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
+        if (ctx->dev_status) cudaFree(ctx->dev_status);
         if (prev >= 0) cudaSetDevice(prev);
     }
     delete ctx;
@@ -194,6 +213,15 @@ size_t adagio_workspace_bytes(const adagio_ctx *ctx) { return ctx ? ctx->ws.cap 
 int adagio_set_timing(adagio_ctx *ctx, int enable) {
     if (!ctx) return ADAGIO_E_INVALID_ARG;
     ctx->collect_timing = enable ? 1 : 0;
+    return ADAGIO_OK;
+}
+
+int adagio_set_tile_kernel(adagio_ctx *ctx, int variant, int chunk_steps) {
+    if (!ctx || variant < ADAGIO_TILES_AUTO || variant > ADAGIO_TILES_PAIR || chunk_steps < 0 ||
+        chunk_steps > 2)
+        return ADAGIO_E_INVALID_ARG;
+    ctx->tc_variant = variant;
+    ctx->tc_chunk = chunk_steps;
     return ADAGIO_OK;
 }
 

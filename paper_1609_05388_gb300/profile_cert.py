@@ -1,6 +1,6 @@
 """Runs certificates of the MNIST-shaped workload at a chosen size, for profilers.
 
-    python -m paper_1609_05388_gb300.profile_cert --n 16384 --m 400 --precision fp16x3 --reps 2
+    python -m paper_1609_05388_gb300.profile_cert --n 16384 --m 400 --precision fp16x3 --reps 2 [--tiles pair]
 
 The embedding is Y = X A^T with A = [P ; S (I - P^T P)] at dimension m, built
 from the library's PCA, JL matrix and assembly (no certificate runs before the
@@ -27,6 +27,8 @@ def main():
     ap.add_argument("--eps", type=float, default=0.1)
     ap.add_argument("--precision", default="fp16x3", choices=["fp32", "fp16x3", "bf16x3"])
     ap.add_argument("--reps", type=int, default=2)
+    ap.add_argument("--tiles", default="auto", choices=["auto", "single", "pair"],
+                    help="tile kernel of the split-precision certificate")
     a = ap.parse_args()
     prec = {"fp32": lib.PREC_FP32, "fp16x3": lib.PREC_FP16X3, "bf16x3": lib.PREC_BF16X3}[a.precision]
     wl = synth.mnist_like(seed=1, n=a.n)
@@ -37,12 +39,19 @@ def main():
         S = ctx.jl_matrix(11, a.m - s, X.shape[1])
         A = torch.from_numpy(ctx.assemble(P, S)).cuda()
         Y = ctx.embed(A, X)
+        ctx.set_tile_kernel({"auto": lib.TILES_AUTO, "single": lib.TILES_SINGLE,
+                             "pair": lib.TILES_PAIR}[a.tiles])
         ctx.set_timing(True)
+        tile_ms = []
         for _ in range(a.reps):
             c = ctx.distortion(X, Y, a.eps, precision=prec)
+            tile_ms.append(ctx.last_cert_stats()["tile_ms"])
         st = ctx.last_cert_stats()
-    print(json.dumps({"n": a.n, "m": a.m, "precision": a.precision, "pairs": c.pairs,
-                      "max": c.max, "recomputed": c.recomputed, **st}))
+        kernel = ctx.tile_kernel_for(a.n)
+    print(json.dumps({"n": a.n, "m": a.m, "precision": a.precision, "tiles": kernel,
+                      "pairs": c.pairs, "max": c.max, "mean": c.mean,
+                      "violations": c.violations, "recomputed": c.recomputed,
+                      "tile_ms_all": tile_ms, **st}))
 
 
 if __name__ == "__main__":

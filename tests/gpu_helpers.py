@@ -1,10 +1,17 @@
 """Shared helpers of the GPU parity tests."""
 import numpy as np
+import pytest
 
 from oracle.certificate import pair_distortion
 
 # Arithmetic of the certificate tiles exercised by the parity tests.
 PRECISIONS = (0, 1, 2)   # FP32 SIMT, FP16x3 and BF16x3 tensor cores
+
+# (arithmetic, tile kernel) of the certificate parity tests: the FP32 SIMT
+# tiles, and each split precision on single-CTA and CTA-pair tensor tiles
+CERT_MODES = [pytest.param(0, 0, id="fp32"),
+              pytest.param(1, 1, id="fp16x3-single"), pytest.param(1, 2, id="fp16x3-pair"),
+              pytest.param(2, 1, id="bf16x3-single"), pytest.param(2, 2, id="bf16x3-pair")]
 
 
 def assert_cert_parity(g, o, X, Y, max_tol=1e-5, mean_tol=1e-6):

@@ -47,9 +47,10 @@ def workload(name):
     return X, Y
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2])
+@pytest.mark.parametrize("prec,kernel", [(0, 0), (1, 1), (1, 2), (2, 1), (2, 2)])
 @pytest.mark.parametrize("name", ["mnist", "small", "powerlaw"])
-def test_fast_path_error_bound(ctx, prec, name):
+def test_fast_path_error_bound(ctx, prec, kernel, name):
+    ctx.set_tile_kernel(kernel)
     X, Y = workload(name)
     n = X.shape[0]
     T = (n + 127) // 128
@@ -71,7 +72,7 @@ def test_fast_path_error_bound(ctx, prec, name):
         rx.append(ratio_x[valid])
         ry.append(ratio_y[valid])
     rx, ry = np.concatenate(rx), np.concatenate(ry)
-    print(f"\n[bound] prec={prec} {name}: |err|/bound x max {rx.max():.3f} p99.9 "
+    print(f"\n[bound] prec={prec} kernel={kernel} {name}: |err|/bound x max {rx.max():.3f} p99.9 "
           f"{np.quantile(rx, 0.999):.3f} median {np.median(rx):.4f}; "
           f"y max {ry.max():.3f} p99.9 {np.quantile(ry, 0.999):.3f} median {np.median(ry):.4f}")
     assert rx.max() <= 1.0 and ry.max() <= 1.0

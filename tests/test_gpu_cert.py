@@ -2,7 +2,7 @@
 import numpy as np
 import pytest
 
-from gpu_helpers import PRECISIONS, assert_cert_parity
+from gpu_helpers import CERT_MODES, assert_cert_parity
 from oracle import adagio as O
 from oracle.certificate import certificate, pair_distortion
 from paper_1609_05388_gb300 import synth
@@ -24,105 +24,106 @@ def oracle_embedding(X, m, seed=3):
     return O.embed(f.A, X).astype(np.float32)
 
 
-def run(ctx, X, Y, eps, prec, lo=0.0, hi=0.0, device=True):
+def run(ctx, X, Y, eps, prec, lo=0.0, hi=0.0, device=True, tiles=0):
+    ctx.set_tile_kernel(tiles)
     if device:
         Xd, Yd = torch.from_numpy(X).cuda(), torch.from_numpy(Y).cuda()
         return ctx.distortion(Xd, Yd, eps, lo, hi, precision=prec)
     return ctx.distortion(X, Y, eps, lo, hi, precision=prec)
 
 
-@pytest.mark.parametrize("prec", PRECISIONS)
-def test_small_workload(ctx, prec):
+@pytest.mark.parametrize("prec,tiles", CERT_MODES)
+def test_small_workload(ctx, prec, tiles):
     wl = synth.small(seed=0)                     # 2000 x 64, 1 999 000 pairs
     Y = oracle_embedding(wl.X, 20)
-    g = run(ctx, wl.X, Y, 0.2, prec)
+    g = run(ctx, wl.X, Y, 0.2, prec, tiles=tiles)
     o = certificate(wl.X, Y, 0.2)
     assert_cert_parity(g, o, wl.X, Y)
 
 
-@pytest.mark.parametrize("prec", PRECISIONS)
-def test_mnist_shaped_ragged(ctx, prec):
+@pytest.mark.parametrize("prec,tiles", CERT_MODES)
+def test_mnist_shaped_ragged(ctx, prec, tiles):
     wl = synth.mnist_like(seed=1, n=3000)        # 23 full tiles + a ragged one
     Y = oracle_embedding(wl.X, 150)
-    g = run(ctx, wl.X, Y, 0.1, prec)
+    g = run(ctx, wl.X, Y, 0.1, prec, tiles=tiles)
     o = certificate(wl.X, Y, 0.1)
     assert_cert_parity(g, o, wl.X, Y)
 
 
-@pytest.mark.parametrize("prec", PRECISIONS)
+@pytest.mark.parametrize("prec,tiles", CERT_MODES)
 @pytest.mark.parametrize("n", [2, 3, 127, 128, 129, 300])
-def test_tiny_and_tile_edges(ctx, prec, n):
+def test_tiny_and_tile_edges(ctx, prec, tiles, n):
     rng = np.random.default_rng(n)
     X = rng.standard_normal((n, 37)).astype(np.float32)
     Y = (X @ rng.standard_normal((37, 11)) / np.sqrt(11)).astype(np.float32)
-    g = run(ctx, X, Y, 0.3, prec, 0.0, 2.0)
+    g = run(ctx, X, Y, 0.3, prec, 0.0, 2.0, tiles=tiles)
     o = certificate(X, Y, 0.3, 0.0, 2.0)
     assert_cert_parity(g, o, X, Y)
 
 
-@pytest.mark.parametrize("prec", PRECISIONS)
-def test_host_and_device_pointers_agree(ctx, prec):
+@pytest.mark.parametrize("prec,tiles", CERT_MODES)
+def test_host_and_device_pointers_agree(ctx, prec, tiles):
     wl = synth.small(seed=0, n=900)
     Y = oracle_embedding(wl.X, 12)
-    a = run(ctx, wl.X, Y, 0.2, prec, device=True)
-    b = run(ctx, wl.X, Y, 0.2, prec, device=False)
+    a = run(ctx, wl.X, Y, 0.2, prec, device=True, tiles=tiles)
+    b = run(ctx, wl.X, Y, 0.2, prec, device=False, tiles=tiles)
     assert a.max == b.max and np.array_equal(a.hist, b.hist) and a.violations == b.violations
 
 
-@pytest.mark.parametrize("prec", PRECISIONS)
-def test_duplicates_are_degenerate(ctx, prec):
+@pytest.mark.parametrize("prec,tiles", CERT_MODES)
+def test_duplicates_are_degenerate(ctx, prec, tiles):
     rng = np.random.default_rng(5)
     X = rng.standard_normal((400, 16)).astype(np.float32)
     X[10] = X[3]
     X[200] = X[3]
     X[399] = X[0]
     Y = (X @ rng.standard_normal((16, 8)) / np.sqrt(8)).astype(np.float32)
-    g = run(ctx, X, Y, 0.5, prec, 0.0, 4.0)
+    g = run(ctx, X, Y, 0.5, prec, 0.0, 4.0, tiles=tiles)
     o = certificate(X, Y, 0.5, 0.0, 4.0)
     assert o.degenerate == 4
     assert_cert_parity(g, o, X, Y)
 
 
-@pytest.mark.parametrize("prec", PRECISIONS)
-def test_all_points_identical(ctx, prec):
+@pytest.mark.parametrize("prec,tiles", CERT_MODES)
+def test_all_points_identical(ctx, prec, tiles):
     X = np.full((50, 5), 0.25, dtype=np.float32)
     Y = np.zeros((50, 2), dtype=np.float32)
-    g = run(ctx, X, Y, 0.1, prec)
+    g = run(ctx, X, Y, 0.1, prec, tiles=tiles)
     assert g.degenerate == g.pairs == 50 * 49 // 2
     assert g.max == 0.0 and int(g.hist.sum()) == 0
 
 
-@pytest.mark.parametrize("prec", PRECISIONS)
-def test_one_dimensional(ctx, prec):
+@pytest.mark.parametrize("prec,tiles", CERT_MODES)
+def test_one_dimensional(ctx, prec, tiles):
     rng = np.random.default_rng(6)
     X = rng.standard_normal((257, 1)).astype(np.float32)
     Y = (1.5 * X).astype(np.float32)
-    g = run(ctx, X, Y, 0.6, prec, 0.0, 1.0)
+    g = run(ctx, X, Y, 0.6, prec, 0.0, 1.0, tiles=tiles)
     o = certificate(X, Y, 0.6, 0.0, 1.0)
     assert_cert_parity(g, o, X, Y)
 
 
-@pytest.mark.parametrize("prec", PRECISIONS)
-def test_pairs_exactly_on_an_edge(ctx, prec):
+@pytest.mark.parametrize("prec,tiles", CERT_MODES)
+def test_pairs_exactly_on_an_edge(ctx, prec, tiles):
     # Y = 1.25 X: every pair has distortion exactly 0.25 = eps = edge of bin 32
     rng = np.random.default_rng(7)
     X = rng.integers(-50, 50, size=(300, 6)).astype(np.float32)
     X = np.unique(X, axis=0)
     Y = (1.25 * X).astype(np.float32)
-    g = run(ctx, X, Y, 0.25, prec)
+    g = run(ctx, X, Y, 0.25, prec, tiles=tiles)
     o = certificate(X, Y, 0.25)
     assert o.near_edge == o.pairs
     assert_cert_parity(g, o, X, Y)
 
 
-@pytest.mark.parametrize("prec", PRECISIONS)
-def test_nonfinite_input_rejected(ctx, prec):
+@pytest.mark.parametrize("prec,tiles", CERT_MODES)
+def test_nonfinite_input_rejected(ctx, prec, tiles):
     from paper_1609_05388_gb300 import adagio as lib
     X = np.ones((10, 3), dtype=np.float32)
     X[4, 1] = np.nan
     Y = np.ones((10, 2), dtype=np.float32)
     with pytest.raises(lib.AdagioError) as ei:
-        run(ctx, X, Y, 0.1, prec)
+        run(ctx, X, Y, 0.1, prec, tiles=tiles)
     assert ei.value.code == lib.E_NONFINITE
 
 
@@ -139,8 +140,8 @@ def test_bad_arguments_rejected(ctx):
         ctx.distortion(X, X, 0.1, precision=7)
 
 
-@pytest.mark.parametrize("prec", PRECISIONS)
-def test_full_size_mnist_shaped_sampled(ctx, prec):
+@pytest.mark.parametrize("prec,tiles", CERT_MODES)
+def test_full_size_mnist_shaped_sampled(ctx, prec, tiles):
     """60 000 x 784 (1.8e9 pairs): properties at full size, sampled pairs by the oracle."""
     wl = synth.mnist_like(seed=1)
     m = 200
@@ -148,7 +149,7 @@ def test_full_size_mnist_shaped_sampled(ctx, prec):
     # the embedding comes from the oracle's map of a 4000-point sample
     f = O.fit(wl.X[:4000].astype(np.float64), m, 3)
     Y = (wl.X.astype(np.float64) @ f.A.T).astype(np.float32)
-    g = run(ctx, wl.X, Y, 0.1, prec)
+    g = run(ctx, wl.X, Y, 0.1, prec, tiles=tiles)
     assert g.pairs == 60000 * 59999 // 2
     assert int(g.hist.sum()) + g.overflow + g.degenerate == g.pairs
     d_arg = pair_distortion(wl.X, Y, [g.argmax_i], [g.argmax_j])[0]
@@ -165,3 +166,22 @@ def test_full_size_mnist_shaped_sampled(ctx, prec):
     p = g.violations / good
     assert abs(p - p_hat) <= 6 * np.sqrt(max(p * (1 - p), 1e-12) / dl.size) + 1e-6
     assert abs(g.mean - dl.mean()) <= 6 * dl.std() / np.sqrt(dl.size)
+
+
+def test_tile_kernels_agree(ctx):
+    """Single-CTA and CTA-pair tiles classify every pair the same way."""
+    from paper_1609_05388_gb300 import adagio as lib
+    wl = synth.mnist_like(seed=1, n=5000)
+    Y = oracle_embedding(wl.X, 150)
+    o = certificate(wl.X, Y, 0.1)
+    res = {}
+    for tiles in (lib.TILES_SINGLE, lib.TILES_PAIR):
+        res[tiles] = run(ctx, wl.X, Y, 0.1, lib.PREC_FP16X3, tiles=tiles)
+        assert_cert_parity(res[tiles], o, wl.X, Y)
+    a, b = res[lib.TILES_SINGLE], res[lib.TILES_PAIR]
+    assert a.max == b.max and (a.argmax_i, a.argmax_j) == (b.argmax_i, b.argmax_j)
+    assert int(np.abs(a.hist - b.hist).sum()) <= 2 * o.near_edge
+    assert abs(a.mean - b.mean) <= 1e-9
+    ctx.set_tile_kernel(lib.TILES_AUTO)
+    assert ctx.tile_kernel_for(60000) in (lib.TILES_SINGLE, lib.TILES_PAIR)
+    assert ctx.tile_kernel_for(1000) == lib.TILES_SINGLE
