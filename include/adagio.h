@@ -396,21 +396,16 @@ int adagio_last_cert_stats(const adagio_ctx *ctx, adagio_cert_stats *out);
 /*
  * Tile kernel of the split-precision certificates (the all-pairs step of
  * Eq. 2 and Eq. 3; the classification of every pair does not depend on it):
- *   variant ADAGIO_TILES_AUTO    default: one CTA per tile
- *           ADAGIO_TILES_SINGLE  one CTA per 128 x 128 tile
- *           ADAGIO_TILES_PAIR    a cluster of two CTAs per 256 x 128 tile
- *                                (SINGLE where such clusters cannot be
- *                                resident on the device)
- *   chunk_steps  64-wide K steps summed in one tensor-core accumulator before
- *                the FP32 register sum: 0 (default) or 1, or 2 (half the
- *                accumulator drains, a wider error bound and so more pairs
- *                for the exact recompute)
+ *   ADAGIO_TILES_AUTO    default: one CTA per tile
+ *   ADAGIO_TILES_SINGLE  one CTA per 128 x 128 tile
+ *   ADAGIO_TILES_PAIR    a cluster of two CTAs per 256 x 128 tile (SINGLE
+ *                        where such clusters cannot be resident on the device)
  * Returns ADAGIO_E_INVALID_ARG for any other value.  Adopted by the next call.
  */
 #define ADAGIO_TILES_AUTO 0
 #define ADAGIO_TILES_SINGLE 1
 #define ADAGIO_TILES_PAIR 2
-int adagio_set_tile_kernel(adagio_ctx *ctx, int variant, int chunk_steps);
+int adagio_set_tile_kernel(adagio_ctx *ctx, int variant);
 /* The tile kernel that certifies n points on ctx (1 = single, 2 = pair);
  * queries the device on first use.  Negative on error. */
 int adagio_tile_kernel_for(adagio_ctx *ctx, int64_t n);

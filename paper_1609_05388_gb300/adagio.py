@@ -150,7 +150,7 @@ def _load() -> ctypes.CDLL:
                                      ctypes.POINTER(FitOptsStruct), i32, vp]),
         "adagio_last_batch_stats": (i32, [vp, ctypes.POINTER(BatchStatsStruct)]),
         "adagio_set_timing": (i32, [vp, i32]),
-        "adagio_set_tile_kernel": (i32, [vp, i32, i32]),
+        "adagio_set_tile_kernel": (i32, [vp, i32]),
         "adagio_tile_kernel_for": (i32, [vp, i64]),
         "adagio_last_cert_stats": (i32, [vp, ctypes.POINTER(CertStatsStruct)]),
         "adagio_launch_count": (ctypes.c_uint64, []),
@@ -292,10 +292,9 @@ class Context:
     def set_timing(self, enable: bool = True):
         self._check(LIB.adagio_set_timing(self.h, 1 if enable else 0))
 
-    def set_tile_kernel(self, variant: int, chunk_steps: int = 0):
-        """Tile kernel of split-precision certificates (TILES_AUTO, TILES_SINGLE or TILES_PAIR)
-        and the 64-wide K steps per tensor-core accumulator chunk (0 = default)."""
-        self._check(LIB.adagio_set_tile_kernel(self.h, int(variant), int(chunk_steps)))
+    def set_tile_kernel(self, variant: int):
+        """Tile kernel of split-precision certificates: TILES_AUTO, TILES_SINGLE or TILES_PAIR."""
+        self._check(LIB.adagio_set_tile_kernel(self.h, int(variant)))
 
     def tile_kernel_for(self, n: int) -> int:
         """The tile kernel (TILES_SINGLE or TILES_PAIR) that certifies n points."""

@@ -51,8 +51,6 @@ void cert_init();
 void tc_tile_coords(adagio_ctx *ctx, int64_t n, long long u, int *I, int *J);
 // tensor-core tile kernel for n points: 1 = one CTA per tile, 2 = CTA pairs
 int tc_variant(adagio_ctx *ctx, int64_t n);
-// K steps per TMEM accumulator chunk of the tensor-core kernel (1 or 2)
-int tc_chunk_steps(adagio_ctx *ctx);
 
 // Exact recompute of the queued pairs from the original (uncentred) inputs.
 void launch_recompute(const float *X, int64_t ldx, int d, const float *Y, int64_t ldy, int m,

@@ -25,12 +25,12 @@
 //               stage, 128-byte swizzle
 //   warp 1      TMEM owner (512 columns = 2 chunk slots of 128 + 256 staging
 //               columns) and, in the single CTA or the pair's leader, MMA
-//               issuer: tcgen05.mma kind::f16, K = 16.  Every chunk of one
-//               (default) or two 64-element K steps goes to a fresh slot, the
-//               cross products (hi.lo, lo.hi) of its steps first and the hi.hi
-//               products last: the FP32 accumulator loses up to one unit in
-//               the last place per MMA (it truncates), so this bounds the
-//               full-size roundings to 4 per K step of the chunk
+//               issuer: tcgen05.mma kind::f16, K = 16.  Every 64-element K
+//               step goes to a fresh slot, cross products (hi.lo, lo.hi)
+//               first and the 4 hi.hi products last: the FP32 accumulator
+//               loses up to one unit in the last place per MMA (it
+//               truncates), so this bounds the full-size roundings to 4 per
+//               chunk
 //   warps 2..9  epilogue: two warps per TMEM lane quarter, 64 columns each;
 //               they drain every slot into register running sums (round to
 //               nearest) and classify their 64 pairs at the end of a tile,
@@ -62,7 +62,6 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;               // producer, MMA, ep
 constexpr int kSlots = 2;                                   // TMEM chunk accumulators
 constexpr int kTile = 128;
 constexpr int kKStep = 64;                                  // fp16 elements per stage row
-constexpr int kMaxChunkSteps = 2;                           // K steps per TMEM chunk slot (at most)
 constexpr int kEpiCols = 64;                                // columns per epilogue warp
 constexpr uint32_t kAPlane = kTile * kKStep * 2;            // 16 KB: 128 rows of one plane
 constexpr uint32_t kStageCol = kSlots * kTile;              // finished Gram sums (gx | gy)
@@ -81,7 +80,6 @@ struct TcArgs {
     const uint32_t *sched;     // (I << 16) | J per tile (pair variant: I counts 256-row blocks)
     long long ntp;
     int n, kx_steps, ky_steps;
-    int csteps;                // K steps per chunk slot (1 or 2)
     uint32_t idesc;
     CertConst cc;
     CertPartial *partials;     // [gridDim.x * kEpiWarps], one slot per epilogue warp
@@ -115,7 +113,6 @@ struct Layout {
     static_assert(totals % 8 == 0, "per-warp totals need 8-byte alignment");
     static_assert(kStageBytes % 1024 == 0 && kBPlane % 1024 == 0, "stage buffers need 1 KB alignment");
     static_assert((2 * kStages + 2 * kSlots + 5) * 8 <= 256, "barriers exceed their area");
-    static_assert(kStages >= kMaxChunkSteps + 1, "a chunk's stages and one more must fit");
 };
 
 // Folds this warp's 32 per-thread counters of every bin into its partial
@@ -247,8 +244,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     // identity: the pair's two CTAs share a tile sequence; rank 0 leads
     const uint32_t rank = PAIR ? cluster_ctarank() : 0u;
     const bool leader = rank == 0;
-    const long long unit0 = PAIR ? (long long)cluster_id_x() : (long long)blockIdx.x;
-    const long long ustride = PAIR ? (long long)ncluster_x() : (long long)gridDim.x;
 
     uint32_t *s_hist = reinterpret_cast<uint32_t *>(smem + L::hist);
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem + L::bars);
@@ -271,7 +266,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int s = 0; s < kSlots; ++s) {
             mbar_init(bar_sfull + 8 * s, 1);
             // one arrival per epilogue warp (of both CTAs of a pair)
-            mbar_init(bar_sempty + 8 * s, kEpiWarps * (PAIR ? 2 : 1));
+            // every epilogue thread arrives (a pair: one arrival per warp of both CTAs)
+            mbar_init(bar_sempty + 8 * s, PAIR ? 2 * kEpiWarps : 32 * kEpiWarps);
         }
         mbar_init(bar_done, 1);
         for (int q = 0; q < 2; ++q) {
@@ -309,13 +305,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_fence_after();
     const uint32_t tmem_base = *s_tmem;
     const int ksteps = p.ky_steps + p.kx_steps;
-    // chunks of up to p.csteps K steps: X chunks first, then Y chunks
-    const int cs = p.csteps;
-    const int xchunks = (p.kx_steps + cs - 1) / cs;
-    const int nchunks = xchunks + (p.ky_steps + cs - 1) / cs;
-    auto chunk_steps = [&](int c) {
-        return c < xchunks ? min(cs, p.kx_steps - c * cs) : min(cs, p.ky_steps - (c - xchunks) * cs);
-    };
 
     if (warp == 0) {
         // ------------------------------------------------------ TMA producer
@@ -329,8 +318,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool issued[kStages];
         for (int s = 0; s < kStages; ++s) issued[s] = false, issued_parity[s] = 0;
         const uint32_t full_tgt = PAIR ? mapa(bar_full, 0) : bar_full;
-        long long t = unit0;
-        for (long long k = 0; ok; ++k, t += ustride) {
+        long long t = PAIR ? (long long)cluster_id_x() : (long long)blockIdx.x;
+        for (long long k = 0; ok; ++k, t += PAIR ? (long long)ncluster_x() : (long long)gridDim.x) {
             bool stop;
             const int q = (int)(k & 1);
             const uint32_t use = (uint32_t)(k >> 1) & 1u;
@@ -425,38 +414,16 @@ __global__ void __launch_bounds__(kThreads, 1)
         __syncwarp();
     } else if (warp == 1) {
         // ------------------------------------------------------- MMA issuer
-        // Every chunk of p.csteps K steps accumulates into a fresh TMEM slot
-        // (128 columns): first the small cross-term products (hi.lo, lo.hi) of
-        // its steps, then the large hi.hi products, so only 4 FP32
-        // accumulator roundings per K step act on full-size partial sums.  The
-        // epilogue drains the slot.  A chunk never mixes X and Y steps.  In a
-        // pair only the leader issues; the peer's warp 1 only holds TMEM.
+        // Every K step accumulates into a fresh TMEM slot (128 columns): first
+        // the 8 small cross-term products (hi.lo, lo.hi), then the 4 large
+        // hi.hi products, so only 4 FP32 accumulator roundings per chunk act
+        // on full-size partial sums.  The epilogue drains the slot.  In a pair
+        // only the leader issues; the peer's warp 1 only holds TMEM.
         if (leader) {
             int stage = 0, slot = 0;
             uint32_t phase = 0, sphase = 0;
             bool any = false;
             bool ok = true;
-            auto cross = [&](int st, uint32_t d, uint32_t accumulate_first) {
-                const uint32_t a0 = sbase + L::stages + st * L::kStageBytes;
-                const uint64_t ah = sw128_desc(a0), al = sw128_desc(a0 + kAPlane);
-                const uint64_t bh = sw128_desc(a0 + 2 * kAPlane);
-                const uint64_t bl = sw128_desc(a0 + 2 * kAPlane + L::kBPlane);
-#pragma unroll
-                for (int kk = 0; kk < kKStep / 16; ++kk) {
-                    const uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 elements = 32 bytes
-                    tc_mma<PAIR>(d, ah + off, bl + off, p.idesc, (kk == 0) ? accumulate_first : 1u);
-                    tc_mma<PAIR>(d, al + off, bh + off, p.idesc, 1u);
-                }
-            };
-            auto full_size = [&](int st, uint32_t d) {
-                const uint32_t a0 = sbase + L::stages + st * L::kStageBytes;
-                const uint64_t ah = sw128_desc(a0), bh = sw128_desc(a0 + 2 * kAPlane);
-#pragma unroll
-                for (int kk = 0; kk < kKStep / 16; ++kk) {
-                    const uint64_t off = (uint64_t)(kk * 32) >> 4;
-                    tc_mma<PAIR>(d, ah + off, bh + off, p.idesc, 1u);
-                }
-            };
             while (ok) {
                 int t = -1;
                 ok = warp_wait<PAIR>(bar_full + 8 * stage, phase, p.status, 2);
@@ -475,51 +442,40 @@ __global__ void __launch_bounds__(kThreads, 1)
                     __syncwarp();
                     break;
                 }
-                for (int c = 0; c < nchunks; ++c) {
-                    const int nst = chunk_steps(c);
-                    if (c > 0) {
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    if (ks > 0) {
                         ok = warp_wait<PAIR>(bar_full + 8 * stage, phase, p.status, 2);
                         if (!ok) break;
                     }
                     ok = warp_wait<PAIR>(bar_sempty + 8 * slot, sphase ^ 1, p.status, 2);
                     if (!ok) break;
                     tc_fence_after();
-                    const uint32_t d = tmem_base + (uint32_t)(slot * kTile);
-                    const int st0 = stage;
-                    int st1 = stage + 1;
-                    uint32_t ph1 = phase;
-                    if (st1 == kStages) {
-                        st1 = 0;
-                        ph1 ^= 1;
-                    }
                     if (lane == 0) {
-                        cross(st0, d, 0u);
-                        any = true;
-                    }
-                    __syncwarp();
-                    if (nst == 2) {
-                        ok = warp_wait<PAIR>(bar_full + 8 * st1, ph1, p.status, 2);
-                        if (!ok) break;
-                        tc_fence_after();
-                        if (lane == 0) cross(st1, d, 1u);
-                        __syncwarp();
-                    }
-                    if (lane == 0) {
-                        full_size(st0, d);
-                        tc_commit<PAIR>(bar_empty + 8 * st0);
-                        if (nst == 2) {
-                            full_size(st1, d);
-                            tc_commit<PAIR>(bar_empty + 8 * st1);
+                        const uint32_t d = tmem_base + (uint32_t)(slot * kTile);
+                        const uint32_t a0 = sbase + L::stages + stage * L::kStageBytes;
+                        const uint64_t ah = sw128_desc(a0), al = sw128_desc(a0 + kAPlane);
+                        const uint64_t bh = sw128_desc(a0 + 2 * kAPlane);
+                        const uint64_t bl = sw128_desc(a0 + 2 * kAPlane + L::kBPlane);
+#pragma unroll
+                        for (int kk = 0; kk < kKStep / 16; ++kk) {
+                            const uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 elements = 32 bytes
+                            tc_mma<PAIR>(d, ah + off, bl + off, p.idesc, kk == 0 ? 0u : 1u);
+                            tc_mma<PAIR>(d, al + off, bh + off, p.idesc, 1u);
                         }
+#pragma unroll
+                        for (int kk = 0; kk < kKStep / 16; ++kk) {
+                            const uint64_t off = (uint64_t)(kk * 32) >> 4;
+                            tc_mma<PAIR>(d, ah + off, bh + off, p.idesc, 1u);
+                        }
+                        tc_commit<PAIR>(bar_empty + 8 * stage);
                         tc_commit<PAIR>(bar_sfull + 8 * slot);
                         any = true;
                     }
                     __syncwarp();
-                    for (int q = 0; q < nst; ++q)
-                        if (++stage == kStages) {
-                            stage = 0;
-                            phase ^= 1;
-                        }
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
                     if (++slot == kSlots) {
                         slot = 0;
                         sphase ^= 1;
@@ -656,27 +612,28 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         };
 
-        long long t = unit0;                    // the producer's static tile sequence
+        // the producer's static tile sequence
+        long long t = PAIR ? (long long)cluster_id_x() : (long long)blockIdx.x;
         bool ok = true;
         while (ok) {
             float gx[kEpiCols];
 #pragma unroll
             for (int c = 0; c < kEpiCols; ++c) gx[c] = 0.0f;
             bool stop = false;
-            for (int c = 0; c < nchunks; ++c) {
+            for (int ks = 0; ks < ksteps; ++ks) {
                 ok = warp_wait<PAIR>(bar_sfull + 8 * slot, sphase, p.status, 3);
                 if (!ok) break;
                 tc_fence_after();
-                if (c == 0) {
+                if (ks == 0) {
                     int cmdv = 0;
-                    if (lane == 0) cmdv = ((volatile int *)s_cmd)[kStages + slot];
+                    if (lane == 0) cmdv = s_cmd[kStages + slot];
                     if (__shfl_sync(0xffffffffu, cmdv, 0) < 0) {
                         stop = true;
                         break;
                     }
                 }
                 const uint32_t ta = tmem_base + lane_addr + (uint32_t)(slot * kTile + h * kEpiCols);
-                if (c < xchunks) {
+                if (ks < p.kx_steps) {
                     // X chunk: registers, all 64 columns behind one wait
                     uint32_t v[64];
                     tmem_ld64_wait(ta, v);
@@ -684,8 +641,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int c = 0; c < kEpiCols; ++c) gx[c] += __uint_as_float(v[c]);
                 } else {
                     // Y chunk: the running columns (the first Y chunk starts them)
-                    if (c == xchunks && pend) finish_pending();
-                    const bool first = c == xchunks;
+                    if (ks == p.kx_steps && pend) finish_pending();
+                    const bool first = ks == p.kx_steps;
 #pragma unroll
                     for (int hh = 0; hh < kEpiCols / 32; ++hh) {
                         uint32_t v[32], w[32];
@@ -704,25 +661,21 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                     tmem_wait_st();
                 }
-                // the slot is drained: one arrival per warp on the (leader's) barrier
+                // the slot is drained: every thread arrives (a pair: one
+                // arrival per warp on the leader's barrier)
                 tc_fence_before();
-                __syncwarp();
-                if (lane == 0) {
-                    if (PAIR)
-                        mbar_arrive_cluster(sempty_tgt + 8 * slot);
-                    else
-                        mbar_arrive(sempty_tgt + 8 * slot);
+                if (PAIR) {
+                    __syncwarp();
+                    if (lane == 0) mbar_arrive_cluster(sempty_tgt + 8 * slot);
+                } else {
+                    mbar_arrive(bar_sempty + 8 * slot);
                 }
                 if (++slot == kSlots) {
                     slot = 0;
                     sphase ^= 1;
                 }
-                // pieces of the previous tile between X-chunk drains, spread so
-                // that all of them are done by the last X chunk
-                if (c < xchunks && pend) {
-                    const int target = ((c + 1) * kPieces + xchunks - 1) / xchunks;
-                    while (pend_pieces < target) classify_next();
-                }
+                // one piece of the previous tile between X-chunk drains
+                if (ks < p.kx_steps && pend && pend_pieces < kPieces) classify_next();
             }
             if (!ok || stop) break;
             // this tile's Y chunks have started the running columns, so the
@@ -760,7 +713,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             qmask = 0ull;
             acc = RowAcc{0.0f, 0.0f, 0.0f, -1.0f, 0, 0, 0, 0};
-            t += ustride;
+            t += PAIR ? (long long)ncluster_x() : (long long)gridDim.x;
         }
         // the last tile (its sums are complete in TMEM)
         if (ok && pend) finish_pending();
@@ -839,10 +792,6 @@ std::vector<uint32_t> band_schedule_pair(int T) {
 }
 
 }  // namespace
-
-// K steps per TMEM chunk slot: one by default (a tighter error bound, and so
-// fewer pairs for the exact recompute), two when the context asks for it
-int tc_chunk_steps(adagio_ctx *ctx) { return ctx->tc_chunk == 2 ? 2 : 1; }
 
 // 128-row tile blocks of a prepared matrix of n rows
 static int tile_blocks(int64_t n) { return (int)(pad_rows(n) / kTile); }
@@ -981,10 +930,9 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
                                                                      (float4 *)L.rs_xy);
     ADAGIO_CHECK_LAUNCH();
     // ex = q4_i q4_j + (c_acc + c_r)(n2_i + n2_j) dominates the split model's
-    // q1 term, because 2 |a| |b| <= |a|^2 + |b|^2; c_acc for this chunking
-    a.csteps = tc_chunk_steps(L.ctx);
-    a.cx = bound_model(precision, x.Kp16, a.csteps).cacc + L.cc.c_r;
-    a.cy = bound_model(precision, y.Kp16, a.csteps).cacc + L.cc.c_r;
+    // q1 term, because 2 |a| |b| <= |a|^2 + |b|^2
+    a.cx = x.bm.cacc + L.cc.c_r;
+    a.cy = y.bm.cacc + L.cc.c_r;
     a.scale_x = x.scale;
     a.scale_y = y.scale;
     const int T = (int)(x.n_pad / kTile);

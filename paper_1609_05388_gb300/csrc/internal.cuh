@@ -87,7 +87,6 @@ struct adagio_ctx {
     // tile kernel of the tensor-core certificate: 0 automatic, 1 one CTA per
     // tile, 2 CTA pairs; and how many CTA pairs fit at once (-1: not queried)
     int tc_variant = 0;
-    int tc_chunk = 0;  // K steps per TMEM chunk slot: 0 automatic (1), 1 or 2
     int tc_pair_clusters = -1;
     // device status word of the tensor-core GEMMs (nonzero: a bounded wait
     // gave up); checked and cleared by the calls that synchronise
@@ -143,8 +142,7 @@ struct BoundModel {
     float c4;    // statistical product-error coefficient (times ||a||_4 ||b||_4)
     float cacc;  // accumulation coefficient (times ||a||_2 ||b||_2)
 };
-// chunk_steps: 64-wide K steps per tensor-core accumulator chunk (1 or 2)
-BoundModel bound_model(int precision, int K, int chunk_steps = 1);
+BoundModel bound_model(int precision, int K);
 
 // Synchronises st and fails with ADAGIO_E_TIMEOUT (clearing the word) when a
 // tensor-core GEMM enqueued on the context recorded a timeout.

@@ -142,7 +142,7 @@ __global__ void split_kernel(const float *__restrict__ X, int64_t n, int64_t n_p
 
 }  // namespace
 
-BoundModel bound_model(int precision, int K, int chunk_steps) {
+BoundModel bound_model(int precision, int K) {
     // Coefficients of the pair error bound (cert_common.cuh).
     //  * products (c4): the split arithmetic drops lo*lo and the residual
     //    beyond hi + lo; the relative error of one term has an RMS of 3.2e-6
@@ -152,12 +152,11 @@ BoundModel bound_model(int precision, int K, int chunk_steps) {
     //      FP32 SIMT: one FMA chain of K round-to-nearest steps, three RMS of
     //      its random-walk error;
     //      tensor cores: the FP32 accumulator truncates (up to one unit in the
-    //      last place per MMA, observed about half on average); each K chunk
-    //      of chunk_steps 64-wide steps (the cross products of all its steps
-    //      first) ends with 4 full-size MMAs per step (<= 4 chunk_steps 2^-23
-    //      of the chunk's absolute Gram, which sums to <= ||a|| ||b|| over the
-    //      chunks) and the chunks are added in FP32 with round to nearest
-    //      (<= 2^-24 of the running sum per chunk).
+    //      last place per MMA, observed about half on average); each 64-wide
+    //      K chunk ends with 4 full-size MMAs (<= 4 * 2^-23 of the chunk's
+    //      absolute Gram, which sums to <= ||a|| ||b|| over the chunks) and the
+    //      chunks are added in FP32 with round to nearest (<= 2^-24 of the
+    //      running sum per chunk).
     BoundModel bm;
     const float u = 5.9604645e-08f;  // 2^-24
     if (precision == ADAGIO_PREC_FP32) {
@@ -165,9 +164,8 @@ BoundModel bound_model(int precision, int K, int chunk_steps) {
         bm.cacc = 3.0f * u * sqrtf(fmaxf((float)K, 1.0f) / 3.0f);
     } else {
         bm.c4 = precision == ADAGIO_PREC_FP16X3 ? 9.0e-7f : 2.6e-5f;
-        const float width = 64.0f * (float)chunk_steps;
-        const float chunks = fmaxf(ceilf((float)K / width), 1.0f);
-        bm.cacc = 8.0f * (float)chunk_steps * u + chunks * u;
+        const float chunks = fmaxf((float)K / 64.0f, 1.0f);
+        bm.cacc = 8.0f * u + chunks * u;
     }
     return bm;
 }

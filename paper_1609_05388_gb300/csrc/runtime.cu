@@ -216,12 +216,9 @@ int adagio_set_timing(adagio_ctx *ctx, int enable) {
     return ADAGIO_OK;
 }
 
-int adagio_set_tile_kernel(adagio_ctx *ctx, int variant, int chunk_steps) {
-    if (!ctx || variant < ADAGIO_TILES_AUTO || variant > ADAGIO_TILES_PAIR || chunk_steps < 0 ||
-        chunk_steps > 2)
-        return ADAGIO_E_INVALID_ARG;
+int adagio_set_tile_kernel(adagio_ctx *ctx, int variant) {
+    if (!ctx || variant < ADAGIO_TILES_AUTO || variant > ADAGIO_TILES_PAIR) return ADAGIO_E_INVALID_ARG;
     ctx->tc_variant = variant;
-    ctx->tc_chunk = chunk_steps;
     return ADAGIO_OK;
 }
 
