@@ -35,19 +35,22 @@ EPS = 0.1
 # Residual tolerance of the randomized PCA (Sec. 4.5 uses randomized PCA as a
 # stand-in for exact PCA; every returned map is certified exhaustively, so the
 # tolerance only trades PCA time against how good the principal subspace is).
-PCA_TOL = 1e-4
+# At 1e-3 the block iteration stops after 7 iterations on this workload (the
+# 4 to 7 power iterations of the randomized PCA the paper uses, Sec. 4.1) and
+# the certified dimension stays within 1 % of the one at 1e-4 (24 iterations).
+PCA_TOL = 1e-3
 WORKLOAD = "mnist_like 60000x784 (10 clusters, rank-50, ~80% zeros, k/255), eps=0.1"
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one tile-kernel
 # launch on this workload from one ncu capture of the full launch
 # (profiles/cert_tc_mnist.md), or None once the kernel has changed since.
-TRAFFIC_BYTES = None
+TRAFFIC_BYTES = 8416345856 + 37529344
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=3)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="adagio", choices=["adagio", "reference"])
     p.add_argument("--precision", default="auto")
