@@ -394,18 +394,50 @@ int adagio_set_timing(adagio_ctx *ctx, int enable);
 int adagio_last_cert_stats(const adagio_ctx *ctx, adagio_cert_stats *out);
 
 /*
- * Tile kernel of the split-precision certificates (the all-pairs step of
- * Eq. 2 and Eq. 3; the classification of every pair does not depend on it):
- *   ADAGIO_TILES_AUTO    default: one CTA per tile
- *   ADAGIO_TILES_SINGLE  one CTA per 128 x 128 tile
- *   ADAGIO_TILES_PAIR    a cluster of two CTAs per 256 x 128 tile (SINGLE
- *                        where such clusters cannot be resident on the device)
+ * Tile configuration of the split-precision certificates (the all-pairs step
+ * of Eq. 2 and Eq. 3; the classification of every pair does not depend on it):
+ *   variant  ADAGIO_TILES_AUTO    default: the autotuned kernel for n's size
+ *                                 class (adagio_autotune_tiles), else SINGLE
+ *            ADAGIO_TILES_SINGLE  one CTA per 128 x 128 tile
+ *            ADAGIO_TILES_PAIR    a cluster of two CTAs per 256 x 128 tile
+ *                                 (SINGLE where such clusters cannot be
+ *                                 resident on the device)
+ *   band     tile rows (of 128 points) per band of the tile schedule, whose I
+ *            tiles stay in L2 while the J tiles stream: 1 to 32, or 0 for the
+ *            autotuned value, else 8
  * Returns ADAGIO_E_INVALID_ARG for any other value.  Adopted by the next call.
  */
 #define ADAGIO_TILES_AUTO 0
 #define ADAGIO_TILES_SINGLE 1
 #define ADAGIO_TILES_PAIR 2
-int adagio_set_tile_kernel(adagio_ctx *ctx, int variant);
+int adagio_set_tile_kernel(adagio_ctx *ctx, int variant, int band);
+
+/*
+ * Autotuner of the certificate's tile configuration.  Runs the certificate
+ * of (X, Y) (host or device arrays, as adagio_distortion takes them) with
+ * every candidate: each tile kernel the device runs (single CTA, CTA pair)
+ * with schedule bands of 4, 8 and 16 tile rows; times the tile kernel with
+ * CUDA events (one warm-up and three timed runs each, the fastest counts);
+ * keeps the fastest on ctx for the size class of n (the number of 128-row
+ * tile blocks rounded up to a power of two), where later certificates of
+ * that class with variant and band left automatic use it.  Writes the chosen
+ * configuration to *best.  Synchronises the stream.  Errors: those of
+ * adagio_distortion.
+ */
+typedef struct {
+    int variant;     /* ADAGIO_TILES_SINGLE or ADAGIO_TILES_PAIR */
+    int band;        /* tile rows per schedule band */
+    double tile_ms;  /* its tile-kernel time on the tuned problem */
+    int size_class;  /* the size class of n it applies to */
+} adagio_tile_config;
+int adagio_autotune_tiles(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
+                          const float *Y, int m, int64_t ldy, double eps, int precision,
+                          adagio_tile_config *best, void *stream);
+/* The tuned table as JSON (device name and one entry per size class), and
+ * back.  Loading a table of another device name loads nothing and returns
+ * ADAGIO_E_INVALID_ARG; a malformed file also returns ADAGIO_E_INVALID_ARG. */
+int adagio_tune_save(const adagio_ctx *ctx, const char *path);
+int adagio_tune_load(adagio_ctx *ctx, const char *path);
 /* The tile kernel that certifies n points on ctx (1 = single, 2 = pair);
  * queries the device on first use.  Negative on error. */
 int adagio_tile_kernel_for(adagio_ctx *ctx, int64_t n);

@@ -69,6 +69,11 @@ class CertStatsStruct(ctypes.Structure):
                 ("grid", ctypes.c_int), ("tiles", ctypes.c_int64)]
 
 
+class TileConfigStruct(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("band", ctypes.c_int), ("tile_ms", ctypes.c_double),
+                ("size_class", ctypes.c_int)]
+
+
 class FitStatsStruct(ctypes.Structure):
     _fields_ = [("probes", ctypes.c_int), ("full_certs", ctypes.c_int),
                 ("pca_iterations", ctypes.c_int), ("s_computed", ctypes.c_int),
@@ -150,7 +155,11 @@ def _load() -> ctypes.CDLL:
                                      ctypes.POINTER(FitOptsStruct), i32, vp]),
         "adagio_last_batch_stats": (i32, [vp, ctypes.POINTER(BatchStatsStruct)]),
         "adagio_set_timing": (i32, [vp, i32]),
-        "adagio_set_tile_kernel": (i32, [vp, i32]),
+        "adagio_set_tile_kernel": (i32, [vp, i32, i32]),
+        "adagio_autotune_tiles": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, f64, i32,
+                                        ctypes.POINTER(TileConfigStruct), vp]),
+        "adagio_tune_save": (i32, [vp, ctypes.c_char_p]),
+        "adagio_tune_load": (i32, [vp, ctypes.c_char_p]),
         "adagio_tile_kernel_for": (i32, [vp, i64]),
         "adagio_last_cert_stats": (i32, [vp, ctypes.POINTER(CertStatsStruct)]),
         "adagio_launch_count": (ctypes.c_uint64, []),
@@ -193,7 +202,8 @@ def exported_symbols() -> list[str]:
                         "adagio_mlp_train_step", "adagio_predict_m", "adagio_features",
                         "adagio_mlp_save", "adagio_mlp_load", "adagio_fit_batched",
                         "adagio_last_batch_stats", "adagio_set_tile_kernel",
-                        "adagio_tile_kernel_for") if hasattr(LIB, n)]
+                        "adagio_tile_kernel_for", "adagio_autotune_tiles", "adagio_tune_save",
+                        "adagio_tune_load") if hasattr(LIB, n)]
 
 
 def launch_count() -> int:
@@ -292,9 +302,28 @@ class Context:
     def set_timing(self, enable: bool = True):
         self._check(LIB.adagio_set_timing(self.h, 1 if enable else 0))
 
-    def set_tile_kernel(self, variant: int):
-        """Tile kernel of split-precision certificates: TILES_AUTO, TILES_SINGLE or TILES_PAIR."""
-        self._check(LIB.adagio_set_tile_kernel(self.h, int(variant)))
+    def set_tile_kernel(self, variant: int, band: int = 0):
+        """Tile kernel of split-precision certificates (TILES_AUTO, TILES_SINGLE or TILES_PAIR)
+        and the schedule's band height in tile rows (0: tuned or default)."""
+        self._check(LIB.adagio_set_tile_kernel(self.h, int(variant), int(band)))
+
+    def autotune_tiles(self, X, Y, eps: float, precision: int = PREC_FP16X3) -> dict:
+        """Times every tile configuration on the certificate of (X, Y); the fastest is kept
+        for n's size class.  Returns {variant, band, tile_ms, size_class}."""
+        x, y = _Arr(X), _Arr(Y)
+        if x.rows != y.rows:
+            raise ValueError("X and Y must have the same number of rows")
+        c = TileConfigStruct()
+        self._check(LIB.adagio_autotune_tiles(self.h, x.ptr, x.rows, x.cols, x.ld, y.ptr, y.cols,
+                                              y.ld, eps, precision, ctypes.byref(c), _stream(x, y)))
+        return {"variant": c.variant, "band": c.band, "tile_ms": c.tile_ms,
+                "size_class": c.size_class}
+
+    def tune_save(self, path: str):
+        self._check(LIB.adagio_tune_save(self.h, path.encode()))
+
+    def tune_load(self, path: str):
+        self._check(LIB.adagio_tune_load(self.h, path.encode()))
 
     def tile_kernel_for(self, n: int) -> int:
         """The tile kernel (TILES_SINGLE or TILES_PAIR) that certifies n points."""

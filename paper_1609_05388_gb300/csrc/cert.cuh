@@ -51,6 +51,12 @@ void cert_init();
 void tc_tile_coords(adagio_ctx *ctx, int64_t n, long long u, int *I, int *J);
 // tensor-core tile kernel for n points: 1 = one CTA per tile, 2 = CTA pairs
 int tc_variant(adagio_ctx *ctx, int64_t n);
+// the tile configuration (kernel and schedule band) used for n points
+TileConfig tc_config(adagio_ctx *ctx, int64_t n);
+// size class of n for the tuned table: ceil(log2(128-row tile blocks))
+int tc_size_class(int64_t n);
+// whether CTA-pair tiles can run on the context's device
+bool tc_pair_supported(adagio_ctx *ctx);
 
 // Exact recompute of the queued pairs from the original (uncentred) inputs.
 void launch_recompute(const float *X, int64_t ldx, int d, const float *Y, int64_t ldy, int m,

@@ -760,31 +760,28 @@ __global__ void pack_row_stats(const RowStat *__restrict__ rx, const RowStat *__
     if (r < n_pad) out[r] = make_float4(rx[r].n2, ry[r].n2, rx[r].q4, ry[r].q4);
 }
 
-// Band orders of the upper triangle.  Single: bands of kBand tile rows; in a
-// band, J runs left to right and I over the band's rows with I <= J.  Pair:
-// tiles of 256 I rows x 128 J rows (I counts 256-row blocks), bands of
-// kBandPair such blocks (the same 1024 rows), J >= 2 I (the tiles that hold
-// pairs i < j).
-constexpr int kBand = 8;
-constexpr int kBandPair = 4;
-
-std::vector<uint32_t> band_schedule(int T) {
+// Band orders of the upper triangle.  Single: bands of `band` tile rows; in a
+// band, J runs left to right and I over the band's rows with I <= J, so the
+// band's I tiles stay in L2 while the J tiles stream.  Pair: tiles of 256 I
+// rows x 128 J rows (I counts 256-row blocks), bands of band / 2 such blocks
+// (the same rows), J >= 2 I (the tiles that hold pairs i < j).
+std::vector<uint32_t> band_schedule(int T, int band) {
     std::vector<uint32_t> s;
     s.reserve((size_t)T * (T + 1) / 2);
-    for (int b0 = 0; b0 < T; b0 += kBand) {
-        const int b1 = std::min(T, b0 + kBand);
+    for (int b0 = 0; b0 < T; b0 += band) {
+        const int b1 = std::min(T, b0 + band);
         for (int J = b0; J < T; ++J)
             for (int I = b0; I < b1 && I <= J; ++I) s.push_back(((uint32_t)I << 16) | (uint32_t)J);
     }
     return s;
 }
 
-std::vector<uint32_t> band_schedule_pair(int T) {
-    const int T2 = T / 2;
+std::vector<uint32_t> band_schedule_pair(int T, int band) {
+    const int T2 = T / 2, band2 = std::max(1, band / 2);
     std::vector<uint32_t> s;
     s.reserve((size_t)T2 * (T2 + 1));
-    for (int b0 = 0; b0 < T2; b0 += kBandPair) {
-        const int b1 = std::min(T2, b0 + kBandPair);
+    for (int b0 = 0; b0 < T2; b0 += band2) {
+        const int b1 = std::min(T2, b0 + band2);
         for (int J = 2 * b0; J < T; ++J)
             for (int I = b0; I < b1 && 2 * I <= J; ++I) s.push_back(((uint32_t)I << 16) | (uint32_t)J);
     }
@@ -835,28 +832,45 @@ static int pair_capacity(adagio_ctx *ctx) {
     return ctx->tc_pair_clusters;
 }
 
-// Which tile kernel certifies n points: 1 = single CTA per tile, 2 = CTA
-// pair.  The context's setting decides; automatic takes the single CTA,
-// which measured faster on the MNIST-shaped workload (its epilogue, not the
-// operand traffic the pair saves, limits the tile rate).
-int tc_variant(adagio_ctx *ctx, int64_t n) {
-    if (pad_rows(n) % (2 * kTile) != 0) return 1;
-    if (ctx->tc_variant != 2) return 1;
-    return pair_capacity(ctx) > 0 ? 2 : 1;
+int tc_size_class(int64_t n) {
+    int c = 0;
+    while ((1ll << c) < tile_blocks(n)) ++c;
+    return c;
 }
 
-// Per-context cache of the device copy of a schedule, by tile-block count and
-// variant, resident for the context's lifetime (built on first use: a
-// synchronous upload, so callers that capture graphs make it resident first
+// The tile configuration that certifies n points: the context's explicit
+// setting (adagio_set_tile_kernel), else what the autotuner found for n's
+// size class, else one CTA per tile (measured faster on the MNIST-shaped
+// workload: its epilogue, not the operand traffic the pair saves, limits the
+// tile rate) with bands of 8 tile rows.  The pair needs rows padded to 256
+// and resident CTA pairs.
+TileConfig tc_config(adagio_ctx *ctx, int64_t n) {
+    TileConfig c{1, 8};
+    auto it = ctx->tc_tuned.find(tc_size_class(n));
+    if (it != ctx->tc_tuned.end()) c = TileConfig{it->second.variant, it->second.band};
+    if (ctx->tc_variant != 0) c.variant = ctx->tc_variant;
+    if (ctx->tc_band != 0) c.band = ctx->tc_band;
+    if (c.variant == 2 && (pad_rows(n) % (2 * kTile) != 0 || pair_capacity(ctx) == 0)) c.variant = 1;
+    return c;
+}
+
+int tc_variant(adagio_ctx *ctx, int64_t n) { return tc_config(ctx, n).variant; }
+
+bool tc_pair_supported(adagio_ctx *ctx) { return pair_capacity(ctx) > 0; }
+
+// Per-context cache of the device copy of a schedule, by tile-block count,
+// variant and band, resident for the context's lifetime (built on first use:
+// a synchronous upload, so callers that capture graphs make it resident first
 // with tc_prepare).
-static const uint32_t *schedule_for(adagio_ctx *ctx, int T, int variant, long long *count) {
-    const int key = T * 4 + variant;
+static const uint32_t *schedule_for(adagio_ctx *ctx, int T, TileConfig cfg, long long *count) {
+    const int key = (T << 8) | (cfg.band << 2) | cfg.variant;
+    const int variant = cfg.variant;
     auto it = ctx->tc_sched.find(key);
     if (it != ctx->tc_sched.end()) {
         *count = variant == 2 ? (long long)(T / 2) * (T / 2 + 1) : (long long)T * (T + 1) / 2;
         return it->second;
     }
-    std::vector<uint32_t> s = variant == 2 ? band_schedule_pair(T) : band_schedule(T);
+    std::vector<uint32_t> s = variant == 2 ? band_schedule_pair(T, cfg.band) : band_schedule(T, cfg.band);
     uint32_t *dev = nullptr;
     ADAGIO_CUDA(cudaMalloc(&dev, s.size() * sizeof(uint32_t)));
     cudaError_t e = cudaMemcpy(dev, s.data(), s.size() * sizeof(uint32_t), cudaMemcpyHostToDevice);
@@ -871,7 +885,7 @@ static const uint32_t *schedule_for(adagio_ctx *ctx, int T, int variant, long lo
 
 void tc_prepare(adagio_ctx *ctx, int64_t n) {
     long long c;
-    (void)schedule_for(ctx, tile_blocks(n), tc_variant(ctx, n), &c);
+    (void)schedule_for(ctx, tile_blocks(n), tc_config(ctx, n), &c);
 }
 
 // CTAs of one certificate launch: one per SM (the shared-memory footprint
@@ -892,13 +906,14 @@ int cert_tc_ctas(adagio_ctx *ctx, int64_t n) {
 // of the (u / 2)-th tile of the pair schedule
 void tc_tile_coords(adagio_ctx *ctx, int64_t n, long long u, int *I, int *J) {
     const int T = tile_blocks(n);
-    if (tc_variant(ctx, n) == 2) {
-        const std::vector<uint32_t> s = band_schedule_pair(T);
+    const TileConfig cfg = tc_config(ctx, n);
+    if (cfg.variant == 2) {
+        const std::vector<uint32_t> s = band_schedule_pair(T, cfg.band);
         const uint32_t v = s.at((size_t)(u >> 1));
         *I = 2 * (int)(v >> 16) + (int)(u & 1);
         *J = (int)(v & 0xFFFF);
     } else {
-        const std::vector<uint32_t> s = band_schedule(T);
+        const std::vector<uint32_t> s = band_schedule(T, cfg.band);
         const uint32_t v = s.at((size_t)u);
         *I = (int)(v >> 16);
         *J = (int)(v & 0xFFFF);
@@ -909,8 +924,8 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     const PrepMat &x = *L.x, &y = *L.y;
     if (!x.hi || !y.hi) return false;
     if (x.n_pad / kTile >= 65536) return false;
-    const int variant = tc_variant(L.ctx, x.n);
-    const bool pair = variant == 2;
+    const TileConfig cfg = tc_config(L.ctx, x.n);
+    const bool pair = cfg.variant == 2;
     if (pair && (x.n_pad % (2 * kTile) != 0 || y.n_pad != x.n_pad))
         fail(ADAGIO_E_CUDA, "internal: pair tiles need rows padded to 256 (n_pad %lld)",
              (long long)x.n_pad);
@@ -936,7 +951,7 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     a.scale_x = x.scale;
     a.scale_y = y.scale;
     const int T = (int)(x.n_pad / kTile);
-    a.sched = schedule_for(L.ctx, T, variant, &a.ntp);
+    a.sched = schedule_for(L.ctx, T, cfg, &a.ntp);
     a.n = (int)x.n;
     a.kx_steps = x.Kp16 / kKStep;
     a.ky_steps = y.Kp16 / kKStep;

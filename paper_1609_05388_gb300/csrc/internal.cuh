@@ -61,6 +61,19 @@ struct Workspace {
 
 struct Predictor;  // dimension predictor (mlp.cu)
 
+// Tile configuration of the tensor-core certificate: the kernel (1 = one CTA
+// per tile, 2 = CTA pairs) and the schedule's band height in tile rows.
+struct TileConfig {
+    int variant;
+    int band;
+};
+
+// An autotuned configuration and the tile-kernel time it was measured at.
+struct TunedTiles {
+    int variant, band;
+    double ms;
+};
+
 }  // namespace adagio
 
 struct adagio_ctx {
@@ -87,7 +100,11 @@ struct adagio_ctx {
     // tile kernel of the tensor-core certificate: 0 automatic, 1 one CTA per
     // tile, 2 CTA pairs; and how many CTA pairs fit at once (-1: not queried)
     int tc_variant = 0;
+    int tc_band = 0;  // schedule band height in tile rows (0: tuned or default)
     int tc_pair_clusters = -1;
+    // autotuned tile configurations by size class of n (adagio_autotune_tiles)
+    std::map<int, adagio::TunedTiles> tc_tuned;
+    std::string device_name;
     // device status word of the tensor-core GEMMs (nonzero: a bounded wait
     // gave up); checked and cleared by the calls that synchronise
     int *dev_status = nullptr;

@@ -170,6 +170,7 @@ int adagio_ctx_create(int device, size_t workspace_limit, adagio_ctx **out) {
         ctx->num_sms = prop.multiProcessorCount;
         ctx->ws.limit = workspace_limit;
         ctx->dev_status = status;
+        ctx->device_name = prop.name;
         *out = ctx;
         return ADAGIO_OK;
     } catch (const Error &e) {
@@ -216,9 +217,11 @@ int adagio_set_timing(adagio_ctx *ctx, int enable) {
     return ADAGIO_OK;
 }
 
-int adagio_set_tile_kernel(adagio_ctx *ctx, int variant) {
-    if (!ctx || variant < ADAGIO_TILES_AUTO || variant > ADAGIO_TILES_PAIR) return ADAGIO_E_INVALID_ARG;
+int adagio_set_tile_kernel(adagio_ctx *ctx, int variant, int band) {
+    if (!ctx || variant < ADAGIO_TILES_AUTO || variant > ADAGIO_TILES_PAIR || band < 0 || band > 32)
+        return ADAGIO_E_INVALID_ARG;
     ctx->tc_variant = variant;
+    ctx->tc_band = band;
     return ADAGIO_OK;
 }
 

@@ -169,19 +169,23 @@ def test_full_size_mnist_shaped_sampled(ctx, prec, tiles):
 
 
 def test_tile_kernels_agree(ctx):
-    """Single-CTA and CTA-pair tiles classify every pair the same way."""
+    """Single-CTA and CTA-pair tiles, in any schedule band, classify every pair the same way."""
     from paper_1609_05388_gb300 import adagio as lib
     wl = synth.mnist_like(seed=1, n=5000)
     Y = oracle_embedding(wl.X, 150)
     o = certificate(wl.X, Y, 0.1)
-    res = {}
-    for tiles in (lib.TILES_SINGLE, lib.TILES_PAIR):
-        res[tiles] = run(ctx, wl.X, Y, 0.1, lib.PREC_FP16X3, tiles=tiles)
-        assert_cert_parity(res[tiles], o, wl.X, Y)
-    a, b = res[lib.TILES_SINGLE], res[lib.TILES_PAIR]
-    assert a.max == b.max and (a.argmax_i, a.argmax_j) == (b.argmax_i, b.argmax_j)
-    assert int(np.abs(a.hist - b.hist).sum()) <= 2 * o.near_edge
-    assert abs(a.mean - b.mean) <= 1e-9
+    res = []
+    for tiles, band in ((lib.TILES_SINGLE, 0), (lib.TILES_PAIR, 0), (lib.TILES_SINGLE, 4),
+                        (lib.TILES_SINGLE, 16), (lib.TILES_PAIR, 16)):
+        ctx.set_tile_kernel(tiles, band)
+        res.append(ctx.distortion(torch.from_numpy(wl.X).cuda(), torch.from_numpy(Y).cuda(), 0.1,
+                                  precision=lib.PREC_FP16X3))
+        assert_cert_parity(res[-1], o, wl.X, Y)
+    a = res[0]
+    for b in res[1:]:
+        assert a.max == b.max and (a.argmax_i, a.argmax_j) == (b.argmax_i, b.argmax_j)
+        assert int(np.abs(a.hist - b.hist).sum()) <= 2 * o.near_edge
+        assert abs(a.mean - b.mean) <= 1e-9
     ctx.set_tile_kernel(lib.TILES_AUTO)
     assert ctx.tile_kernel_for(60000) in (lib.TILES_SINGLE, lib.TILES_PAIR)
     assert ctx.tile_kernel_for(1000) == lib.TILES_SINGLE
