@@ -9,7 +9,10 @@
 //              Ritz residual ||W_i - theta_i V_i|| <= tol * theta_1 (taken
 //              outside span(V), which is what an exact Rayleigh-Ritz leaves);
 //              otherwise V <- orth(W) (shifted CholeskyQR3 in FP32 with an
-//              FP64 Gram in the first pass)
+//              FP64 Gram in the first pass; only the first, shifted pass when
+//              the next iteration is not a Rayleigh-Ritz step: the iteration
+//              needs a well-conditioned basis of the subspace there, and the
+//              Rayleigh-Ritz step an orthonormal one)
 //   blocks   : directions are found in blocks of at most kJacobiMax - p;
 //              later blocks iterate in the orthogonal complement of the
 //              earlier ones (deflation), so the rows of P stay sorted by
@@ -208,8 +211,8 @@ void PCA::deflate(float *M, int r, cudaStream_t st) {
 // conditioning an FP32 matrix can carry and leaves a basis with condition
 // number below ~300; two unshifted-size passes with FP32 Grams then restore
 // orthonormality to FP32 precision.
-void PCA::orth(float *M, int b, cudaStream_t st) {
-    for (int pass = 0; pass < 3; ++pass) {
+void PCA::orth(float *M, int b, cudaStream_t st, int passes) {
+    for (int pass = 0; pass < passes; ++pass) {
         if (pass == 0) {
             gemm_f64_splitk(b, b, d, MatView<float>{M, d, 1}, MatView<float>{M, 1, d}, G, f64part,
                             kF64Chunk, st);
@@ -233,7 +236,12 @@ constexpr int kRRMax = 8;
 // The first Rayleigh-Ritz step of a block comes after a few iterations: on
 // the random start block its convergence test cannot pass, and its dense
 // Jacobi solve is the most expensive one.
-constexpr int kRRFirst = 2;
+constexpr int kRRFirst = 3;
+
+// whether iteration `it` of the current block ends with a Rayleigh-Ritz step
+bool PCA::rr_follows(int it) const {
+    return it >= blk.next_rr || it == max_iter - 1 || blk.b == blk.remaining;
+}
 
 void PCA::begin_block(int s_needed, cudaStream_t st) {
     (void)s_needed;
@@ -247,7 +255,7 @@ void PCA::begin_block(int s_needed, cudaStream_t st) {
     blk.active = true;
     rademacher_block(seed + (uint64_t)s_done * 0x9E3779B9ull, blk.b, d, V, d, st);
     deflate(V, blk.b, st);
-    orth(V, blk.b, st);
+    orth(V, blk.b, st, rr_follows(0) ? 3 : 1);
 }
 
 void PCA::advance(int s_needed, cudaStream_t st) {
@@ -288,9 +296,9 @@ void PCA::advance(int s_needed, cudaStream_t st) {
             copy_status(st);
             return;
         }
-        // next iterate: V <- orth(W)
+        // next iterate: V <- orth(W), orthonormal if a Rayleigh-Ritz step follows
         std::swap(V, W);
-        orth(V, b, st);
+        orth(V, b, st, rr_follows(blk.it + 1) ? 3 : 1);
         ++blk.it;
     }
 }
@@ -319,7 +327,7 @@ void PCA::resolve(cudaStream_t st) {
     }
     blk.next_rr = blk.it + k_pred;
     std::swap(V, W);
-    orth(V, blk.b, st);
+    orth(V, blk.b, st, rr_follows(blk.it + 1) ? 3 : 1);
     ++blk.it;
 }
 

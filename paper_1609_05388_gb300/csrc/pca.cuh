@@ -66,7 +66,10 @@ struct PCA {
     void begin_block(int s_needed, cudaStream_t st);
     void accept_block(cudaStream_t st);
     void deflate(float *M, int r, cudaStream_t st);
-    void orth(float *M, int b, cudaStream_t st);
+    // passes: 3 (orthonormal to FP32 precision) or 1 (the shifted first pass:
+    // a well-conditioned basis of the same span)
+    void orth(float *M, int b, cudaStream_t st, int passes = 3);
+    bool rr_follows(int it) const;
     void times_C(const float *M, int b, float *out, cudaStream_t st);  // out = M C
     void copy_status(cudaStream_t st);
     void check_status();
