@@ -139,7 +139,7 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
         ws_fixed += align_up((size_t)std::max(I.k_cap, 1) * d * sizeof(float), 256);
         ws_fixed += 2 * align_up((size_t)std::max(I.cap, 1) * d * sizeof(float), 256);
         ws_fixed += align_up((size_t)std::max(I.k_cap, 1) * std::max(I.s_cap, 1) * sizeof(float), 256);
-        ws_fixed += align_up((size_t)p.n * std::max(I.cap, 1) * sizeof(float), 256);
+        ws_fixed += align_up((size_t)p.n * emb_ld(I.cap) * sizeof(float), 256);
         ws_fixed += cert_prep_x_bytes(p.n, d, o.precision) + cert_job_bytes(ctx, p.n, I.cap, o.precision);
         ws_fixed += align_up(embed_planes_bytes(ctx, p.n, d, I.cap), 256);
         ws_fixed += 3 * 256 + align_up(68 * sizeof(float), 256);
@@ -265,7 +265,7 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
             I.A = ws_array<float>(ctx, (size_t)std::max(I.cap, 1) * p.d);
             I.Abest = ws_array<float>(ctx, (size_t)std::max(I.cap, 1) * p.d);
             I.T = ws_array<float>(ctx, (size_t)std::max(I.k_cap, 1) * std::max(I.s_cap, 1));
-            I.Y = ws_array<float>(ctx, (size_t)p.n * std::max(I.cap, 1));
+            I.Y = ws_array<float>(ctx, (size_t)p.n * emb_ld(I.cap));
             embed_planes_init(ctx, p.X, p.n, p.d, p.ldx, I.cap, I.ep, I.st);
             I.xflags = ws_array<unsigned>(ctx, 1);
             ADAGIO_CUDA(cudaMemsetAsync(I.xflags, 0, sizeof(unsigned), I.st));
@@ -306,9 +306,9 @@ int fit_batched(adagio_ctx *ctx, int count, adagio_instance *pub, const adagio_f
         const int s = I.split_s(r), k = r - s;
         if (k > 0) jl_matrix(o.seed, k, p.d, o.jl_dist, I.S, p.d, I.st);
         assemble(I.pca.P, s, p.d, I.S, k, p.d, p.d, I.A, p.d, I.T, I.st);
-        embed_planes_run(ctx, I.ep, I.A, r, p.d, I.Y, r, I.st);
+        embed_planes_run(ctx, I.ep, I.A, r, p.d, I.Y, emb_ld(r), I.st);
         I.job.Y = I.Y;
-        I.job.ldy = r;
+        I.job.ldy = emb_ld(r);
         I.job.m = r;
         I.job.opt = copt_for(I);
         I.job.opt.stop_early = I.search && !I.final_probe;

@@ -73,7 +73,7 @@ size_t fit_bytes(adagio_ctx *ctx, int64_t n, int d, int s_cap, int k_cap, int m_
     b += align_up((size_t)std::max(k_cap, 1) * d * sizeof(float), 256);          // S
     b += 2 * align_up((size_t)std::max(m_cap, 1) * d * sizeof(float), 256);      // A probe, A best
     b += align_up((size_t)std::max(k_cap, 1) * std::max(s_cap, 1) * sizeof(float), 256);  // T
-    b += align_up((size_t)n * std::max(m_cap, 1) * sizeof(float), 256);          // Y
+    b += align_up((size_t)n * emb_ld(m_cap) * sizeof(float), 256);               // Y
     b += certify_bytes(ctx, n, d, std::max(m_cap, 1), precision);
     b += embed_planes_bytes(ctx, n, d, m_cap);
     return b + 65536;
@@ -114,7 +114,7 @@ struct Prober {
         assemble(pca->P, s, d, S, k, d, d, A, d, T, st);
     }
 
-    void embed(int r, cudaStream_t st) { embed_planes_run(ctx, ep, A, r, d, Y, r, st); }
+    void embed(int r, cudaStream_t st) { embed_planes_run(ctx, ep, A, r, d, Y, emb_ld(r), st); }
 
     bool probe(int r, bool stop_early, cudaStream_t st) {
         build(r, st);
@@ -123,7 +123,7 @@ struct Prober {
         CertOptions co = copt;
         co.stop_early = stop_early;
         bool stopped = false;
-        certify(ctx, X, ldx, Y, r, n, d, r, co, &c, st, &stopped, px);
+        certify(ctx, X, ldx, Y, emb_ld(r), n, d, r, co, &c, st, &stopped, px);
         const bool ok = !stopped && c.max <= copt.eps;
         probes.push_back({r, ok, c.max});
         last_r = r;
@@ -183,7 +183,7 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
     pr.A = ws_array<float>(ctx, (size_t)std::max(cap, 1) * d);
     pr.Abest = ws_array<float>(ctx, (size_t)std::max(cap, 1) * d);
     pr.T = ws_array<float>(ctx, (size_t)std::max(k_cap, 1) * std::max(s_cap, 1));
-    pr.Y = ws_array<float>(ctx, (size_t)n * std::max(cap, 1));
+    pr.Y = ws_array<float>(ctx, (size_t)n * emb_ld(cap));
     embed_planes_init(ctx, X, n, d, ldx, cap, pr.ep, st);
     const double eps = search ? o->eps : 0.1;
     pr.copt.eps = eps;
@@ -210,7 +210,7 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
         pr.build(cap, st);
         if (cert) {
             pr.embed(cap, st);
-            certify(ctx, X, ldx, pr.Y, cap, n, d, cap, pr.copt, cert, st, nullptr, &px);
+            certify(ctx, X, ldx, pr.Y, emb_ld(cap), n, d, cap, pr.copt, cert, st, nullptr, &px);
         }
         ADAGIO_CUDA(cudaMemcpyAsync(A_out, pr.A, sizeof(float) * (size_t)cap * d,
                                     cudaMemcpyDeviceToDevice, st));
@@ -242,7 +242,7 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
             pr.build(cap, st);
             pr.embed(cap, st);
             adagio_cert c;
-            certify(ctx, X, ldx, pr.Y, cap, n, d, cap, pr.copt, &c, st, nullptr, &px);
+            certify(ctx, X, ldx, pr.Y, emb_ld(cap), n, d, cap, pr.copt, &c, st, nullptr, &px);
             if (cert) *cert = c;
             ADAGIO_CUDA(cudaMemcpyAsync(A_out, pr.A, sizeof(float) * (size_t)cap * d,
                                         cudaMemcpyDeviceToDevice, st));

@@ -107,23 +107,39 @@ __device__ __forceinline__ void add_vec(DF (&c)[4], float2 a, float2 b) {
 }
 __device__ __forceinline__ void add_vec(DF (&c)[4], float a, float b) { add_sq_diff(c[0], a, b); }
 
-// sum over this lane's elements k of (a_k - b_k)^2: V-wide loads (the rows
-// are V-aligned), two loads in flight per chain, a scalar tail
+template <int V>
+__device__ __forceinline__ typename VecT<V>::T vec_zero();
+template <>
+__device__ __forceinline__ float4 vec_zero<4>() { return make_float4(0.0f, 0.0f, 0.0f, 0.0f); }
+template <>
+__device__ __forceinline__ float2 vec_zero<2>() { return make_float2(0.0f, 0.0f); }
+template <>
+__device__ __forceinline__ float vec_zero<1>() { return 0.0f; }
+
+// sum over this lane's elements k of (a_k - b_k)^2.  The rows are V-aligned
+// and read with V-wide loads in chunks of U loads per row, all of a chunk's
+// 2U loads issued before the first is used (a pair is a few dependent L2
+// round trips, not one per element); missing entries of the last chunk read
+// as zero in both rows and add nothing.  A scalar tail follows.
 template <int V>
 __device__ __forceinline__ DF sq_dist_lanes(const float *__restrict__ a, const float *__restrict__ b,
                                             int n, int lane) {
     using T = typename VecT<V>::T;
+    constexpr int UU = V == 4 ? 4 : (V == 2 ? 8 : 16);  // 64 bytes of each row per lane and chunk
     DF c[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
     const T *av = reinterpret_cast<const T *>(a), *bv = reinterpret_cast<const T *>(b);
     const int nv = n / V;
-    int v = lane;
-    for (; v + 32 < nv; v += 64) {
-        const T a0 = __ldg(av + v), a1 = __ldg(av + v + 32);
-        const T b0 = __ldg(bv + v), b1 = __ldg(bv + v + 32);
-        add_vec(c, a0, b0);
-        add_vec(c, a1, b1);
+    for (int base = lane; base < nv; base += 32 * UU) {
+        T x[UU], y[UU];
+#pragma unroll
+        for (int u = 0; u < UU; ++u) {
+            const int v = base + 32 * u;
+            x[u] = v < nv ? __ldg(av + v) : vec_zero<V>();
+            y[u] = v < nv ? __ldg(bv + v) : vec_zero<V>();
+        }
+#pragma unroll
+        for (int u = 0; u < UU; ++u) add_vec(c, x[u], y[u]);
     }
-    for (; v < nv; v += 32) add_vec(c, __ldg(av + v), __ldg(bv + v));
     for (int k = nv * V + lane; k < n; k += 32) add_sq_diff(c[0], __ldg(a + k), __ldg(b + k));
     return df_add(df_add(c[0], c[1]), df_add(c[2], c[3]));
 }
