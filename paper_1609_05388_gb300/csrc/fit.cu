@@ -90,6 +90,7 @@ struct Prober {
     PCA *pca;
     float *S, *A, *Abest, *T, *Y;
     EmbedPlanes ep;            // X split once for every probe's embedding
+    cudaEvent_t prep_ready = nullptr;  // ep and px are ready (side stream)
     CertOptions copt;
     const PrepMat *px = nullptr;  // X prepared once for every probe's certificate
     int fixed_s;  // >= 0: every probe uses this many principal rows
@@ -114,7 +115,13 @@ struct Prober {
         assemble(pca->P, s, d, S, k, d, d, A, d, T, st);
     }
 
-    void embed(int r, cudaStream_t st) { embed_planes_run(ctx, ep, A, r, d, Y, emb_ld(r), st); }
+    void embed(int r, cudaStream_t st) {
+        if (prep_ready) {
+            ADAGIO_CUDA(cudaStreamWaitEvent(st, prep_ready, 0));
+            prep_ready = nullptr;
+        }
+        embed_planes_run(ctx, ep, A, r, d, Y, emb_ld(r), st);
+    }
 
     bool probe(int r, bool stop_early, cudaStream_t st) {
         build(r, st);
@@ -184,7 +191,6 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
     pr.Abest = ws_array<float>(ctx, (size_t)std::max(cap, 1) * d);
     pr.T = ws_array<float>(ctx, (size_t)std::max(k_cap, 1) * std::max(s_cap, 1));
     pr.Y = ws_array<float>(ctx, (size_t)n * emb_ld(cap));
-    embed_planes_init(ctx, X, n, d, ldx, cap, pr.ep, st);
     const double eps = search ? o->eps : 0.1;
     pr.copt.eps = eps;
     pr.copt.precision = o->precision;
@@ -196,13 +202,28 @@ int fit_device(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
         pr.copt.hi = search ? 2.0 * eps : 1.0;
     }
     pr.fixed_s = o->s;
+    // The embedding's split planes of X and the certificate's preparation of
+    // X do not depend on the PCA: a side stream computes them while the
+    // PCA's chain of small kernels leaves most of the GPU idle.  The first
+    // embedding waits for them; every exit waits for the side stream, so no
+    // later call reuses the workspace under it.
     PrepMat px;
+    cudaStream_t side = side_stream(ctx);
+    struct SideJoin {
+        cudaStream_t s;
+        ~SideJoin() { cudaStreamSynchronize(s); }
+    } side_join{side};
+    ADAGIO_CUDA(cudaEventRecord(ctx->side_ev[0], st));
+    ADAGIO_CUDA(cudaStreamWaitEvent(side, ctx->side_ev[0], 0));
+    embed_planes_init(ctx, X, n, d, ldx, cap, pr.ep, side);
     {
         unsigned *xflags = ws_array<unsigned>(ctx, 1);
-        ADAGIO_CUDA(cudaMemsetAsync(xflags, 0, sizeof(unsigned), st));
-        cert_prepare_x(ctx, X, ldx, n, d, o->precision, px, xflags, st);
+        ADAGIO_CUDA(cudaMemsetAsync(xflags, 0, sizeof(unsigned), side));
+        cert_prepare_x(ctx, X, ldx, n, d, o->precision, px, xflags, side);
         pr.px = &px;  // X is finite: the PCA's preparation checked it
     }
+    ADAGIO_CUDA(cudaEventRecord(ctx->side_ev[1], side));
+    pr.prep_ready = ctx->side_ev[1];
 
     int status = ADAGIO_OK;
     int r_final, s_final;

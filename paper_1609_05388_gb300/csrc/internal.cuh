@@ -108,6 +108,10 @@ struct adagio_ctx {
     // device status word of the tensor-core GEMMs (nonzero: a bounded wait
     // gave up); checked and cleared by the calls that synchronise
     int *dev_status = nullptr;
+    // a side stream and two events for work that overlaps the caller's
+    // stream (created on first use)
+    cudaStream_t side_stream = nullptr;
+    cudaEvent_t side_ev[2] = {nullptr, nullptr};
     // streams and pinned host memory of batched fits (grown on demand)
     std::vector<cudaStream_t> batch_streams;
     void *batch_host = nullptr;
@@ -167,6 +171,8 @@ BoundModel bound_model(int precision, int K);
 // Synchronises st and fails with ADAGIO_E_TIMEOUT (clearing the word) when a
 // tensor-core GEMM enqueued on the context recorded a timeout.
 void check_device_status(adagio_ctx *ctx, cudaStream_t st);
+// The context's side stream (created on first use, with its two events).
+cudaStream_t side_stream(adagio_ctx *ctx);
 
 // Releases the dimension predictor held by a context (mlp.cu).
 void free_predictor(adagio_ctx *ctx);

@@ -206,17 +206,17 @@ void PCA::deflate(float *M, int r, cudaStream_t st) {
 // Orthonormalises the rows of M (b x d): shifted CholeskyQR3 (Fukaya et al.,
 // SIAM J. Sci. Comput. 2020) in FP32.  Each pass forms the Gram M M^T, factors
 // it as R^T R with the blocked one-CTA Cholesky and replaces M by R^{-T} M
-// (block forward substitution).  The first pass takes its Gram in FP64 and a
-// shift of 1e-5 of the largest diagonal entry, so it succeeds for any
-// conditioning an FP32 matrix can carry and leaves a basis with condition
-// number below ~300; two unshifted-size passes with FP32 Grams then restore
-// orthonormality to FP32 precision.
-void PCA::orth(float *M, int b, cudaStream_t st, int passes) {
+// (block forward substitution).  The first pass takes its Gram in FP64 and
+// (by default) a shift of 1e-5 of the largest diagonal entry, so it succeeds
+// for any conditioning an FP32 matrix can carry and leaves a basis with
+// condition number below ~300; passes with FP32 Grams (shift 1e-7, then
+// none) then restore orthonormality.
+void PCA::orth(float *M, int b, cudaStream_t st, int passes, float shift0) {
     for (int pass = 0; pass < passes; ++pass) {
         if (pass == 0) {
             gemm_f64_splitk(b, b, d, MatView<float>{M, d, 1}, MatView<float>{M, 1, d}, G, f64part,
                             kF64Chunk, st);
-            cholesky_blocked<double>(G, b, 1e-5f, R32, Dinv, st);
+            cholesky_blocked<double>(G, b, shift0, R32, Dinv, st);
         } else {
             gemm_f32(b, b, d, 1.0f, MatView<float>{M, d, 1}, MatView<float>{M, 1, d}, 0.0f, G32, b,
                      part, part_floats, st);
@@ -338,7 +338,9 @@ void PCA::accept_block(cudaStream_t st) {
     float *dst = P + (size_t)s_done * d;
     copy_rows(V, d, dst, d, s_blk, d, st);
     deflate(dst, s_blk, st);
-    orth(dst, s_blk, st);
+    // the Ritz vectors are orthonormal to ~1e-6 and the deflation moves them
+    // by less: one unshifted pass with an FP64 Gram suffices
+    orth(dst, s_blk, st, 1, 0.0f);
     canonical_signs(dst, s_blk, d, d, st);
     ADAGIO_CUDA(cudaMemcpyAsync(theta + s_done, theta_blk, sizeof(double) * s_blk,
                                 cudaMemcpyDeviceToDevice, st));

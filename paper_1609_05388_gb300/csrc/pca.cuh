@@ -66,9 +66,12 @@ struct PCA {
     void begin_block(int s_needed, cudaStream_t st);
     void accept_block(cudaStream_t st);
     void deflate(float *M, int r, cudaStream_t st);
-    // passes: 3 (orthonormal to FP32 precision) or 1 (the shifted first pass:
-    // a well-conditioned basis of the same span)
-    void orth(float *M, int b, cudaStream_t st, int passes = 3);
+    // passes: 3 (orthonormal to FP32 precision from any FP32-representable
+    // conditioning) or 1 (the first pass alone: with shift0 > 0 a
+    // well-conditioned basis of the same span; with shift0 = 0 the
+    // re-orthonormalisation of an almost orthonormal M); shift0 is relative
+    // to the largest Gram entry
+    void orth(float *M, int b, cudaStream_t st, int passes = 3, float shift0 = 1e-5f);
     bool rr_follows(int it) const;
     void times_C(const float *M, int b, float *out, cudaStream_t st);  // out = M C
     void copy_status(cudaStream_t st);

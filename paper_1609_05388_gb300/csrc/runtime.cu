@@ -104,6 +104,14 @@ void check_device_status(adagio_ctx *ctx, cudaStream_t st) {
     }
 }
 
+cudaStream_t side_stream(adagio_ctx *ctx) {
+    if (!ctx->side_stream) {
+        ADAGIO_CUDA(cudaStreamCreateWithFlags(&ctx->side_stream, cudaStreamNonBlocking));
+        for (cudaEvent_t &e : ctx->side_ev) ADAGIO_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
+    return ctx->side_stream;
+}
+
 const float *stage_input(adagio_ctx *ctx, const float *p, int64_t rows, int cols, int64_t ld,
                          int64_t *ld_out, cudaStream_t st) {
     if (is_device_ptr(p, ctx->device)) {
@@ -196,6 +204,9 @@ int adagio_ctx_destroy(adagio_ctx *ctx) {
         if (ctx->host_stage) cudaFreeHost(ctx->host_stage);
         for (auto &e : ctx->tc_sched) cudaFree(e.second);
         for (cudaStream_t s : ctx->batch_streams) cudaStreamDestroy(s);
+        if (ctx->side_stream) cudaStreamDestroy(ctx->side_stream);
+        for (cudaEvent_t e : ctx->side_ev)
+            if (e) cudaEventDestroy(e);
         if (ctx->batch_host) cudaFreeHost(ctx->batch_host);
         if (ctx->dev_status) cudaFree(ctx->dev_status);
         if (prev >= 0) cudaSetDevice(prev);
