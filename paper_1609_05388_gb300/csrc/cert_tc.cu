@@ -175,15 +175,15 @@ static_assert(sizeof(WarpTotals) <= 64, "per-warp totals exceed their shared-mem
 // (dx2 > 8 ex and dy2 > 8 ey) and
 //   B <= min(1e-5, max(1e-6, distance of delta to the nearest bin edge or eps)),
 // i.e. B is within the maximum's tolerance, and either B <= 1e-6 or no edge
-// and not eps lies within B of delta; every other pair is flagged in qmask for
-// the exact recompute.  A NaN Gram entry (how the caller marks a column that
+// and not eps lies within B of delta; every other pair is flagged (bit c of
+// q8, the piece's queue mask) for the exact recompute.  A NaN Gram entry (how the caller marks a column that
 // is not a real pair) fails the test: the pair is flagged and adds nothing to
 // the statistics, and the caller clears its qmask bit.
 template <bool DUMP>
 __device__ __forceinline__ void classify_piece(const float (&gx)[kPiece], const float (&gy)[kPiece],
                                                const float4 ri, const float4 *__restrict__ rsj,
                                                int c0, const EpiConst &k, uint32_t *hrow, RowAcc &a,
-                                               unsigned long long &qmask, float4 *dump_row) {
+                                               uint32_t &q8, float4 *dump_row) {
 #pragma unroll
     for (int c = 0; c < kPiece; ++c) {
         const float4 rj = __ldg(rsj + c);
@@ -203,7 +203,7 @@ __device__ __forceinline__ void classify_piece(const float (&gx)[kPiece], const 
         const float lim = fminf(kMaxTol, fmaxf(kExempt, fminf(dedge, fabsf(delta - k.eps))));
         const float cond = fminf(fmaf(-8.0f, ex, dx2), fmaf(-8.0f, ey, dy2));
         const bool ok = (cond > 0.0f) & (B <= lim);
-        qmask |= ok ? 0ull : (1ull << (c0 + c));
+        q8 |= ok ? 0u : (1u << c);
         const bool in_range = (t >= 0.0f) & (t < (float)kBins);
         const bool binned = ok & in_range;
         const int bin = (int)t;
@@ -549,20 +549,24 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int c0 = pend_pieces * kPiece;
             uint32_t ux[kPiece], uy[kPiece];
             tmem_ld8x2_wait(gx_stage + c0, gy_run + c0, ux, uy);
+            // this piece's valid-pair bits; bit c is a constant after unrolling
+            const uint32_t v8 = (uint32_t)(pend_vmask >> c0) & 0xFFu;
             float px[kPiece], py[kPiece];
 #pragma unroll
             for (int c = 0; c < kPiece; ++c) {
-                const bool valid = (pend_vmask >> (c0 + c)) & 1ull;
+                const bool valid = (v8 >> c) & 1u;
                 px[c] = valid ? __uint_as_float(ux[c]) : __int_as_float(0x7fc00000);
                 py[c] = __uint_as_float(uy[c]);
             }
+            uint32_t q8 = 0u;
             if (DUMP && p.dump && pend_u < p.dump_tiles) {
                 float4 *drow = p.dump + (size_t)pend_u * kTile * kTile + r * kTile + h * kEpiCols + c0;
-                classify_piece<DUMP>(px, py, pend_ri, p.rs + pend_j0 + c0, c0, k, hrow, acc, qmask, drow);
+                classify_piece<DUMP>(px, py, pend_ri, p.rs + pend_j0 + c0, c0, k, hrow, acc, q8, drow);
             } else {
-                classify_piece<false>(px, py, pend_ri, p.rs + pend_j0 + c0, c0, k, hrow, acc, qmask,
+                classify_piece<false>(px, py, pend_ri, p.rs + pend_j0 + c0, c0, k, hrow, acc, q8,
                                       nullptr);
             }
+            qmask |= (unsigned long long)q8 << c0;
             ++pend_pieces;
         };
         // queue pushes and warp totals of the fully classified pending tile
