@@ -19,16 +19,33 @@ namespace adagio {
 
 namespace {
 
+// Error-free sum of two floats (TwoSum, Knuth TAOCP vol. 2, 4.2.2): s + e = a + b.
+__device__ __forceinline__ void two_sum_f(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bp = __fsub_rn(s, a);
+    const float ap = __fsub_rn(s, bp);
+    e = __fadd_rn(__fsub_rn(a, ap), __fsub_rn(b, bp));
+}
+
+// Column sums of a chunk of rows.  Each thread keeps an unevaluated
+// double-float sum (hi + lo, TwoSum per element): about 2^-44 relative per
+// step, FP64-grade without the slow FP64 pipe; the 8 partial sums of a column
+// are then added in FP64.
 __global__ void colsum_partial_kernel(const float *__restrict__ X, int64_t n, int K, int64_t ld,
                                       int64_t rows_per_chunk, double *__restrict__ part) {
     const int c = blockIdx.x * 32 + threadIdx.x;
     const int64_t r0 = (int64_t)blockIdx.y * rows_per_chunk;
     const int64_t r1 = min(n, r0 + rows_per_chunk);
-    double acc = 0.0;
+    float hi = 0.0f, lo = 0.0f;
     if (c < K)
-        for (int64_t r = r0 + threadIdx.y; r < r1; r += blockDim.y) acc += (double)X[r * ld + c];
+        for (int64_t r = r0 + threadIdx.y; r < r1; r += blockDim.y) {
+            float s, e;
+            two_sum_f(hi, __ldg(X + r * ld + c), s, e);
+            hi = s;
+            lo = __fadd_rn(lo, e);
+        }
     __shared__ double sh[8][33];
-    sh[threadIdx.y][threadIdx.x] = acc;
+    sh[threadIdx.y][threadIdx.x] = (double)hi + (double)lo;
     __syncthreads();
     if (threadIdx.y == 0 && c < K) {
         double t = 0.0;
@@ -46,7 +63,13 @@ __global__ void colmean_kernel(const double *__restrict__ part, int chunks, int 
     mu[c] = (float)(t / (double)n);
 }
 
-// One warp per row: centre, FP32 copy, norms, |max|, finiteness.
+// One warp per row: centre, FP32 copy, norms, |max|, finiteness.  The squared
+// 2-norm is a double-float sum of exact squares (FMA TwoProduct, TwoSum), so
+// it is correct to about one FP32 rounding without the slow FP64 pipe.  The
+// 4-norm feeds only a bound coefficient: an FP32 sum of fourth powers, taken
+// 2^-10 high, while the row's largest |x| lies in [1e-8, 1e8] (no overflow, and
+// what underflows is below 1e-6 of the sum); outside that range the upper
+// bound ||x||_4 <= sqrt(||x||_inf ||x||_2).
 __global__ void rowprep_kernel(const float *__restrict__ X, int64_t n, int64_t n_pad, int K,
                                int64_t ld, const float *__restrict__ mu, float *__restrict__ c32,
                                int Kp32, RowStat *__restrict__ rs, float s4, float s1,
@@ -54,18 +77,22 @@ __global__ void rowprep_kernel(const float *__restrict__ X, int64_t n, int64_t n
     const int lane = threadIdx.x & 31;
     const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= n_pad) return;
-    double n2 = 0.0, n4 = 0.0;
+    float h2 = 0.0f, l2 = 0.0f, n4 = 0.0f;
     float amax = 0.0f;
     bool bad = false;
     if (r < n) {
         for (int k = lane; k < K; k += 32) {
-            float x = X[r * ld + k];
+            const float x = __ldg(X + r * ld + k);
             bad |= !isfinite(x);
-            float xc = __fsub_rn(x, mu[k]);
+            const float xc = __fsub_rn(x, __ldg(mu + k));
             amax = fmaxf(amax, fabsf(xc));
-            double q = (double)xc * (double)xc;
-            n2 += q;
-            n4 += q * q;
+            const float p = __fmul_rn(xc, xc);
+            const float pe = __fmaf_rn(xc, xc, -p);  // xc^2 = p + pe exactly
+            float s, e;
+            two_sum_f(h2, p, s, e);
+            h2 = s;
+            l2 = __fadd_rn(l2, __fadd_rn(e, pe));
+            n4 = __fmaf_rn(p, p, n4);
             if (c32) c32[r * Kp32 + k] = xc;
         }
     }
@@ -74,16 +101,22 @@ __global__ void rowprep_kernel(const float *__restrict__ X, int64_t n, int64_t n
         for (int k = k0 + lane; k < Kp32; k += 32) c32[r * Kp32 + k] = 0.0f;
     }
     for (int o = 16; o > 0; o >>= 1) {
-        n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+        const float oh = __shfl_xor_sync(0xffffffffu, h2, o), ol = __shfl_xor_sync(0xffffffffu, l2, o);
+        float s, e;
+        two_sum_f(h2, oh, s, e);
+        h2 = s;
+        l2 = __fadd_rn(__fadd_rn(l2, ol), e);
         n4 += __shfl_xor_sync(0xffffffffu, n4, o);
         amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     }
     unsigned anybad = __ballot_sync(0xffffffffu, bad);
     if (lane == 0) {
         RowStat st;
-        st.n2 = (float)n2;
-        st.q4 = s4 * (float)sqrt(sqrt(n4));
-        st.q1 = s1 * (float)sqrt(n2);
+        const float n2 = __fadd_rn(h2, l2);
+        st.n2 = n2;
+        const bool in_range = amax >= 1e-8f && amax <= 1e8f;
+        st.q4 = s4 * (in_range ? sqrtf(sqrtf(n4 * (1.0f + 9.765625e-4f))) : sqrtf(amax * sqrtf(n2)));
+        st.q1 = s1 * sqrtf(n2);
         st.pad = 0.0f;
         rs[r] = st;
         if (amax > 0.0f) atomicMax(amax_bits, __float_as_uint(amax));
