@@ -81,6 +81,79 @@ __global__ void splitk_reduce_kernel(const float *__restrict__ part, int64_t chu
 
 constexpr int kSplitRows = 2048;
 
+// C_z = A B over the K chunk z, FP32 operands, each product exact (FMA
+// TwoProduct) and summed as an unevaluated double-float (TwoSum; Dekker 1971,
+// Knuth TAOCP vol. 2, 4.2.2): FP64-grade sums on the FP32 pipes, which run far
+// faster than FP64 on this GPU.  Same tiling as gemm_kernel; FP64 output.
+__device__ __forceinline__ void df_fma(float a, float b, float &hi, float &lo) {
+    const float p = __fmul_rn(a, b);
+    const float pe = __fmaf_rn(a, b, -p);  // a b = p + pe exactly
+    const float s = __fadd_rn(hi, p);
+    const float bp = __fsub_rn(s, hi);
+    const float ap = __fsub_rn(s, bp);
+    const float e = __fadd_rn(__fsub_rn(hi, ap), __fsub_rn(p, bp));
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, pe));
+}
+
+__global__ void __launch_bounds__(GNT) gemm_df_kernel(int M, int N, int K, int kchunk, MatView<float> A,
+                                                      MatView<float> B, double *C, int64_t ldc,
+                                                      int64_t zstride) {
+    __shared__ float As[GK][GT + 1];
+    __shared__ float Bs[GK][GT + 1];
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int row0 = blockIdx.y * GT, col0 = blockIdx.x * GT;
+    const int kbeg = blockIdx.z * kchunk;
+    const int kend = min(K, kbeg + kchunk);
+    C += (int64_t)blockIdx.z * zstride;
+    float hi[4][4], lo[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) hi[i][j] = lo[i][j] = 0.0f;
+    const bool a_kmajor = (A.cs == 1);
+    const bool b_nmajor = (B.cs == 1);
+    for (int k0 = kbeg; k0 < kend; k0 += GK) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + GNT * q;
+            int r, k;
+            if (a_kmajor) { r = e >> 4; k = e & 15; } else { k = e >> 6; r = e & 63; }
+            const int gr = row0 + r, gk = k0 + k;
+            As[k][r] = (gr < M && gk < kend) ? A.p[(int64_t)gr * A.rs + (int64_t)gk * A.cs] : 0.0f;
+            int c, kb;
+            if (b_nmajor) { kb = e >> 6; c = e & 63; } else { c = e >> 4; kb = e & 15; }
+            const int gc = col0 + c, gkb = k0 + kb;
+            Bs[kb][c] = (gc < N && gkb < kend) ? B.p[(int64_t)gkb * B.rs + (int64_t)gc * B.cs] : 0.0f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < GK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) df_fma(a[i], b[j], hi[i][j], lo[i][j]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int r = row0 + ty + 16 * i;
+        if (r >= M) continue;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int c = col0 + tx + 16 * j;
+            if (c >= N) continue;
+            C[(int64_t)r * ldc + c] = (double)hi[i][j] + (double)lo[i][j];
+        }
+    }
+}
+
 __global__ void splitk_reduce_f64_kernel(const double *__restrict__ part, int chunks, int64_t mn,
                                          double *__restrict__ C) {
     const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -787,8 +860,7 @@ void gemm_f64_splitk(int M, int N, int K, MatView<float> A, MatView<float> B, do
     if (M <= 0 || N <= 0) return;
     const int chunks = (int)ceil_div(K, kchunk);
     dim3 grid((unsigned)ceil_div(N, GT), (unsigned)ceil_div(M, GT), (unsigned)chunks);
-    gemm_kernel<float, float, double, double><<<grid, GNT, 0, st>>>(
-        M, N, K, kchunk, 1.0, A, B, 0.0, partials, N, (int64_t)M * N);
+    gemm_df_kernel<<<grid, GNT, 0, st>>>(M, N, K, kchunk, A, B, partials, N, (int64_t)M * N);
     ADAGIO_CHECK_LAUNCH();
     const int64_t mn = (int64_t)M * N;
     splitk_reduce_f64_kernel<<<(unsigned)ceil_div(mn, 256), 256, 0, st>>>(partials, chunks, mn, C);
