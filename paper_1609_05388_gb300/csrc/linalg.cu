@@ -618,7 +618,7 @@ constexpr int kJacobiColIt = (kJacobiMax / 2 + 31) / 32;  // column-pair rotatio
 __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const double *__restrict__ Hin, int b,
                                                                 double *__restrict__ theta,
                                                                 float *__restrict__ Uout,
-                                                                int max_sweeps) {
+                                                                int max_sweeps, float off_rel2) {
     extern __shared__ float sm[];
     const int B = (b + 1) & ~1;   // even size (index b is a zero dummy when b is odd)
     const int half = B / 2;
@@ -730,10 +730,11 @@ __global__ void __launch_bounds__(kJacobiThreads) jacobi_kernel(const double *__
         if (tid == 0) {
             float o2 = 0.0f, d2 = 0.0f;
             for (int w = 0; w < nt / 32; ++w) { o2 += red[w][0]; d2 += red[w][1]; }
-            // converged: off-diagonal norm <= 1e-6 of the diagonal's; or at the
-            // FP32 rounding floor: after the first sweeps (the quadratic
-            // phase) a sweep no longer halves the off-diagonal mass
-            s_done = (o2 <= 1e-12f * d2) || (sweep >= 2 && o2 > 0.25f * prev_off);
+            // converged: squared off-diagonal norm <= off_rel2 of the
+            // diagonal's; or at the FP32 rounding floor: after the first
+            // sweeps (the quadratic phase) a sweep no longer halves the
+            // off-diagonal mass
+            s_done = (o2 <= off_rel2 * d2) || (sweep >= 2 && o2 > 0.25f * prev_off);
             prev_off = o2;
         }
         __syncthreads();
@@ -979,11 +980,12 @@ void trsm_rows(const double *R, int b, float *V, int64_t ldv, int d, cudaStream_
     ADAGIO_CHECK_LAUNCH();
 }
 
-void jacobi_eig(const double *H, int b, double *theta, float *U, int max_sweeps, cudaStream_t st) {
+void jacobi_eig(const double *H, int b, double *theta, float *U, int max_sweeps, float off_rel2,
+                cudaStream_t st) {
     if (b > kJacobiMax) fail(ADAGIO_E_INVALID_ARG, "internal: Jacobi block %d > %d", b, kJacobiMax);
     const size_t smem = jacobi_smem(b);
     set_max_dyn_smem((const void *)jacobi_kernel, (int)smem);
-    jacobi_kernel<<<1, kJacobiThreads, smem, st>>>(H, b, theta, U, max_sweeps);
+    jacobi_kernel<<<1, kJacobiThreads, smem, st>>>(H, b, theta, U, max_sweeps, std::max(off_rel2, 1e-12f));
     ADAGIO_CHECK_LAUNCH();
 }
 

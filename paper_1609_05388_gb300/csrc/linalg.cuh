@@ -79,8 +79,12 @@ void gemm_f32(int M, int N, int K, float alpha, MatView<float> A, MatView<float>
 // Symmetric eigen-decomposition of a b x b matrix (b <= kJacobiMax) by
 // parallel cyclic Jacobi in one CTA: H (FP64 in) -> theta (descending, FP64
 // out) and U (b x b FP32 row-major, column c = eigenvector of theta[c]).
+// Sweeps stop once the squared off-diagonal Frobenius norm is at most
+// off_rel2 (at least 1e-12) of the diagonal's, at the FP32 floor, or after
+// max_sweeps.
 constexpr int kJacobiMax = 160;
-void jacobi_eig(const double *H, int b, double *theta, float *U, int max_sweeps, cudaStream_t st);
+void jacobi_eig(const double *H, int b, double *theta, float *U, int max_sweeps, float off_rel2,
+                cudaStream_t st);
 
 // Per-row residual norms ||W_i - theta_i V_i|| for i < s (FP32 out).
 void ritz_residuals(const float *W, const float *V, int64_t ld, int d, const double *theta, int s,

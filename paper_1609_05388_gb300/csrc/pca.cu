@@ -277,7 +277,11 @@ void PCA::advance(int s_needed, cudaStream_t st) {
             // separated Ritz values.  Rotations inside a cluster of nearly equal
             // values are left unfinished: they mix directions that are
             // interchangeable, and the convergence test measures the subspace.
-            jacobi_eig(H, b, theta_blk, U, blk.rr == 0 ? 6 : 3, st);
+            // the off-diagonal rows of H are in-subspace residuals of the
+            // Ritz rows: once their norm is below 0.1 tol theta_1 (squared:
+            // 0.01 tol^2 of the diagonal mass, which is at least theta_1^2)
+            // they are negligible next to what the residual test accepts
+            jacobi_eig(H, b, theta_blk, U, blk.rr == 0 ? 6 : 3, (float)(0.01 * tol * tol), st);
             ++blk.rr;
             // V <- U^T V, W <- U^T W
             gemm_f32(b, d, b, 1.0f, MatView<float>{U, 1, b}, MatView<float>{V, d, 1}, 0.0f, T, d,
