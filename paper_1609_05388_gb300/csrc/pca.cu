@@ -255,7 +255,10 @@ void PCA::begin_block(int s_needed, cudaStream_t st) {
     blk.active = true;
     rademacher_block(seed + (uint64_t)s_done * 0x9E3779B9ull, blk.b, d, V, d, st);
     deflate(V, blk.b, st);
-    orth(V, blk.b, st, rr_follows(0) ? 3 : 1);
+    // the +-1 rows are nearly orthogonal (|cos| ~ 1/sqrt(d)) and their common
+    // scale does not matter to the iteration: only a Rayleigh-Ritz step right
+    // away needs an orthonormal start
+    if (rr_follows(0)) orth(V, blk.b, st, 3);
 }
 
 void PCA::advance(int s_needed, cudaStream_t st) {
@@ -341,10 +344,13 @@ void PCA::accept_block(cudaStream_t st) {
     const int s_blk = blk.s_blk;
     float *dst = P + (size_t)s_done * d;
     copy_rows(V, d, dst, d, s_blk, d, st);
-    deflate(dst, s_blk, st);
-    // the Ritz vectors are orthonormal to ~1e-6 and the deflation moves them
-    // by less: one unshifted pass with an FP64 Gram suffices
-    orth(dst, s_blk, st, 1, 0.0f);
+    // the Ritz vectors are orthonormal to ~1e-6 (an orthonormal basis turned
+    // by the Jacobi rotations); a later block's deflation moves them by less,
+    // and one unshifted pass with an FP64 Gram restores FP32 orthonormality
+    if (s_done > 0) {
+        deflate(dst, s_blk, st);
+        orth(dst, s_blk, st, 1, 0.0f);
+    }
     canonical_signs(dst, s_blk, d, d, st);
     ADAGIO_CUDA(cudaMemcpyAsync(theta + s_done, theta_blk, sizeof(double) * s_blk,
                                 cudaMemcpyDeviceToDevice, st));
