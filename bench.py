@@ -44,7 +44,7 @@ WORKLOAD = "mnist_like 60000x784 (10 clusters, rank-50, ~80% zeros, k/255), eps=
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one tile-kernel
 # launch on this workload from one ncu capture of the full launch
 # (profiles/cert_tc_mnist.md), or None once the kernel has changed since.
-TRAFFIC_BYTES = 8416345856 + 37529344
+TRAFFIC_BYTES = 8054875136 + 37042176
 
 
 def parse():
