@@ -2,7 +2,18 @@
 //
 // K9 takes every pair the tile kernels could not classify with certainty and
 // recomputes both squared distances from coordinate differences of the
-// ORIGINAL float32 inputs (no centring, no Gram), one warp per pair.  Each
+// ORIGINAL float32 inputs (no centring, no Gram), one warp per pair, in two
+// levels.  Level 1: each difference rounded once to FP32, its square added
+// by FMA into a short FP32 chain (at most 4 terms), each chain added into a
+// double-float sum (TwoSum), lanes combined in double-float: the squared
+// distance is within 7u (u = 2^-24) of the exact one (2u from the difference,
+// 4u from the chain, u from the final rounding), and the distortion within
+//     B1 = 7u (1 + rho^2) / (1 + rho) + 12u delta,   rho = sqrt(dy2 / dx2)
+// (the numerator error over the denominator, plus the denominator's own
+// rounding), taken as 8u and 13u.  The pair is counted from level 1 when B1
+// <= 1e-6 (the certificate's band: a count may differ only for pairs within
+// 1e-6 of a bin edge or of eps) or when no edge and not eps lies within B1 of
+// its distortion.  Otherwise the warp recomputes it at level 2.  Level 2: each
 // difference is rounded once to FP32 (relative error <= 2^-24), squared
 // exactly by an FMA-based TwoProduct, and the squares are summed as an
 // unevaluated hi + lo pair with TwoSum (Dekker 1971; Knuth TAOCP vol. 2,
@@ -144,6 +155,85 @@ __device__ __forceinline__ DF sq_dist_lanes(const float *__restrict__ a, const f
     return df_add(df_add(c[0], c[1]), df_add(c[2], c[3]));
 }
 
+// Level 1 of this lane's share of sum_k (a_k - b_k)^2.  Chain g is the
+// coordinates 4g .. 4g + 3: their squares summed by FMA in FP32, the chain
+// added into one of two double-float sums.  The chains, their lanes
+// (g mod 32), their order and their accumulators depend only on the
+// coordinate index, not on the load width V, so rows with any alignment give
+// the same bits.  A lane issues all loads of four chains before using them;
+// chains past the end read as zero; the n mod 4 last coordinates are
+// one-term chains.
+template <int V>
+__device__ __forceinline__ void load_chain(const float *__restrict__ p, int g, float (&v)[4]) {
+    if constexpr (V == 4) {
+        const float4 q = __ldg(reinterpret_cast<const float4 *>(p) + g);
+        v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+    } else if constexpr (V == 2) {
+        const float2 q0 = __ldg(reinterpret_cast<const float2 *>(p) + 2 * g);
+        const float2 q1 = __ldg(reinterpret_cast<const float2 *>(p) + 2 * g + 1);
+        v[0] = q0.x; v[1] = q0.y; v[2] = q1.x; v[3] = q1.y;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = __ldg(p + 4 * g + k);
+    }
+}
+
+__device__ __forceinline__ void df_add_chain(DF &acc, float c) {
+    float s, e;
+    two_sum(acc.hi, c, s, e);
+    acc.hi = s;
+    acc.lo = __fadd_rn(acc.lo, e);
+}
+
+template <int V>
+__device__ __forceinline__ DF sq_dist_lanes_fast(const float *__restrict__ a, const float *__restrict__ b,
+                                                 int n, int lane) {
+    constexpr int CH = 4;  // chains per lane and chunk
+    DF c[2] = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+    const int ng = n / 4;
+    for (int base = lane; base < ng; base += 32 * CH) {
+        float x[CH][4], y[CH][4];
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            const int g = base + 32 * u;
+            if (g < ng) {
+                load_chain<V>(a, g, x[u]);
+                load_chain<V>(b, g, y[u]);
+            } else {
+#pragma unroll
+                for (int k = 0; k < 4; ++k) x[u][k] = y[u][k] = 0.0f;
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CH; ++u) {
+            float d = __fsub_rn(x[u][0], y[u][0]), s = __fmul_rn(d, d);
+#pragma unroll
+            for (int k = 1; k < 4; ++k) {
+                d = __fsub_rn(x[u][k], y[u][k]);
+                s = __fmaf_rn(d, d, s);
+            }
+            df_add_chain(c[u & 1], s);
+        }
+    }
+    for (int k = 4 * ng + lane; k < n; k += 32) {
+        const float d = __fsub_rn(__ldg(a + k), __ldg(b + k));
+        df_add_chain(c[0], __fmul_rn(d, d));
+    }
+    return df_add(c[0], c[1]);
+}
+
+// distortion (Eq. 2) of a pair from its double-float squared distances, in
+// the cancellation-free form (FP32 division and square roots, IEEE)
+__device__ __forceinline__ float pair_delta(DF ax, DF ay, float &dx2, float &dy2) {
+    const DF dd = df_sub(ay, ax);
+    dx2 = __fadd_rn(ax.hi, ax.lo);
+    dy2 = __fadd_rn(ay.hi, ay.lo);
+    const float den = __fmaf_rn(__fsqrt_rn(dx2), __fsqrt_rn(dy2), dx2);
+    return __fdiv_rn(fabsf(__fadd_rn(dd.hi, dd.lo)), den);
+}
+
+constexpr float kBandR = 1e-6f;  // a count may differ only for pairs this close to an edge or eps
+
 template <int VX, int VY>
 __global__ void __launch_bounds__(RT, 3) recompute_kernel(const float *__restrict__ X, int64_t ldx,
                                                         int d, const float *__restrict__ Y,
@@ -165,20 +255,38 @@ __global__ void __launch_bounds__(RT, 3) recompute_kernel(const float *__restric
     int ai = 0x7fffffff, aj = 0x7fffffff;
     for (long long q = (long long)blockIdx.x * NW + warp; q < (long long)qlen; q += warps) {
         const int2 pr = queue[q];
-        DF ax = sq_dist_lanes<VX>(X + (int64_t)pr.x * ldx, X + (int64_t)pr.y * ldx, d, lane);
-        DF ay = sq_dist_lanes<VY>(Y + (int64_t)pr.x * ldy, Y + (int64_t)pr.y * ldy, m, lane);
-        ax = warp_sum(ax);
-        ay = warp_sum(ay);
+        const float *xi = X + (int64_t)pr.x * ldx, *xj = X + (int64_t)pr.y * ldx;
+        const float *yi = Y + (int64_t)pr.x * ldy, *yj = Y + (int64_t)pr.y * ldy;
+        DF ax = warp_sum(sq_dist_lanes_fast<VX>(xi, xj, d, lane));
+        DF ay = warp_sum(sq_dist_lanes_fast<VY>(yi, yj, m, lane));
+        float delta = 0.0f;
+        int exact = 0;
+        if (lane == 0 && ax.hi != 0.0f) {
+            float dx2, dy2;
+            delta = pair_delta(ax, ay, dx2, dy2);
+            const float rho2 = __fdiv_rn(dy2, dx2), rho = __fsqrt_rn(rho2);
+            const float u = 5.9604645e-08f;
+            const float b1 = u * (8.0f * (1.0f + rho2) / (1.0f + rho) + 13.0f * delta);
+            // distance to the nearest bin edge (edges at integer t in [0, 64]) and to eps
+            const float t = (delta - cc.lo) * cc.inv_w;
+            const float tc = fminf(fmaxf(t, -0.5f), (float)kBins + 0.5f);
+            const float dedge = fabsf(tc - rintf(tc)) * cc.w;
+            const bool settled = (b1 <= kBandR) || (dedge > b1 && fabsf(delta - cc.eps) > b1);
+            exact = settled ? 0 : 1;
+        }
+        if (__shfl_sync(0xffffffffu, exact, 0)) {
+            // level 2 for this pair (rare): exact squares, double-float sums
+            ax = warp_sum(sq_dist_lanes<VX>(xi, xj, d, lane));
+            ay = warp_sum(sq_dist_lanes<VY>(yi, yj, m, lane));
+            float dx2, dy2;
+            if (lane == 0) delta = pair_delta(ax, ay, dx2, dy2);
+        }
         if (lane == 0) {
-            // the squares of exact differences sum to zero only if every
+            // the squares of the differences sum to zero only if every
             // difference is zero
             if (ax.hi == 0.0f) {
                 ++ndeg;
             } else {
-                const DF dd = df_sub(ay, ax);
-                const float dx2 = __fadd_rn(ax.hi, ax.lo), dy2 = __fadd_rn(ay.hi, ay.lo);
-                const float den = __fmaf_rn(__fsqrt_rn(dx2), __fsqrt_rn(dy2), dx2);
-                const float delta = __fdiv_rn(fabsf(__fadd_rn(dd.hi, dd.lo)), den);
                 ++npairs;
                 sum += (double)delta;
                 nviol += delta > cc.eps;
