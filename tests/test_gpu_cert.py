@@ -117,6 +117,22 @@ def test_pairs_exactly_on_an_edge(ctx, prec, tiles):
 
 
 @pytest.mark.parametrize("prec,tiles", CERT_MODES)
+def test_pairs_just_off_a_large_edge(ctx, prec, tiles):
+    # Y ~ 1.7500012 X: distortions scatter within a few 1e-7 of 0.7500012, just
+    # above eps = 0.75 (the edge of bin 32).  At this distortion the
+    # recompute's first level bounds its error by ~1.3e-6, more than the 1e-6
+    # band, so pairs between 1e-6 and that bound from the edge are settled by
+    # its exact second level; every pair farther than 1e-6 must count exactly.
+    rng = np.random.default_rng(17)
+    X = np.unique(rng.integers(-8, 9, size=(300, 6)).astype(np.float32), axis=0)
+    Y = (np.float32(1.7500012) * X).astype(np.float32)
+    g = run(ctx, X, Y, 0.75, prec, tiles=tiles)
+    o = certificate(X, Y, 0.75)
+    assert o.near_edge < o.pairs
+    assert_cert_parity(g, o, X, Y)
+
+
+@pytest.mark.parametrize("prec,tiles", CERT_MODES)
 def test_nonfinite_input_rejected(ctx, prec, tiles):
     from paper_1609_05388_gb300 import adagio as lib
     X = np.ones((10, 3), dtype=np.float32)
