@@ -119,9 +119,14 @@ const float *stage_input(adagio_ctx *ctx, const float *p, int64_t rows, int cols
         return p;
     }
     float *d = ws_array<float>(ctx, (size_t)rows * cols);
-    ADAGIO_CUDA(cudaMemcpy2DAsync(d, (size_t)cols * sizeof(float), p, (size_t)ld * sizeof(float),
-                                  (size_t)cols * sizeof(float), (size_t)rows,
-                                  cudaMemcpyHostToDevice, st));
+    // contiguous rows: one linear copy (a pitched copy of many short rows
+    // moves far slower over the host link)
+    if (ld == cols)
+        ADAGIO_CUDA(cudaMemcpyAsync(d, p, (size_t)rows * cols * sizeof(float), cudaMemcpyHostToDevice, st));
+    else
+        ADAGIO_CUDA(cudaMemcpy2DAsync(d, (size_t)cols * sizeof(float), p, (size_t)ld * sizeof(float),
+                                      (size_t)cols * sizeof(float), (size_t)rows,
+                                      cudaMemcpyHostToDevice, st));
     *ld_out = cols;
     return d;
 }
