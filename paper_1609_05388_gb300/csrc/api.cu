@@ -56,12 +56,13 @@ int adagio_distortion(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t
     check_precision(precision);
     check_hist(eps, hist_lo, hist_hi);
     cudaStream_t st = (cudaStream_t)stream;
-    size_t need = staging_bytes(ctx, X, n, d) + staging_bytes(ctx, Y, n, m) +
-                  certify_bytes(ctx, n, d, m, precision);
+    // rows staged 16-byte aligned: the recompute reads them with 16-byte loads
+    size_t need = stage_aligned_bytes(ctx, X, n, d, ldx) + stage_aligned_bytes(ctx, Y, n, m, ldy) +
+                  certify_bytes(ctx, n, d, m, precision) + 1024;
     ws_reserve(ctx, need);
     int64_t lx, ly;
-    const float *dX = stage_input(ctx, X, n, d, ldx, &lx, st);
-    const float *dY = stage_input(ctx, Y, n, m, ldy, &ly, st);
+    const float *dX = stage_aligned(ctx, X, n, d, ldx, &lx, st);
+    const float *dY = stage_aligned(ctx, Y, n, m, ldy, &ly, st);
     CertOptions co;
     co.eps = eps;
     co.lo = hist_lo;

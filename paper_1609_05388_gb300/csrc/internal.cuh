@@ -173,6 +173,15 @@ BoundModel bound_model(int precision, int K);
 void check_device_status(adagio_ctx *ctx, cudaStream_t st);
 // The context's side stream (created on first use, with its two events).
 cudaStream_t side_stream(adagio_ctx *ctx);
+// A device copy of a rows x cols FP32 matrix whose rows start 16-byte aligned
+// (base aligned, row stride a multiple of 4 floats), for kernels that read
+// whole rows with 16-byte loads: aligned device data is used in place; host
+// data is copied linearly and, when cols is not a multiple of 4, re-pitched
+// on the device; unaligned device data is re-pitched.  *ld_out receives the
+// stride; stage_aligned_bytes is the workspace it takes.
+const float *stage_aligned(adagio_ctx *ctx, const float *p, int64_t rows, int cols, int64_t ld,
+                           int64_t *ld_out, cudaStream_t st);
+size_t stage_aligned_bytes(adagio_ctx *ctx, const float *p, int64_t rows, int cols, int64_t ld);
 
 // Releases the dimension predictor held by a context (mlp.cu).
 void free_predictor(adagio_ctx *ctx);

@@ -1,5 +1,6 @@
 // Context, workspace arena, status handling and host/device pointer staging.
 #include "internal.cuh"
+#include "linalg.cuh"
 
 #include <atomic>
 #include <cstring>
@@ -102,6 +103,38 @@ void check_device_status(adagio_ctx *ctx, cudaStream_t st) {
         ADAGIO_CUDA(cudaMemset(ctx->dev_status, 0, sizeof(int)));
         fail(ADAGIO_E_TIMEOUT, "tensor-core GEMM gave up a bounded wait (status %d)", h);
     }
+}
+
+static bool rows_aligned(const float *p, int64_t ld) {
+    return reinterpret_cast<uintptr_t>(p) % 16 == 0 && ld % 4 == 0;
+}
+
+size_t stage_aligned_bytes(adagio_ctx *ctx, const float *p, int64_t rows, int cols, int64_t ld) {
+    const size_t padded = align_up((size_t)rows * emb_ld(cols) * sizeof(float), 256);
+    if (is_device_ptr(p, ctx->device)) return rows_aligned(p, ld) ? 0 : padded;
+    const size_t linear = align_up((size_t)rows * cols * sizeof(float), 256);
+    return linear + (cols % 4 == 0 ? 0 : padded);
+}
+
+const float *stage_aligned(adagio_ctx *ctx, const float *p, int64_t rows, int cols, int64_t ld,
+                           int64_t *ld_out, cudaStream_t st) {
+    const float *src = p;
+    int64_t lds = ld;
+    if (!is_device_ptr(p, ctx->device)) {
+        src = stage_input(ctx, p, rows, cols, ld, &lds, st);  // linear, stride cols
+    } else if (rows_aligned(p, ld)) {
+        *ld_out = ld;
+        return p;
+    }
+    if (rows_aligned(src, lds)) {
+        *ld_out = lds;
+        return src;
+    }
+    const int ldp = emb_ld(cols);
+    float *d = ws_array<float>(ctx, (size_t)rows * ldp);
+    copy_rows(src, lds, d, ldp, (int)rows, cols, st);
+    *ld_out = ldp;
+    return d;
 }
 
 cudaStream_t side_stream(adagio_ctx *ctx) {

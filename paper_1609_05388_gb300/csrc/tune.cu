@@ -15,10 +15,6 @@ using namespace adagio;
 
 namespace {
 
-size_t staging_bytes(adagio_ctx *ctx, const void *p, int64_t rows, int cols) {
-    return is_device_ptr(p, ctx->device) ? 0 : align_up((size_t)rows * cols * sizeof(float), 256);
-}
-
 // the fastest of one warm-up and three timed certificates, tile kernel only
 double time_config(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_t ldy,
                    int64_t n, int d, int m, const CertOptions &co, cudaStream_t st) {
@@ -75,11 +71,11 @@ int adagio_autotune_tiles(adagio_ctx *ctx, const float *X, int64_t n, int d, int
     ADAGIO_REQUIRE(precision == ADAGIO_PREC_FP16X3 || precision == ADAGIO_PREC_BF16X3,
                    "the tile configuration applies to the split precisions, not %d", precision);
     cudaStream_t st = (cudaStream_t)stream;
-    ws_reserve(ctx, staging_bytes(ctx, X, n, d) + staging_bytes(ctx, Y, n, m) +
+    ws_reserve(ctx, stage_aligned_bytes(ctx, X, n, d, ldx) + stage_aligned_bytes(ctx, Y, n, m, ldy) +
                         certify_bytes(ctx, n, d, m, precision) + 4096);
     int64_t lx, ly;
-    const float *dX = stage_input(ctx, X, n, d, ldx, &lx, st);
-    const float *dY = stage_input(ctx, Y, n, m, ldy, &ly, st);
+    const float *dX = stage_aligned(ctx, X, n, d, ldx, &lx, st);
+    const float *dY = stage_aligned(ctx, Y, n, m, ldy, &ly, st);
     CertOptions co;
     co.eps = eps;
     co.lo = 0.0;
