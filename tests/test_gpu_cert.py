@@ -229,3 +229,54 @@ def test_strided_host_inputs_match_contiguous(ctx):
     got = lib.Certificate.from_struct(c)
     assert got.max == ref.max and got.mean == ref.mean
     assert np.array_equal(got.hist, ref.hist) and got.violations == ref.violations
+
+
+def test_unaligned_device_rows_match_contiguous(ctx):
+    """Device views whose row stride is not a multiple of 4 floats are
+    re-pitched to 16-byte aligned rows before the certificate; the result is
+    the one of the contiguous arrays, bit for bit."""
+    import torch
+    rng = np.random.default_rng(29)
+    n, d, m = 650, 21, 11
+    X = rng.standard_normal((n, d)).astype(np.float32)
+    Y = (X @ rng.standard_normal((d, m)).astype(np.float32) / np.sqrt(m)).astype(np.float32)
+    Xw = torch.zeros((n, d + 2), dtype=torch.float32, device="cuda")
+    Yw = torch.zeros((n, m + 1), dtype=torch.float32, device="cuda")
+    Xw[:, :d] = torch.from_numpy(X).cuda()
+    Yw[:, :m] = torch.from_numpy(Y).cuda()
+    ref = ctx.distortion(X, Y, 0.3, precision=1)
+    got = ctx.distortion(Xw[:, :d], Yw[:, :m], 0.3, precision=1)
+    torch.cuda.synchronize()
+    assert got.max == ref.max and got.mean == ref.mean
+    assert np.array_equal(got.hist, ref.hist) and got.violations == ref.violations
+
+
+@pytest.mark.parametrize("prec", [1, 2])
+def test_full_size_large_sampled(ctx, prec):
+    """200 000 x 2048 (2.0e10 pairs, the largest synthetic workload: power-law
+    spectrum plus Laplace outliers): properties at full size, sampled pairs by
+    the oracle.  The map is a JL matrix of m = 300 rows, the oracle's bit for bit."""
+    wl = synth.large(seed=4)
+    n, d, m = wl.X.shape[0], wl.X.shape[1], 300
+    S = ctx.jl_matrix(9, m, d)
+    assert np.array_equal(S, O.jl_matrix(9, m, d).astype(np.float32))
+    Xd = torch.from_numpy(wl.X).cuda()
+    Y = (Xd @ torch.from_numpy(S).cuda().T).contiguous()
+    g = ctx.distortion(Xd, Y, 0.1, precision=prec)
+    Yh = Y.cpu().numpy()
+    assert g.pairs == n * (n - 1) // 2
+    assert int(g.hist.sum()) + g.overflow + g.degenerate == g.pairs
+    d_arg = pair_distortion(wl.X, Yh, [g.argmax_i], [g.argmax_j])[0]
+    assert abs(d_arg - g.max) <= 1e-5
+    rng = np.random.default_rng(5)
+    I = rng.integers(0, n, 100000)
+    J = rng.integers(0, n, 100000)
+    keep = I != J
+    dl = pair_distortion(wl.X, Yh, I[keep], J[keep])
+    dl = dl[np.isfinite(dl)]
+    assert dl.max() <= g.max + 1e-5
+    good = g.pairs - g.degenerate
+    p_hat = np.mean(dl > 0.1)
+    p = g.violations / good
+    assert abs(p - p_hat) <= 6 * np.sqrt(max(p * (1 - p), 1e-12) / dl.size) + 1e-6
+    assert abs(g.mean - dl.mean()) <= 6 * dl.std() / np.sqrt(dl.size)
