@@ -98,6 +98,25 @@ typedef struct {
 } adagio_cert;
 
 /*
+ * One shard's part of a certificate (adagio_distortion_shard): the raw sums
+ * that adagio_cert_merge combines.  Fields as in adagio_cert, except
+ *  pairs        the pairs of this shard's tiles
+ *  sum          sum of the distortions of its non-degenerate pairs
+ *  bound_sum    sum of their error bounds
+ *  max          -1 when the shard has no non-degenerate pair
+ *  max_bound    largest per-pair error bound
+ *  shard, nshards   which part of how many
+ */
+typedef struct {
+    uint64_t pairs, degenerate, violations, overflow, recomputed;
+    uint64_t hist[ADAGIO_HIST_BINS];
+    double sum, bound_sum, max, max_bound;
+    int64_t argmax_i, argmax_j;
+    double hist_lo, hist_hi, eps;
+    int32_t shard, nshards;
+} adagio_cert_part;
+
+/*
  * Options of adagio_fit.  Fill with adagio_default_fit_opts() first.
  *  eps         > 0: search the smallest certified target dimension m (the
  *              exhaustive certificate's maximum distortion <= eps) by
@@ -159,6 +178,35 @@ size_t adagio_workspace_bytes(const adagio_ctx *ctx);
 int adagio_distortion(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
                       const float *Y, int m, int64_t ldy, double eps, double hist_lo,
                       double hist_hi, int precision, adagio_cert *out, void *stream);
+
+/*
+ * Shard `shard` of `nshards` of the certificate of adagio_distortion (the
+ * same pairs, Eq. 2 and Eq. 3, split so that several GPUs or calls can each
+ * take a part: the introduction's list of contributions and the conclusion
+ * call the method amenable to distributed implementation).
+ * The pairs are grouped in 128 x 128 tiles of the upper triangle, numbered
+ * row by row; shard s takes the tiles [T s / nshards, T (s + 1) / nshards) of
+ * the T tiles.  The partition depends only on n, so shards computed on
+ * different GPUs (whatever their tuned tile configuration) cover every pair
+ * exactly once.  Arguments as adagio_distortion; 0 <= shard < nshards.
+ * Writes `out`; synchronises `stream`.  ADAGIO_E_INVALID_ARG on bad sizes or
+ * shard numbers.
+ */
+int adagio_distortion_shard(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
+                            const float *Y, int m, int64_t ldy, double eps, double hist_lo,
+                            double hist_hi, int precision, int shard, int nshards,
+                            adagio_cert_part *out, void *stream);
+
+/*
+ * Combines the `count` parts of one sharded certificate (host only, no GPU
+ * work): counts and histograms add, the maximum is the largest (ties: the
+ * lexicographically smallest pair, as in one call), the mean is the summed
+ * distortions over the non-degenerate pairs.  Counts, histogram, maximum and
+ * its pair equal those of adagio_distortion; the mean agrees to rounding.
+ * ADAGIO_E_INVALID_ARG unless the parts are shards 0 .. count - 1 of count with
+ * the same eps and histogram range.
+ */
+int adagio_cert_merge(const adagio_cert_part *parts, int count, adagio_cert *out);
 
 /*
  * Allocation-free certificate (the paper has no counterpart; this is a

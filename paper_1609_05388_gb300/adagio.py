@@ -53,6 +53,20 @@ class CertStruct(ctypes.Structure):
     ]
 
 
+class CertPartStruct(ctypes.Structure):
+    """adagio_cert_part: one shard's raw sums (adagio_distortion_shard)."""
+    _fields_ = [
+        ("pairs", ctypes.c_uint64), ("degenerate", ctypes.c_uint64),
+        ("violations", ctypes.c_uint64), ("overflow", ctypes.c_uint64),
+        ("recomputed", ctypes.c_uint64), ("hist", ctypes.c_uint64 * HIST_BINS),
+        ("sum", ctypes.c_double), ("bound_sum", ctypes.c_double),
+        ("max", ctypes.c_double), ("max_bound", ctypes.c_double),
+        ("argmax_i", ctypes.c_int64), ("argmax_j", ctypes.c_int64),
+        ("hist_lo", ctypes.c_double), ("hist_hi", ctypes.c_double), ("eps", ctypes.c_double),
+        ("shard", ctypes.c_int32), ("nshards", ctypes.c_int32),
+    ]
+
+
 class FitOptsStruct(ctypes.Structure):
     _fields_ = [
         ("eps", ctypes.c_double), ("m", ctypes.c_int), ("s", ctypes.c_int),
@@ -179,6 +193,9 @@ def _load() -> ctypes.CDLL:
                                            vp]),
         "adagio_distortion_noalloc": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, f64, f64, f64,
                                             ctypes.POINTER(CertStruct), vp]),
+        "adagio_distortion_shard": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, f64, f64, f64, i32,
+                                          i32, i32, ctypes.POINTER(CertPartStruct), vp]),
+        "adagio_cert_merge": (i32, [ctypes.POINTER(CertPartStruct), i32, ctypes.POINTER(CertStruct)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -203,7 +220,18 @@ def exported_symbols() -> list[str]:
                         "adagio_mlp_save", "adagio_mlp_load", "adagio_fit_batched",
                         "adagio_last_batch_stats", "adagio_set_tile_kernel",
                         "adagio_tile_kernel_for", "adagio_autotune_tiles", "adagio_tune_save",
-                        "adagio_tune_load") if hasattr(LIB, n)]
+                        "adagio_tune_load", "adagio_distortion_shard", "adagio_cert_merge")
+            if hasattr(LIB, n)]
+
+
+def cert_merge(parts) -> "Certificate":
+    """adagio_cert_merge of CertPartStruct parts (host only)."""
+    arr = (CertPartStruct * len(parts))(*parts)
+    c = CertStruct()
+    rc = LIB.adagio_cert_merge(arr, len(parts), ctypes.byref(c))
+    if rc != 0:
+        raise AdagioError(rc, "adagio_cert_merge: parts are not shards 0..count-1 of one certificate")
+    return Certificate.from_struct(c)
 
 
 def launch_count() -> int:
@@ -353,6 +381,17 @@ class Context:
                                           eps, hist_lo, hist_hi, precision, ctypes.byref(c),
                                           _stream(x, y)))
         return Certificate.from_struct(c)
+
+    def distortion_shard(self, X, Y, eps: float, shard: int, nshards: int, hist_lo: float = 0.0,
+                         hist_hi: float = 0.0, precision: int = PREC_FP16X3) -> CertPartStruct:
+        x, y = _Arr(X), _Arr(Y)
+        if x.rows != y.rows:
+            raise ValueError("X and Y must have the same number of rows")
+        part = CertPartStruct()
+        self._check(LIB.adagio_distortion_shard(self.h, x.ptr, x.rows, x.cols, x.ld, y.ptr, y.cols,
+                                                y.ld, eps, hist_lo, hist_hi, precision, shard,
+                                                nshards, ctypes.byref(part), _stream(x, y)))
+        return part
 
     def debug_tile_bounds(self, X, Y, tiles: int, precision: int = PREC_FP16X3):
         """(dump[tiles,128,128,4] = (dx2, dy2, ex, ey), tile_ij[tiles,2]) of the fast path."""

@@ -11,6 +11,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <vector>
 #include <cstring>
 #include <exception>
 
@@ -70,6 +71,55 @@ int adagio_distortion(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t
     co.precision = precision;
     return certify(ctx, dX, lx, dY, ly, n, d, m, co, out, st);
     API_END(ctx)
+}
+
+int adagio_distortion_shard(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
+                            const float *Y, int m, int64_t ldy, double eps, double hist_lo,
+                            double hist_hi, int precision, int shard, int nshards,
+                            adagio_cert_part *out, void *stream) {
+    API_BEGIN(ctx)
+    ADAGIO_REQUIRE(X && Y && out, "null pointer argument");
+    ADAGIO_REQUIRE(n >= 2 && n < (1ll << 31) - 256, "n = %lld out of range [2, 2^31)", (long long)n);
+    ADAGIO_REQUIRE(d >= 1 && m >= 1, "d and m must be >= 1 (d=%d, m=%d)", d, m);
+    ADAGIO_REQUIRE(ldx >= d && ldy >= m, "leading dimensions too small");
+    const long long T = pad_rows(n) / kTileRows, ntp = T * (T + 1) / 2;
+    ADAGIO_REQUIRE(nshards >= 1 && nshards <= ntp && shard >= 0 && shard < nshards,
+                   "shard %d of %d: need 0 <= shard < nshards <= %lld (the tiles of n = %lld)", shard,
+                   nshards, ntp, (long long)n);
+    check_precision(precision);
+    check_hist(eps, hist_lo, hist_hi);
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t need = stage_aligned_bytes(ctx, X, n, d, ldx) + stage_aligned_bytes(ctx, Y, n, m, ldy) +
+                  certify_bytes(ctx, n, d, m, precision) + align_up((size_t)ntp * 4, 256) + 1024;
+    ws_reserve(ctx, need);
+    int64_t lx, ly;
+    const float *dX = stage_aligned(ctx, X, n, d, ldx, &lx, st);
+    const float *dY = stage_aligned(ctx, Y, n, m, ldy, &ly, st);
+    CertOptions co;
+    co.eps = eps;
+    co.lo = hist_lo;
+    co.hi = hist_hi;
+    co.precision = precision;
+    co.shard = shard;
+    co.nshards = nshards;
+    return certify(ctx, dX, lx, dY, ly, n, d, m, co, nullptr, st, nullptr, nullptr, out);
+    API_END(ctx)
+}
+
+int adagio_cert_merge(const adagio_cert_part *parts, int count, adagio_cert *out) {
+    if (!parts || !out || count < 1) return ADAGIO_E_INVALID_ARG;
+    std::vector<int> seen(count, 0);
+    for (int q = 0; q < count; ++q) {
+        const adagio_cert_part &p = parts[q];
+        if (p.nshards != count || p.shard < 0 || p.shard >= count || seen[p.shard]++) return ADAGIO_E_INVALID_ARG;
+        if (p.eps != parts[0].eps || p.hist_lo != parts[0].hist_lo || p.hist_hi != parts[0].hist_hi)
+            return ADAGIO_E_INVALID_ARG;
+    }
+    // parts in shard order, so the sums do not depend on the order given
+    std::vector<adagio_cert_part> ordered(count);
+    for (int q = 0; q < count; ++q) ordered[parts[q].shard] = parts[q];
+    cert_from_parts(ordered.data(), count, out);
+    return ADAGIO_OK;
 }
 
 int adagio_debug_tile_bounds(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,

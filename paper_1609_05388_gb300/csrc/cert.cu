@@ -125,6 +125,7 @@ void cert_job_enqueue(adagio_ctx *ctx, CertJob &job, cudaStream_t st, cudaEvent_
     L.dump = opt.dump;
     L.dump_tiles = opt.dump_tiles;
     L.rs_xy = job.rs_xy;
+    if (opt.nshards > 1) shard_range(job.n, opt.shard, opt.nshards, &L.t_begin, &L.t_end);
     if (tc) {
         if (!launch_cert_tc(L, opt.precision, st))
             fail(ADAGIO_E_UNSUPPORTED, "tensor-core certificate does not support n=%lld",
@@ -139,8 +140,81 @@ void cert_job_enqueue(adagio_ctx *ctx, CertJob &job, cudaStream_t st, cudaEvent_
                     job.status, job.stop, job.dres, st);
 }
 
-int cert_job_collect(const CertJob &job, const CertDevResult &h, adagio_cert *out, bool *stopped) {
-    const unsigned long long pairs = (unsigned long long)job.n * (unsigned long long)(job.n - 1) / 2;
+void shard_range(int64_t n, int shard, int nshards, long long *t0, long long *t1) {
+    const long long T = pad_rows(n) / kTileRows, ntp = T * (T + 1) / 2;
+    *t0 = (long long)((__int128)ntp * shard / nshards);
+    *t1 = (long long)((__int128)ntp * (shard + 1) / nshards);
+}
+
+unsigned long long shard_pairs(int64_t n, long long t0, long long t1) {
+    const long long T = pad_rows(n) / kTileRows;
+    auto rows = [&](long long I) {
+        return (unsigned long long)std::max<int64_t>(0, std::min<int64_t>(kTileRows, n - I * kTileRows));
+    };
+    unsigned long long p = 0;
+    long long off = 0;
+    for (long long I = 0; I < T && off < t1; off += T - I, ++I) {
+        // row I holds tiles off .. off + T - I - 1 (J = I .. T - 1)
+        const long long lo = std::max(t0, off), hi = std::min(t1, off + T - I);
+        const unsigned long long rI = rows(I);
+        for (long long t = lo; t < hi; ++t) {
+            const long long J = I + (t - off);
+            p += J == I ? rI * (rI - (rI > 0)) / 2 : rI * rows(J);
+        }
+    }
+    return p;
+}
+
+void cert_from_parts(const adagio_cert_part *parts, int count, adagio_cert *out) {
+    std::memset(out, 0, sizeof(*out));
+    double sum = 0.0, bsum = 0.0, mxb = 0.0;
+    double mx = -1.0;
+    int64_t ai = -1, aj = -1;
+    for (int q = 0; q < count; ++q) {
+        const adagio_cert_part &p = parts[q];
+        out->pairs += p.pairs;
+        out->degenerate += p.degenerate;
+        out->violations += p.violations;
+        out->overflow += p.overflow;
+        out->recomputed += p.recomputed;
+        for (int b = 0; b < kBins; ++b) out->hist[b] += p.hist[b];
+        sum += p.sum;
+        bsum += p.bound_sum;
+        mxb = std::max(mxb, p.max_bound);
+        // the larger distortion; on a tie the lexicographically smaller pair
+        if (p.max >= 0.0 && (p.max > mx || (p.max == mx && (p.argmax_i < ai || (p.argmax_i == ai &&
+                                                                                  p.argmax_j < aj))))) {
+            mx = p.max;
+            ai = p.argmax_i;
+            aj = p.argmax_j;
+        }
+    }
+    const unsigned long long good = out->pairs - out->degenerate;
+    if (mx >= 0.0) {
+        out->max = mx;
+        out->argmax_i = ai;
+        out->argmax_j = aj;
+    } else {
+        out->max = 0.0;
+        out->argmax_i = out->argmax_j = -1;
+    }
+    out->mean = good ? sum / (double)good : 0.0;
+    out->max_err_bound = std::max(mxb, 1e-12);
+    out->mean_err_bound = good ? bsum / (double)good : 0.0;
+    out->hist_lo = parts[0].hist_lo;
+    out->hist_hi = parts[0].hist_hi;
+    out->eps = parts[0].eps;
+}
+
+int cert_job_collect(const CertJob &job, const CertDevResult &h, adagio_cert *out, bool *stopped,
+                     adagio_cert_part *part_out) {
+    const CertOptions &opt = job.opt;
+    unsigned long long pairs = (unsigned long long)job.n * (unsigned long long)(job.n - 1) / 2;
+    if (opt.nshards > 1) {
+        long long t0, t1;
+        shard_range(job.n, opt.shard, opt.nshards, &t0, &t1);
+        pairs = shard_pairs(job.n, t0, t1);
+    }
     if (h.flags & 1u) fail(ADAGIO_E_NONFINITE, "input holds NaN or Inf");
     if (h.status != 0)
         fail(ADAGIO_E_TIMEOUT, "certificate kernel gave up a bounded wait (status %d)", h.status);
@@ -156,35 +230,33 @@ int cert_job_collect(const CertJob &job, const CertDevResult &h, adagio_cert *ou
                  "%llu, degenerate %llu)",
                  h.fast_pairs, h.queued, pairs, h.recomputed, h.degenerate);
     }
-    const CertOptions &opt = job.opt;
-    std::memset(out, 0, sizeof(*out));
-    out->pairs = pairs;
-    out->degenerate = h.degenerate;
-    out->violations = h.violations;
-    out->overflow = h.overflow;
-    out->recomputed = h.recomputed + h.degenerate;
-    std::memcpy(out->hist, h.hist, sizeof(out->hist));
-    const unsigned long long good = pairs - h.degenerate;
-    if (h.max >= 0.0f) {
-        out->max = h.max;
-        out->argmax_i = h.argmax_i;
-        out->argmax_j = h.argmax_j;
-    } else {
-        out->max = 0.0;
-        out->argmax_i = out->argmax_j = -1;
-    }
-    out->mean = good ? h.sum / (double)good : 0.0;
-    out->max_err_bound = std::max((double)h.max_bound, 1e-12);
-    out->mean_err_bound = good ? h.bound_sum / (double)good : 0.0;
-    out->hist_lo = opt.lo;
-    out->hist_hi = opt.hi;
-    out->eps = opt.eps;
+    adagio_cert_part p;
+    std::memset(&p, 0, sizeof(p));
+    p.pairs = pairs;
+    p.degenerate = h.degenerate;
+    p.violations = h.violations;
+    p.overflow = h.overflow;
+    p.recomputed = h.recomputed + h.degenerate;
+    std::memcpy(p.hist, h.hist, sizeof(p.hist));
+    p.sum = h.sum;
+    p.bound_sum = h.bound_sum;
+    p.max = h.max >= 0.0f ? (double)h.max : -1.0;
+    p.max_bound = h.max_bound;
+    p.argmax_i = h.max >= 0.0f ? h.argmax_i : -1;
+    p.argmax_j = h.max >= 0.0f ? h.argmax_j : -1;
+    p.hist_lo = opt.lo;
+    p.hist_hi = opt.hi;
+    p.eps = opt.eps;
+    p.shard = opt.shard;
+    p.nshards = opt.nshards;
+    if (part_out) *part_out = p;
+    if (out) cert_from_parts(&p, 1, out);
     return ADAGIO_OK;
 }
 
 int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_t ldy, int64_t n,
             int d, int m, const CertOptions &opt, adagio_cert *out, cudaStream_t st,
-            bool *stopped, const PrepMat *px_ready) {
+            bool *stopped, const PrepMat *px_ready, adagio_cert_part *part_out) {
     const bool tc = opt.precision != ADAGIO_PREC_FP32;
     const unsigned long long pairs = (unsigned long long)n * (unsigned long long)(n - 1) / 2;
     if (!ctx->qbuf_fixed) cert_ensure_queue(ctx, cert_queue_capacity(pairs));
@@ -237,7 +309,7 @@ int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_
         cs.grid = job.nparts;
         const int64_t T = pad_rows(n) / kTileRows;
         cs.tiles = T * (T + 1) / 2;
-        const int rc = cert_job_collect(job, *h, out, stopped);
+        const int rc = cert_job_collect(job, *h, out, stopped, part_out);
         if (rc == ADAGIO_E_QUEUE_OVERFLOW) {
             const unsigned long long need = h->qlen;
             if (attempt == 0 && !ctx->qbuf_fixed) {

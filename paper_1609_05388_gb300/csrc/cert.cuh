@@ -23,6 +23,9 @@ struct CertLaunch {
     void *dump = nullptr;             // optional per-pair (dx2, dy2, ex, ey) dump
     long long dump_tiles = 0;         // tile pairs to dump (schedule order)
     void *rs_xy = nullptr;            // tensor path: packed per-row statistics (n_pad float4)
+    // tiles [t_begin, t_end) of the row-major upper triangle of 128 x 128
+    // tiles (a shard); t_end < 0: all of them
+    long long t_begin = 0, t_end = -1;
 };
 
 // Device-side result of the finaliser (host copies it back).
@@ -80,14 +83,25 @@ struct CertOptions {
     bool stop_early = false;
     void *dump = nullptr;       // per-pair fast values of the first dump_tiles tile pairs
     long long dump_tiles = 0;
+    int shard = 0, nshards = 1;  // this shard of the tiles (adagio_distortion_shard)
 };
+
+// Tiles [*t0, *t1) of shard `shard` of `nshards` (row-major upper triangle of
+// the 128 x 128 tiles of n points) and the pairs i < j < n they hold.
+void shard_range(int64_t n, int shard, int nshards, long long *t0, long long *t1);
+unsigned long long shard_pairs(int64_t n, long long t0, long long t1);
+// the certificate of one or more shard parts (adagio_cert_merge's arithmetic)
+void cert_from_parts(const adagio_cert_part *parts, int count, adagio_cert *out);
 
 // 128-row block coordinates of the t-th 128 x 128 tile the tile kernel of
 // `precision` visits for n points (host side, for diagnostics).
 void tile_coords(adagio_ctx *ctx, int precision, int64_t n, long long t, int *I, int *J);
+// Writes `out` (the certificate), or with part_out the raw part of the shard
+// that opt selects (out may then be null).
 int certify(adagio_ctx *ctx, const float *X, int64_t ldx, const float *Y, int64_t ldy, int64_t n,
             int d, int m, const CertOptions &opt, adagio_cert *out, cudaStream_t st,
-            bool *stopped = nullptr, const PrepMat *px_ready = nullptr);
+            bool *stopped = nullptr, const PrepMat *px_ready = nullptr,
+            adagio_cert_part *part_out = nullptr);
 size_t certify_bytes(adagio_ctx *ctx, int64_t n, int d, int m, int precision);
 
 // The certificate as three host steps, so that many can be enqueued before
@@ -123,7 +137,8 @@ void cert_job_setup(adagio_ctx *ctx, CertJob &job, int2 *queue, unsigned long lo
 // preps and ev[2] after the tile kernel
 void cert_job_enqueue(adagio_ctx *ctx, CertJob &job, cudaStream_t st, cudaEvent_t *ev = nullptr);
 // 0 = ok; ADAGIO_E_QUEUE_OVERFLOW when the queue was too small (retry with more)
-int cert_job_collect(const CertJob &job, const CertDevResult &h, adagio_cert *out, bool *stopped);
+int cert_job_collect(const CertJob &job, const CertDevResult &h, adagio_cert *out, bool *stopped,
+                     adagio_cert_part *part_out = nullptr);
 unsigned long long cert_queue_capacity(unsigned long long pairs);
 void cert_ensure_queue(adagio_ctx *ctx, unsigned long long cap);
 // tensor path: makes the tile schedule for n points resident (call before capture)

@@ -23,7 +23,7 @@ struct SimtArgs {
     int Kx, Ky;        // padded contraction lengths
     const RowStat *rsx, *rsy;
     int n, T;
-    long long ntp;     // number of tile pairs
+    long long t_begin, ntp;  // tile pairs [t_begin, ntp) of the row-major triangle
     CertConst cc;
     CertPartial *partials;
     int2 *queue;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(NT, 1) cert_simt_kernel(SimtArgs p) {
     float gx[8][8], gy[8][8];
 
     __shared__ int s_stop;
-    for (long long t = blockIdx.x; t < p.ntp; t += gridDim.x) {
+    for (long long t = p.t_begin + blockIdx.x; t < p.ntp; t += gridDim.x) {
         // block-uniform early-exit decision; also orders the previous tile's
         // epilogue reads of the row statistics before they are overwritten
         __syncthreads();
@@ -169,7 +169,8 @@ void launch_cert_simt(const CertLaunch &L, cudaStream_t st) {
     p.rsx = L.x->rs; p.rsy = L.y->rs;
     p.n = (int)L.x->n;
     p.T = (int)(L.x->n_pad / BM);
-    p.ntp = (long long)p.T * (p.T + 1) / 2;
+    p.ntp = L.t_end >= 0 ? L.t_end : (long long)p.T * (p.T + 1) / 2;
+    p.t_begin = L.t_end >= 0 ? L.t_begin : 0;
     p.cc = L.cc;
     p.partials = L.partials;
     p.queue = L.queue; p.qcount = L.qcount; p.qcap = L.qcap;

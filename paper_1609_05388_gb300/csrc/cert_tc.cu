@@ -928,7 +928,10 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     const PrepMat &x = *L.x, &y = *L.y;
     if (!x.hi || !y.hi) return false;
     if (x.n_pad / kTile >= 65536) return false;
-    const TileConfig cfg = tc_config(L.ctx, x.n);
+    TileConfig cfg = tc_config(L.ctx, x.n);
+    // a shard runs the single-CTA kernel over its own tiles
+    const bool sharded = L.t_end >= 0;
+    if (sharded) cfg.variant = 1;
     const bool pair = cfg.variant == 2;
     if (pair && (x.n_pad % (2 * kTile) != 0 || y.n_pad != x.n_pad))
         fail(ADAGIO_E_CUDA, "internal: pair tiles need rows padded to 256 (n_pad %lld)",
@@ -955,7 +958,22 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     a.scale_x = x.scale;
     a.scale_y = y.scale;
     const int T = (int)(x.n_pad / kTile);
-    a.sched = schedule_for(L.ctx, T, cfg, &a.ntp);
+    if (sharded) {
+        // the band order restricted to tiles [t_begin, t_end) of the
+        // row-major triangle; uploaded into the call's workspace
+        std::vector<uint32_t> s;
+        for (uint32_t e : band_schedule(T, cfg.band)) {
+            const long long I = e >> 16, J = e & 0xFFFF;
+            const long long t = I * T - I * (I - 1) / 2 + (J - I);
+            if (t >= L.t_begin && t < L.t_end) s.push_back(e);
+        }
+        uint32_t *dev = ws_array<uint32_t>(L.ctx, std::max<size_t>(s.size(), 1));
+        ADAGIO_CUDA(cudaMemcpy(dev, s.data(), s.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+        a.sched = dev;
+        a.ntp = (long long)s.size();
+    } else {
+        a.sched = schedule_for(L.ctx, T, cfg, &a.ntp);
+    }
     a.n = (int)x.n;
     a.kx_steps = x.Kp16 / kKStep;
     a.ky_steps = y.Kp16 / kKStep;

@@ -280,3 +280,37 @@ def test_full_size_large_sampled(ctx, prec):
     p = g.violations / good
     assert abs(p - p_hat) <= 6 * np.sqrt(max(p * (1 - p), 1e-12) / dl.size) + 1e-6
     assert abs(g.mean - dl.mean()) <= 6 * dl.std() / np.sqrt(dl.size)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_sharded_certificate_matches_whole(ctx, prec):
+    """Shards of the tile triangle, certified one by one and merged, give the
+    whole certificate: counts, histogram, recomputed pairs, maximum and its
+    pair bit for bit, the mean to rounding."""
+    from paper_1609_05388_gb300 import adagio as lib
+    wl = synth.mnist_like(seed=1, n=3001)
+    Y = oracle_embedding(wl.X, 120)
+    X, Yd = torch.from_numpy(wl.X).cuda(), torch.from_numpy(Y).cuda()
+    whole = ctx.distortion(X, Yd, 0.1, precision=prec)
+    for k in (2, 3, 7):
+        parts = [ctx.distortion_shard(X, Yd, 0.1, s, k, precision=prec) for s in range(k)]
+        assert sum(p.pairs for p in parts) == whole.pairs
+        g = lib.cert_merge(parts)
+        assert (g.pairs, g.degenerate, g.violations, g.overflow, g.recomputed) == \
+            (whole.pairs, whole.degenerate, whole.violations, whole.overflow, whole.recomputed)
+        assert np.array_equal(g.hist, whole.hist)
+        assert (g.max, g.argmax_i, g.argmax_j) == (whole.max, whole.argmax_i, whole.argmax_j)
+        assert abs(g.mean - whole.mean) <= 1e-12 * whole.mean
+    with pytest.raises(lib.AdagioError):
+        ctx.distortion_shard(X, Yd, 0.1, 3, 3, precision=prec)
+
+
+def test_shards_of_two_points(ctx):
+    """n = 2: three tiles, one pair; the shards without it are empty."""
+    from paper_1609_05388_gb300 import adagio as lib
+    X = np.array([[0.0, 0.0], [3.0, 4.0]], dtype=np.float32)
+    Y = np.array([[0.0], [6.0]], dtype=np.float32)
+    parts = [ctx.distortion_shard(X, Y, 0.5, s, 3, precision=1) for s in range(3)]
+    assert [p.pairs for p in parts] == [1, 0, 0]
+    g = lib.cert_merge(parts)
+    assert g.pairs == 1 and abs(g.max - 0.2) <= 1e-6 and (g.argmax_i, g.argmax_j) == (0, 1)
