@@ -123,7 +123,10 @@ typedef struct {
  *              galloping (m = 16, 32, 64, ... capped at m_cap) and bisection;
  *              <= 0: fit at the fixed dimension `m`
  *  m           target dimension when eps <= 0
- *  s           number of principal rows; -1 = floor(m/2) (Sec. 4.1)
+ *  s           number of principal rows; -1 = floor(m/2) (Sec. 4.1).  In a
+ *              search, probe r uses min(s, r) of them: s = 0 is the JL-only
+ *              map and s >= m_cap the PCA-only map, the two baselines Table 3
+ *              compares ADAGIO with
  *  seed        seed of the JL matrix and of the randomized PCA start block
  *  jl_dist     ADAGIO_JL_RADEMACHER (default) or ADAGIO_JL_GAUSSIAN
  *  precision   arithmetic of the certificate tiles (ADAGIO_PREC_*)

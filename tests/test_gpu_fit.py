@@ -165,3 +165,29 @@ def test_fit_not_certifiable(ctx):
     X = rng.standard_normal((600, 40)).astype(np.float32)   # isotropic: no reduction
     A, m, s, cert, rc = ctx.fit(X, eps=0.01, m_cap=8, seed=1, precision=0)
     assert rc == lib.E_NOT_CERTIFIABLE and m == 8 and cert.max > 0.01
+
+
+@pytest.mark.parametrize("mode", ["adagio", "pca", "jl"])
+def test_search_modes_agree_with_oracle(ctx, mode):
+    """Table 3's three maps (ADAGIO's split, PCA only, JL only) through the
+    certified search, capped at the full dimension: the GPU and the oracle
+    agree on whether eps is reachable, the returned map's certificate holds,
+    and the dimension is the oracle's in the same mode unless a probe was
+    marginal."""
+    from paper_1609_05388_gb300 import adagio as lib
+    wl = synth.mnist_like(seed=1, n=1200)
+    X = wl.X
+    eps, cap = 0.2, X.shape[1]
+    s = {"adagio": -1, "pca": cap, "jl": 0}[mode]
+    A, m, s_out, cert, rc = ctx.fit(X, eps=eps, m_cap=cap, s=s, seed=5, precision=1)
+    ref = O.search(X.astype(np.float64), eps=eps, m_cap=cap, seed=5, mode=mode)
+    assert (rc == 0) == ref.certified, (mode, rc, ref.r, ref.probes)
+    assert rc in (0, lib.E_NOT_CERTIFIABLE)
+    if rc != 0:
+        return
+    assert cert.max <= eps
+    assert s_out == {"adagio": m // 2, "pca": m, "jl": 0}[mode]
+    if m != ref.r:
+        for rr, mx in ref.probes:
+            if (rr < m) != (rr < ref.r):
+                assert abs(mx - eps) < 0.02, (mode, m, ref.r, ref.probes)
