@@ -57,7 +57,7 @@ extern "C" {
 
 #define ADAGIO_HIST_BINS 64
 
-/* Arithmetic of the all-pairs Gram tiles (the exact recompute of flagged
+/* Arithmetic of the all-pairs Gram tiles (the recompute of flagged
  * pairs is the same in every mode). */
 #define ADAGIO_PREC_FP32     0  /* plain FP32 SIMT Gram tiles                       */
 #define ADAGIO_PREC_FP16X3   1  /* tensor cores: 2-term FP16 split, 3 products,     */
@@ -78,7 +78,8 @@ typedef struct adagio_ctx adagio_ctx;
  *  overflow     pairs outside [hist_lo, hist_hi)
  *  recomputed   pairs whose fast tensor/SIMT value was too close to a bin
  *               edge, to eps, or too ill-conditioned, and were recomputed
- *               exactly from coordinate differences
+ *               from coordinate differences (to within 1e-6, or exactly
+ *               where that still leaves a bin edge or eps within reach)
  *  hist[b]      pairs with hist_lo + b*w <= distortion < hist_lo + (b+1)*w,
  *               w = (hist_hi - hist_lo) / 64
  *  max          largest distortion, at pair (argmax_i, argmax_j), i < j
@@ -413,8 +414,8 @@ int adagio_mlp_load(adagio_ctx *ctx, const char *path);
  * stage).  All times in milliseconds; -1 when not measured.
  *  prep_ms       K0 (centring, split planes) of X and Y
  *  tile_ms       K8, the all-pairs tile kernel
- *  recompute_ms  K9 + K10 (exact recompute of queued pairs, finaliser)
- *  queued        pairs sent to the exact recompute
+ *  recompute_ms  K9 + K10 (recompute of queued pairs, finaliser)
+ *  queued        pairs sent to the recompute
  *  grid          CTAs of the tile kernel; tiles = tile pairs it walked
  */
 typedef struct {

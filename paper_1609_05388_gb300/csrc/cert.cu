@@ -1,5 +1,5 @@
 // Certificate orchestration (Eq. 2, Eq. 3): K0 prep of X and Y, K8 tile
-// kernel (FP32 SIMT or tcgen05 split precision), K9 exact recompute of the
+// kernel (FP32 SIMT or tcgen05 split precision), K9 recompute of the
 // flagged pairs, K10 finaliser, one device->host copy of the result.
 #include "internal.cuh"
 #include "cert.cuh"

@@ -1,5 +1,5 @@
 // Certificate pipeline: launch descriptors shared by the tile kernels, the
-// exact recompute and the finaliser.
+// recompute and the finaliser.
 #pragma once
 
 #include "internal.cuh"

@@ -14,7 +14,7 @@
 // (accumulation rounding).  With a = E_x/dx2 and b = E_y/dy2 the distortion
 // error is at most B = 0.55 rho (a + b) + 2^-22.
 //
-// A pair goes to the exact recompute queue when its bound could change any
+// A pair goes to the recompute queue when its bound could change any
 // reported quantity: B > 1e-6 and an edge of the histogram (or eps) lies
 // within B of delta; or B > 1e-5 (the maximum's tolerance); or the Gram
 // values are too ill-conditioned to bound (a or b > 1/8, dx2 <= 0, dy2 <= 0).

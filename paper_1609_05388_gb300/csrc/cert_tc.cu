@@ -8,7 +8,7 @@
 // three products hi.hi + hi.lo + lo.hi per K chunk, accumulated in FP32 in
 // tensor memory chunk by chunk, and hand the sums to the epilogue
 // (cert_common.cuh), which classifies every pair (Eq. 2), accumulates max /
-// histogram / counts and queues the pairs that need the exact recompute.
+// histogram / counts and queues the pairs that need the recompute.
 //
 // Two variants share the code:
 //   single  one CTA per 128 x 128 tile (tcgen05 cta_group::1, M = N = 128)
@@ -176,9 +176,10 @@ static_assert(sizeof(WarpTotals) <= 64, "per-warp totals exceed their shared-mem
 //   B <= min(1e-5, max(1e-6, distance of delta to the nearest bin edge or eps)),
 // i.e. B is within the maximum's tolerance, and either B <= 1e-6 or no edge
 // and not eps lies within B of delta; every other pair is flagged (bit c of
-// q8, the piece's queue mask) for the exact recompute.  A NaN Gram entry (how the caller marks a column that
-// is not a real pair) fails the test: the pair is flagged and adds nothing to
-// the statistics, and the caller clears its qmask bit.
+// q8, the piece's queue mask) for the recompute.  A NaN Gram entry (how the
+// caller marks a column that is not a real pair) fails the test: the pair is
+// flagged and adds nothing to the statistics, and the caller clears its
+// queue bit.
 template <bool DUMP>
 __device__ __forceinline__ void classify_piece(const float (&gx)[kPiece], const float (&gy)[kPiece],
                                                const float4 ri, const float4 *__restrict__ rsj,

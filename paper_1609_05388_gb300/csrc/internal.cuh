@@ -149,7 +149,7 @@ void *host_stage(adagio_ctx *ctx, size_t bytes);
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
 // Row stride of an internal n x m embedding: a multiple of 4 floats, so the
-// exact recompute reads its rows with 16-byte loads.
+// recompute reads its rows with 16-byte loads.
 inline int emb_ld(int m) { return (int)align_up((size_t)(m < 1 ? 1 : m), 4); }
 
 // Pointer kinds ----------------------------------------------------------------

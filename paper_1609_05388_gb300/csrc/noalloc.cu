@@ -5,7 +5,7 @@
 // cudaMalloc then fails or fragments the pool), or a latency-critical loop
 // that cannot afford the implicit device synchronisation of cudaMalloc and
 // cudaFree.  adagio_distortion_noalloc serves them for small problems: it runs
-// the FP32 certificate (K0 prep, SIMT tiles, exact recompute, finaliser)
+// the FP32 certificate (K0 prep, SIMT tiles, recompute, finaliser)
 // entirely inside a fixed scratch area that is a file-scope __device__ array
 // of this library, instead of the context workspace.
 //

@@ -1,4 +1,5 @@
-// K9 + K10: exact recompute of flagged pairs and the certificate finaliser.
+// K9 + K10: recompute of flagged pairs (two levels, the second exact) and the
+// certificate finaliser.
 //
 // K9 takes every pair the tile kernels could not classify with certainty and
 // recomputes both squared distances from coordinate differences of the
