@@ -57,3 +57,18 @@ def test_default_opts_without_gpu():
     from paper_1609_05388_gb300 import adagio
     o = adagio.Context.default_opts()
     assert o.s == -1 and o.oversample == 32 and o.precision == adagio.PREC_FP16X3
+
+
+def test_binding_refuses_to_load_without_the_library(tmp_path):
+    """No CPU fallback: without libadagio.so the binding raises on import."""
+    import shutil
+    import subprocess
+    import sys
+    pkg = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                       "paper_1609_05388_gb300")
+    copy = tmp_path / "paper_1609_05388_gb300"
+    shutil.copytree(pkg, copy, ignore=shutil.ignore_patterns("*.so", "_build", "__pycache__", "csrc"))
+    r = subprocess.run([sys.executable, "-c", "import paper_1609_05388_gb300.adagio"],
+                       cwd=tmp_path, capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0
+    assert "libadagio.so is missing" in r.stderr
