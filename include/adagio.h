@@ -221,14 +221,16 @@ int adagio_cert_merge(const adagio_cert_part *parts, int count, adagio_cert *out
  * certificate as adagio_distortion with precision ADAGIO_PREC_FP32, using
  * only a fixed 8 MiB scratch array that the library keeps in static device
  * memory (held by every GPU that loads the library until the process exits).
- *  Limits: n <= 1024, d <= 512, m <= 256; larger inputs fail with
+ *  Limits: n <= 1024, d <= 512, m <= 256, on a GPU of any SM count (the
+ *          call uses at most 160 SMs' worth of CTAs); larger inputs fail with
  *          ADAGIO_E_INVALID_ARG.  X and Y must be device pointers; out is host.
  *  The first call on a device looks up the scratch array's device address;
  *  make that first call before capturing any stream on the device.
  *  All calls share the scratch array (it keeps the last call's contents and
  *  each call clears what must start at zero); overlapping calls would race, so
  *  calls are serialised by a host lock and the stream is synchronised before
- *  returning.  No cudaMalloc, cudaFree or allocating library call is made.
+ *  returning, on failure too.  No cudaMalloc, cudaFree or allocating library
+ *  call is made.  adagio_last_cert_stats then reports this call.
  */
 int adagio_distortion_noalloc(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
                               const float *Y, int m, int64_t ldy, double eps, double hist_lo,

@@ -217,7 +217,7 @@ def gallop_bisect(ok, cap: int) -> tuple[int, bool]:
 
 def search(X: np.ndarray, eps: float, m_cap: int, seed: int,
            dist: str = "rademacher", threads: int | None = None,
-           mode: str = "adagio") -> SearchResult:
+           mode: str = "adagio", s_fixed: int = 0) -> SearchResult:
     """Smallest certified target dimension found by ``gallop_bisect``.
 
     ok(r) means the exhaustive certificate of the rank-r map has maximum
@@ -225,17 +225,20 @@ def search(X: np.ndarray, eps: float, m_cap: int, seed: int,
     random), so the answer is the smallest passing probe this procedure meets.
     ``mode`` selects the map: "adagio" (Sec. 4.1 split), "pca" (r principal
     components only) or "jl" (r JL rows only), the three rows of Table 3
-    this library can reproduce without NuMax.
+    this library can reproduce without NuMax; "fixed" is Theorem 2's
+    construction: a PCA part of ``s_fixed`` rows (all r rows when r is
+    smaller) padded with r - s_fixed JL rows on its residual.
     """
     d = X.shape[1]
     cap = min(m_cap, d)
-    pr = pca(X, cap if mode == "pca" else cap // 2)
+    n_pc = {"pca": cap, "fixed": min(s_fixed, cap)}.get(mode, cap // 2)
+    pr = pca(X, n_pc)
     probes = []
     cache = {}
 
     def ok(r):
         if r not in cache:
-            s = {"adagio": r // 2, "pca": r, "jl": 0}[mode]
+            s = {"adagio": r // 2, "pca": r, "jl": 0, "fixed": min(s_fixed, r)}[mode]
             f = fit(X, r, seed, s=s, dist=dist, pca_result=pr)
             Y = embed(f.A, X)
             c = certificate(X, Y, eps, threads=threads)

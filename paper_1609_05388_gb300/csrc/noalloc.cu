@@ -12,7 +12,10 @@
 //  * Scratch: kScratchBytes (8 MiB) of static device memory.  Every GPU that
 //    loads the library holds it until the process exits.
 //  * Limits: n <= 1024 points, d <= 512, m <= 256.  Larger inputs are
-//    rejected with ADAGIO_E_INVALID_ARG before any work is enqueued.
+//    rejected with ADAGIO_E_INVALID_ARG before any work is enqueued.  The
+//    kernels run on at most kMaxCtaSms SMs' worth of CTAs (their per-CTA
+//    partial records live in the scratch too), so the limits hold on a GPU
+//    of any SM count.
 //  * Set-up: the first call on a device looks up the array's device address
 //    with cudaGetSymbolAddress (the host-side name of the array is only a
 //    stand-in, not a device address) with that device current, and caches it.
@@ -21,12 +24,16 @@
 //    contents; every counter, flag and partial that must start at zero is
 //    cleared on the stream at the start of each call.  Calls that overlapped
 //    on the GPU would race on the array, so this entry point serialises its
-//    callers with a host lock and synchronises the stream before returning.
+//    callers with a host lock and synchronises the stream before returning,
+//    also when it fails after enqueuing work.
+//  * The certificate statistics of the call (adagio_last_cert_stats) are
+//    those of the context passed in.
 //  * It calls no cudaMalloc, cudaFree or allocating library routine: the
 //    result is copied into a static host buffer and then into *out.
 #include "internal.cuh"
 #include "cert.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <mutex>
@@ -43,6 +50,9 @@ constexpr int kMaxM = 256;
 constexpr unsigned long long kQueueEntries = (unsigned long long)kMaxN * (kMaxN - 1) / 2;
 constexpr size_t kQueueBytes = kQueueEntries * sizeof(int2);
 constexpr int kMaxDevices = 256;
+// SMs whose CTAs the call uses at most: the FP32 tile kernel runs one CTA per
+// SM and the recompute three, each with a partial record in the scratch
+constexpr int kMaxCtaSms = 160;
 
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
@@ -101,7 +111,7 @@ extern "C" int adagio_distortion_noalloc(adagio_ctx *ctx, const float *X, int64_
         // static scratch, result staging is a static host buffer
         adagio_ctx view;
         view.device = ctx->device;
-        view.num_sms = ctx->num_sms;
+        view.num_sms = std::min(ctx->num_sms, kMaxCtaSms);
         view.qbuf = reinterpret_cast<int2 *>(base);
         view.qbuf_cap = kQueueEntries;
         view.qbuf_fixed = true;
@@ -123,11 +133,16 @@ extern "C" int adagio_distortion_noalloc(adagio_ctx *ctx, const float *X, int64_
         try {
             rc = certify(&view, X, ldx, Y, ldy, n, d, m, co, out, (cudaStream_t)stream);
         } catch (...) {
+            // work may still be queued on the stream: the scratch stays
+            // locked until the GPU is done with it
+            cudaStreamSynchronize((cudaStream_t)stream);
+            cudaGetLastError();
             view.qbuf = nullptr;
             view.host_stage = nullptr;
             view.ws.base = nullptr;
             throw;
         }
+        ctx->last_stats = view.last_stats;
         // the view owns none of these buffers
         view.qbuf = nullptr;
         view.host_stage = nullptr;

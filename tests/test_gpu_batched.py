@@ -8,7 +8,9 @@ its search and maps are checked against the oracle on small instances.
 import numpy as np
 import pytest
 
+from gpu_helpers import assert_cert_parity
 from oracle import adagio as O
+from oracle.certificate import certificate
 from paper_1609_05388_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -161,6 +163,12 @@ def test_batched_workload_64_instances(ctx):
             assert r["status"] == -7 and r["m"] == w.X.shape[1] and r["cert"].max > w.eps
         assert r["cert"].pairs == w.X.shape[0] * (w.X.shape[0] - 1) // 2
     assert certified >= 32
+    # every instance's certificate against the oracle's certificate of the
+    # same (X, Y), all pairs (about 1.7e9 over the batch)
+    for w, r in zip(wls, res):
+        Y = ctx.embed(r["A"], torch.from_numpy(w.X).cuda()).cpu().numpy()
+        o = certificate(w.X, Y, w.eps)
+        assert_cert_parity(r["cert"], o, w.X, Y)
     # a sample of instances against the single fit
     for i in (0, 17, 40, 63):
         A, m, s, c, rc = ctx.fit(dX[i], eps=epss[i], precision=1)

@@ -292,6 +292,8 @@ def test_sharded_certificate_matches_whole(ctx, prec):
     Y = oracle_embedding(wl.X, 120)
     X, Yd = torch.from_numpy(wl.X).cuda(), torch.from_numpy(Y).cuda()
     whole = ctx.distortion(X, Yd, 0.1, precision=prec)
+    o = certificate(wl.X, Y, 0.1)
+    assert_cert_parity(whole, o, wl.X, Y)
     for k in (2, 3, 7):
         parts = [ctx.distortion_shard(X, Yd, 0.1, s, k, precision=prec) for s in range(k)]
         assert sum(p.pairs for p in parts) == whole.pairs
@@ -301,6 +303,7 @@ def test_sharded_certificate_matches_whole(ctx, prec):
         assert np.array_equal(g.hist, whole.hist)
         assert (g.max, g.argmax_i, g.argmax_j) == (whole.max, whole.argmax_i, whole.argmax_j)
         assert abs(g.mean - whole.mean) <= 1e-12 * whole.mean
+        assert_cert_parity(g, o, wl.X, Y)
     with pytest.raises(lib.AdagioError):
         ctx.distortion_shard(X, Yd, 0.1, 3, 3, precision=prec)
 

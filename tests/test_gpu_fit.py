@@ -4,7 +4,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_helpers import PRECISIONS
+from gpu_helpers import PRECISIONS, assert_cert_parity
 from oracle import adagio as O
 from oracle.certificate import certificate
 from paper_1609_05388_gb300 import synth
@@ -167,26 +167,30 @@ def test_fit_not_certifiable(ctx):
     assert rc == lib.E_NOT_CERTIFIABLE and m == 8 and cert.max > 0.01
 
 
-@pytest.mark.parametrize("mode", ["adagio", "pca", "jl"])
+@pytest.mark.parametrize("mode", ["adagio", "pca", "jl", "fixed"])
 def test_search_modes_agree_with_oracle(ctx, mode):
-    """Table 3's three maps (ADAGIO's split, PCA only, JL only) through the
+    """Table 3's three maps (ADAGIO's split, PCA only, JL only) and Theorem 2's
+    construction (a fixed PCA part of 40 rows padded with JL rows) through the
     certified search, capped at the full dimension: the GPU and the oracle
-    agree on whether eps is reachable, the returned map's certificate holds,
-    and the dimension is the oracle's in the same mode unless a probe was
-    marginal."""
+    agree on whether eps is reachable, the returned map's certificate holds
+    and is the oracle's certificate of the same map, and the dimension is the
+    oracle's in the same mode unless a probe was marginal."""
     from paper_1609_05388_gb300 import adagio as lib
     wl = synth.mnist_like(seed=1, n=1200)
     X = wl.X
-    eps, cap = 0.2, X.shape[1]
-    s = {"adagio": -1, "pca": cap, "jl": 0}[mode]
+    eps, cap, s_fixed = 0.2, X.shape[1], 40
+    s = {"adagio": -1, "pca": cap, "jl": 0, "fixed": s_fixed}[mode]
     A, m, s_out, cert, rc = ctx.fit(X, eps=eps, m_cap=cap, s=s, seed=5, precision=1)
-    ref = O.search(X.astype(np.float64), eps=eps, m_cap=cap, seed=5, mode=mode)
+    ref = O.search(X.astype(np.float64), eps=eps, m_cap=cap, seed=5, mode=mode, s_fixed=s_fixed)
     assert (rc == 0) == ref.certified, (mode, rc, ref.r, ref.probes)
     assert rc in (0, lib.E_NOT_CERTIFIABLE)
     if rc != 0:
         return
     assert cert.max <= eps
-    assert s_out == {"adagio": m // 2, "pca": m, "jl": 0}[mode]
+    assert s_out == {"adagio": m // 2, "pca": m, "jl": 0, "fixed": min(s_fixed, m)}[mode]
+    Ah = A.cpu().numpy() if hasattr(A, "cpu") else A
+    Y = ctx.embed(Ah, X)              # the fit certified this embedding, bit for bit
+    assert_cert_parity(cert, certificate(X, Y, eps), X, Y)
     if m != ref.r:
         for rr, mx in ref.probes:
             if (rr < m) != (rr < ref.r):

@@ -56,6 +56,22 @@ def test_gaussian_option_moments():
     assert abs(S.var() - 1.0) < 6 * math.sqrt(2) / 200
 
 
+def test_gaussian_option_matches_the_normal_law():
+    """Kolmogorov-Smirnov distance of the scaled entries to the standard normal
+    CDF (scipy's, an independent implementation), for the whole matrix and for
+    single rows and columns: a wrong Box-Muller transform (a dropped factor of
+    2, sin/cos of the wrong uniform, a missing sqrt) fails it."""
+    stats = pytest.importorskip("scipy.stats")
+    k, d = 100, 400
+    S = O.jl_matrix(12345, k, d, dist="gaussian") * math.sqrt(k)
+    assert stats.kstest(S.ravel(), "norm").pvalue > 1e-3
+    assert stats.kstest(S[0], "norm").pvalue > 1e-4
+    assert stats.kstest(S[:, 7], "norm").pvalue > 1e-4
+    # the two halves of the matrix are uncorrelated (independent counters)
+    r = np.corrcoef(S[: k // 2].ravel(), S[k // 2:].ravel())[0, 1]
+    assert abs(r) < 6 / math.sqrt(S.size / 2)
+
+
 def achlioptas_k(n, eps, beta=1.0):
     return math.ceil((4 + 2 * beta) * math.log(n) / (eps * eps / 2 - eps ** 3 / 3))
 
@@ -175,3 +191,21 @@ def test_table3_ordering_on_mnist_shaped_data():
     dims = {m: O.search(X, eps=0.2, m_cap=784, seed=3, mode=m).r
             for m in ("adagio", "pca", "jl")}
     assert dims["adagio"] < dims["pca"] < dims["jl"]
+
+
+def test_fixed_mode_search_pads_a_fixed_pca_part():
+    """The "fixed" mode (Theorem 2's construction) keeps s_fixed principal rows
+    for every probe r >= s_fixed, padded with r - s_fixed JL rows; for
+    r < s_fixed all r rows are principal.  On data inside a 6-dimensional
+    affine subspace with s_fixed = 6, every probe r >= 6 has zero distortion
+    (the JL rows see only Q(x - y) = 0) and every probe r < 6 projects out a
+    spanned direction (some pair keeps almost none of its length), so the
+    procedure must return exactly r = 6 with s = 6 and k = 0."""
+    rng = np.random.default_rng(41)
+    X = synth.affine_subspace(rng, 300, 40, 6).astype(np.float64)
+    res = O.search(X, eps=0.3, m_cap=40, seed=4, mode="fixed", s_fixed=6)
+    assert res.certified and res.r == 6
+    assert res.cert.max < 1e-6
+    assert [r for r, mx in res.probes if mx <= 0.3] == [r for r, _ in res.probes if r >= 6]
+    for r, mx in res.probes:
+        assert (mx < 1e-6) if r >= 6 else (mx > 0.5)

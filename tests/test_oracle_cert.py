@@ -139,3 +139,31 @@ def test_brute_force_tiny():
             ref[int(v * 10)] += 1
     np.testing.assert_array_equal(c.hist, ref)
     assert c.overflow == over
+
+
+@pytest.mark.parametrize("offset,near", [(-2e-6, 0), (-5e-7, 1), (5e-7, 1), (2e-6, 0)])
+@pytest.mark.parametrize("target", ["edge", "eps"])
+def test_near_edge_counts_pairs_within_1e6_of_an_edge_or_eps(offset, near, target):
+    """One pair with a hand-placed distortion: 1-D points 0 and 1 mapped to 0
+    and 1 + delta have distortion exactly delta (up to FP64 rounding, ~1e-16).
+    near_edge counts it when delta lies within 1e-6 of a bin edge or of eps,
+    and the histogram puts it on the correct side of the edge."""
+    lo, hi, nbins = 0.0, 0.5, 64
+    w = (hi - lo) / nbins                     # 0.0078125: edges at multiples of w
+    if target == "edge":
+        eps = 0.2                              # 0.2 / w = 25.6: eps is not an edge
+        base = 20 * w                          # the lower edge of bin 20
+    else:
+        eps = 0.2
+        base = eps
+    delta = base + offset
+    X = np.array([[0.0], [1.0]])
+    Y = np.array([[0.0], [1.0 + delta]])
+    c = certificate(X, Y, eps=eps, lo=lo, hi=hi, nbins=nbins)
+    assert c.pairs == 1 and c.degenerate == 0
+    assert c.max == pytest.approx(delta, abs=1e-15)
+    assert c.near_edge == near
+    assert int(np.argmax(c.hist)) == int(math.floor(delta / w)) and c.hist.sum() == 1
+    if target == "edge":
+        assert int(np.argmax(c.hist)) == (20 if offset > 0 else 19)
+    assert c.violations == (1 if delta > eps else 0)
