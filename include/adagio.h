@@ -86,7 +86,9 @@ typedef struct adagio_ctx adagio_ctx;
  *  mean         mean distortion over the non-degenerate pairs
  *  max_err_bound   bound on |max - exact max| implied by the per-pair error
  *                  bounds (<= 1e-5 by construction)
- *  mean_err_bound  mean of the per-pair error bounds
+ *  mean_err_bound  bound on |mean - exact mean|: the per-pair error bounds
+ *                  averaged over the non-degenerate pairs (the tensor-core
+ *                  tiles take each tile row's largest bound for its pairs)
  *  Histogram and violation counts are exact except possibly for pairs whose
  *  exact distortion lies within 1e-6 of a bin edge or of eps.
  */
@@ -498,18 +500,19 @@ int adagio_tile_kernel_for(adagio_ctx *ctx, int64_t n);
 
 /*
  * Error-model check of the certificate's fast path.  Runs the certificate of
- * (X, Y) like adagio_distortion and, for the first `tiles` 128 x 128 tile
- * pairs the tile kernel visits, writes per pair (local row a, local column b)
- * four floats at out[((t * 128 + a) * 128 + b) * 4]: the fast squared
+ * (X, Y) like adagio_distortion and, for the 128 x 128 tile pairs number
+ * q * stride (q = 0 .. tiles - 1) in the order the tile kernel visits them,
+ * writes per pair (local row a, local column b) four floats at
+ * out[((q * 128 + a) * 128 + b) * 4]: the fast squared
  * distances dx2 = ||xc_a||^2 + ||xc_b||^2 - 2 xc_a.xc_b and dy2 (likewise)
- * and their error bounds ex, ey; tile_ij[2t], tile_ij[2t+1] receive the tile
+ * and their error bounds ex, ey; tile_ij[2q], tile_ij[2q+1] receive the tile
  * coordinates (I, J), so the pair is (128 I + a, 128 J + b).  Entries of
  * pairs outside i < j < n are written but meaningless.  Arrays are host or
  * device; `out` holds tiles * 65536 floats.  Synchronises `stream`.
  */
 int adagio_debug_tile_bounds(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
                              const float *Y, int m, int64_t ldy, int precision, int64_t tiles,
-                             float *out, int *tile_ij, void *stream);
+                             int64_t stride, float *out, int *tile_ij, void *stream);
 
 /* Number of kernels this library has launched in this process (all contexts,
  * all devices); a difference of two readings counts the launches between. */

@@ -189,8 +189,8 @@ def _load() -> ctypes.CDLL:
         "adagio_features": (i32, [vp, vp, i64, i32, i64, f64, ctypes.POINTER(FitOptsStruct), vp, vp]),
         "adagio_mlp_save": (i32, [vp, ctypes.c_char_p]),
         "adagio_mlp_load": (i32, [vp, ctypes.c_char_p]),
-        "adagio_debug_tile_bounds": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, i32, i64, vp, vp,
-                                           vp]),
+        "adagio_debug_tile_bounds": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, i32, i64, i64, vp,
+                                           vp, vp]),
         "adagio_distortion_noalloc": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, f64, f64, f64,
                                             ctypes.POINTER(CertStruct), vp]),
         "adagio_distortion_shard": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, f64, f64, f64, i32,
@@ -393,13 +393,14 @@ class Context:
                                                 nshards, ctypes.byref(part), _stream(x, y)))
         return part
 
-    def debug_tile_bounds(self, X, Y, tiles: int, precision: int = PREC_FP16X3):
-        """(dump[tiles,128,128,4] = (dx2, dy2, ex, ey), tile_ij[tiles,2]) of the fast path."""
+    def debug_tile_bounds(self, X, Y, tiles: int, precision: int = PREC_FP16X3, stride: int = 1):
+        """(dump[tiles,128,128,4] = (dx2, dy2, ex, ey), tile_ij[tiles,2]) of the fast path,
+        for every stride-th tile pair the tile kernel visits."""
         x, y = _Arr(X), _Arr(Y)
         out = np.empty((tiles, 128, 128, 4), dtype=np.float32)
         ij = np.empty((tiles, 2), dtype=np.int32)
         self._check(LIB.adagio_debug_tile_bounds(self.h, x.ptr, x.rows, x.cols, x.ld, y.ptr, y.cols,
-                                                 y.ld, precision, tiles, out.ctypes.data,
+                                                 y.ld, precision, tiles, stride, out.ctypes.data,
                                                  ij.ctypes.data, _stream(x, y)))
         return out, ij
 

@@ -124,7 +124,7 @@ int adagio_cert_merge(const adagio_cert_part *parts, int count, adagio_cert *out
 
 int adagio_debug_tile_bounds(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
                              const float *Y, int m, int64_t ldy, int precision, int64_t tiles,
-                             float *out, int *tile_ij, void *stream) {
+                             int64_t stride, float *out, int *tile_ij, void *stream) {
     API_BEGIN(ctx)
     ADAGIO_REQUIRE(X && Y && out && tile_ij, "null pointer argument");
     ADAGIO_REQUIRE(n >= 2 && n < (1ll << 31) - 256 && d >= 1 && m >= 1 && ldx >= d && ldy >= m,
@@ -132,7 +132,8 @@ int adagio_debug_tile_bounds(adagio_ctx *ctx, const float *X, int64_t n, int d, 
     check_precision(precision);
     const int T = (int)((n + 127) / 128);
     const long long ntp = (long long)T * (T + 1) / 2;
-    ADAGIO_REQUIRE(tiles >= 1 && tiles <= ntp, "tiles must lie in [1, %lld]", ntp);
+    ADAGIO_REQUIRE(stride >= 1 && tiles >= 1 && (tiles - 1) * stride < ntp,
+                   "need stride >= 1 and tiles >= 1 with (tiles - 1) * stride < %lld", ntp);
     cudaStream_t st = (cudaStream_t)stream;
     const bool out_dev = is_device_ptr(out, ctx->device);
     const size_t dump_bytes = (size_t)tiles * 128 * 128 * 4 * sizeof(float);
@@ -150,6 +151,7 @@ int adagio_debug_tile_bounds(adagio_ctx *ctx, const float *X, int64_t n, int d, 
     co.precision = precision;
     co.dump = dump;
     co.dump_tiles = tiles;
+    co.dump_stride = stride;
     adagio_cert c;
     const int rc = certify(ctx, dX, lx, dY, ly, n, d, m, co, &c, st);
     if (!out_dev) {
@@ -157,7 +159,7 @@ int adagio_debug_tile_bounds(adagio_ctx *ctx, const float *X, int64_t n, int d, 
         ADAGIO_CUDA(cudaStreamSynchronize(st));
     }
     for (long long t = 0; t < tiles; ++t)
-        tile_coords(ctx, precision, n, t, &tile_ij[2 * t], &tile_ij[2 * t + 1]);
+        tile_coords(ctx, precision, n, t * stride, &tile_ij[2 * t], &tile_ij[2 * t + 1]);
     return rc;
     API_END(ctx)
 }

@@ -22,6 +22,7 @@ struct CertLaunch {
     int *status = nullptr;            // device status word (timeouts)
     void *dump = nullptr;             // optional per-pair (dx2, dy2, ex, ey) dump
     long long dump_tiles = 0;         // tile pairs to dump (schedule order)
+    long long dump_stride = 1;        // every dump_stride-th tile pair
     void *rs_xy = nullptr;            // tensor path: packed per-row statistics (n_pad float4)
     // tiles [t_begin, t_end) of the row-major upper triangle of 128 x 128
     // tiles (a shard); t_end < 0: all of them
@@ -83,6 +84,7 @@ struct CertOptions {
     bool stop_early = false;
     void *dump = nullptr;       // per-pair fast values of the first dump_tiles tile pairs
     long long dump_tiles = 0;
+    long long dump_stride = 1;
     int shard = 0, nshards = 1;  // this shard of the tiles (adagio_distortion_shard)
 };
 

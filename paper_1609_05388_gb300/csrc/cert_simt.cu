@@ -31,6 +31,7 @@ struct SimtArgs {
     int *stop_flag;    // non-null: early exit on a certain violation
     float4 *dump;      // optional per-pair (dx2, dy2, ex, ey) of tile pairs t < dump_tiles
     long long dump_tiles;
+    long long dump_stride;  // tile pairs t = q * dump_stride, q < dump_tiles, into slot q
 };
 
 // acc[a][b] += rows(I) . rows(J) over K, for the thread's 8 x 8 block.
@@ -127,14 +128,14 @@ __global__ void __launch_bounds__(NT, 1) cert_simt_kernel(SimtArgs p) {
                 FastPair fp;
                 int cls = PAIR_SKIP;
                 if (i < j && j < p.n) cls = classify_pair(gx[a][b], gy[a][b], xi, sJx[lj], yi, sJy[lj], p.cc, fp);
-                if (p.dump && t < p.dump_tiles) {
+                if (p.dump && t % p.dump_stride == 0 && t / p.dump_stride < p.dump_tiles) {
                     const RowStat xj = sJx[lj], yj = sJy[lj];
                     float4 v;
                     v.x = (xi.n2 + xj.n2) - 2.0f * gx[a][b];
                     v.y = (yi.n2 + yj.n2) - 2.0f * gy[a][b];
                     v.z = fmaf(xi.q4, xj.q4, fmaf(xi.q1, xj.q1, p.cc.c_r * (xi.n2 + xj.n2)));
                     v.w = fmaf(yi.q4, yj.q4, fmaf(yi.q1, yj.q1, p.cc.c_r * (yi.n2 + yj.n2)));
-                    p.dump[(t * BM + li) * BM + lj] = v;
+                    p.dump[((t / p.dump_stride) * BM + li) * BM + lj] = v;
                 }
                 queue_push(cls == PAIR_QUEUE, i, j, p.queue, p.qcount, p.qcap);
                 if (cls == PAIR_OK) {
@@ -177,6 +178,7 @@ void launch_cert_simt(const CertLaunch &L, cudaStream_t st) {
     p.stop_flag = L.stop_flag;
     p.dump = reinterpret_cast<float4 *>(L.dump);
     p.dump_tiles = L.dump_tiles;
+    p.dump_stride = L.dump_stride > 0 ? L.dump_stride : 1;
     const size_t smem = (size_t)kBins * NT * sizeof(unsigned);
     set_max_dyn_smem((const void *)cert_simt_kernel, (int)smem);
     cert_simt_kernel<<<L.grid, NT, smem, st>>>(p);

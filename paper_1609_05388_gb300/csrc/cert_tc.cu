@@ -49,6 +49,7 @@
 #include "cert.cuh"
 #include "tc_ptx.cuh"
 
+#include <cmath>
 #include <vector>
 
 namespace adagio {
@@ -69,26 +70,36 @@ constexpr uint32_t kTmemCols = kStageCol + 2 * kTile;       // 512
 static_assert(kTmemCols == 512, "TMEM holds 512 columns");
 constexpr int kPiece = 8;                                   // columns classified per step
 constexpr int kPieces = kEpiCols / kPiece;
-constexpr int kHistFlushTiles = 1000;                       // u16 counters: <= 64 per tile
-// per-thread histogram: two 16-bit bin counters per 32-bit word
-constexpr int kHistWords = kBins / 2;
+// Histogram counters in shared memory: 64 bins plus an overflow bin (64),
+// one u32 counter per (bin, tile row), shared by the two epilogue warps of a
+// lane quarter (atomic adds; lane l of a warp always hits bank l).
+constexpr int kHBins = kBins + 1;
+constexpr int kHRows = kTile;
+// Bound coefficient: with s = ex / dx2 + ey / dy2 <= 1/8 the square root of
+// the ratio moves by at most ((1 - s)^(-1/2) - 1) <= 0.5523 s relative; the
+// kernel carries ex, ey pre-multiplied by 0.56 (the row statistics' q4 by
+// sqrt(0.56), the (n2_i + n2_j) coefficients by 0.56).
+constexpr float kBoundCoef = 0.56f;
+constexpr float kCondMax = kBoundCoef * 0.125f;
 
 struct TcArgs {
-    const float4 *rs;          // per row: (|xc|^2, |yc|^2, q4x, q4y)
-    float cx, cy;              // bound coefficients of (n2_i + n2_j) per side
+    const float4 *rs;          // per row: (|xc|^2, |yc|^2, sqrt(0.56) q4x, sqrt(0.56) q4y)
+    float cx, cy;              // 0.56 x bound coefficients of (n2_i + n2_j) per side
     const float *scale_x, *scale_y;
     const uint32_t *sched;     // (I << 16) | J per tile (pair variant: I counts 256-row blocks)
     long long ntp;
     int n, kx_steps, ky_steps;
     uint32_t idesc;
     CertConst cc;
+    int eps_bin;               // standard range: eps is the lower edge of this bin
     CertPartial *partials;     // [gridDim.x * kEpiWarps], one slot per epilogue warp
     int2 *queue;
     unsigned long long *qcount, qcap;
     int *stop_flag;
     int *status;
-    float4 *dump;              // optional: (dx2, dy2, ex, ey) of 128 x 128 tile units u < dump_tiles
-    long long dump_tiles;
+    float4 *dump;              // optional: (dx2, dy2, ex, ey) of 128 x 128 tile units
+    long long dump_tiles;      // u = q * dump_stride, q < dump_tiles, into slot q
+    long long dump_stride;
 };
 
 // Shared-memory layout of one CTA.  The pair variant loads half of the J rows
@@ -101,8 +112,8 @@ struct Layout {
     static constexpr uint32_t kStageBytes = 2 * kAPlane + 2 * kBPlane;
     static constexpr uint32_t kTxBytes = PAIR ? 2 * kStageBytes : kStageBytes;  // per full barrier
     static constexpr uint32_t stages = 0;
-    static constexpr uint32_t hist = kStages * kStageBytes;                  // u32 [32][256]
-    static constexpr uint32_t bars = hist + kHistWords * 32 * kEpiWarps * 4;
+    static constexpr uint32_t hist = kStages * kStageBytes;                  // u32 [65][128]
+    static constexpr uint32_t bars = hist + kHBins * kHRows * 4;
     static constexpr uint32_t cmd = bars + 256;                               // int [16]
     static constexpr uint32_t dec = cmd + 64;                                 // int [4]
     static constexpr uint32_t tmem_ptr = dec + 16;
@@ -112,49 +123,57 @@ struct Layout {
     static_assert(smem <= 232448, "tile kernel exceeds the 227 KB shared-memory limit");
     static_assert(totals % 8 == 0, "per-warp totals need 8-byte alignment");
     static_assert(kStageBytes % 1024 == 0 && kBPlane % 1024 == 0, "stage buffers need 1 KB alignment");
-    static_assert((2 * kStages + 2 * kSlots + 5) * 8 <= 256, "barriers exceed their area");
+    static_assert((2 * kStages + 2 * kSlots + 6) * 8 <= 256, "barriers exceed their area");
 };
 
-// Folds this warp's 32 per-thread counters of every bin into its partial
-// (the bins and their total, part of `pairs`).
-__device__ __forceinline__ void fold_hist(uint32_t *s_hist, int ew, CertPartial *dst) {
+// Folds the CTA's histogram counters into this epilogue warp's partial, once
+// every epilogue warp has finished: warp ew takes bins ew, ew + 8, ...
+// (the overflow bin 64 falls to warp 0).  With the standard range (STD) the
+// violations come from the bins too: eps is the lower edge of bin eps_bin,
+// so delta > eps <=> bin >= eps_bin (up to pairs within rounding of eps,
+// which the exactness band exempts), and the overflow pairs lie above eps.
+template <bool STD>
+__device__ __forceinline__ void fold_hist(const uint32_t *s_hist, int ew, int eps_bin,
+                                          CertPartial *dst) {
     const int lane = threadIdx.x & 31;
-    unsigned long long pairs = 0;
-    for (int w = 0; w < kHistWords; ++w) {
-        uint32_t *c = s_hist + w * (32 * kEpiWarps) + ew * 32 + lane;
-        const uint32_t v = *c;
-        *c = 0;
-        unsigned a = v & 0xFFFFu, b = v >> 16;
-        for (int o = 16; o > 0; o >>= 1) {
-            a += __shfl_xor_sync(0xffffffffu, a, o);
-            b += __shfl_xor_sync(0xffffffffu, b, o);
-        }
-        if (lane == 0) {
-            dst->hist[2 * w] += a;
-            dst->hist[2 * w + 1] += b;
-            pairs += a + b;
-        }
+    unsigned long long pairs = 0, viol = 0, over = 0;
+    for (int b = ew; b < kHBins; b += kEpiWarps) {
+        const uint32_t *c = s_hist + b * kHRows;
+        unsigned long long v = (unsigned long long)c[lane] + c[lane + 32] + c[lane + 64] + c[lane + 96];
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        pairs += v;
+        if (b == kBins) over = v;
+        else dst->hist[b] = v;
+        if (STD && b >= eps_bin) viol += v;
     }
-    if (lane == 0) dst->pairs += pairs;
+    if (lane == 0) {
+        dst->pairs += pairs;
+        dst->overflow = over;
+        if (STD) dst->violations = viol;
+    }
     __syncwarp();
 }
 
 struct EpiConst {
     float m2sx, m2sy;      // -2 / scale^2 of the split planes
-    float cx, cy;          // bound coefficients of (n2_i + n2_j) per side
+    float cx, cy;          // 0.56 x bound coefficients of (n2_i + n2_j) per side
     float inv_w, t0, w;    // t = delta * inv_w + t0 = (delta - lo) / w
+    float tlo;             // lowest t at which an edge is real, minus 0.5
     float eps;
 };
 
 // Statistics one epilogue thread keeps over the pairs of one tile row.
 struct RowAcc {
-    float sum, bsum, mxb, mx;
-    int viol, over, certain, arg;
+    float sum;     // sum of the distortions of the pairs counted here
+    float mxb;     // largest error bound among them
+    float mx;      // largest distortion among them (0: possibly none)
+    int mp;        // the piece (8 columns) where mx was first reached
+    int viol;      // delta > eps (ranges where eps is not a bin edge)
 };
 
 // Per-warp running totals of the epilogue, in shared memory (lane 0 owns them).
 struct WarpTotals {
-    unsigned long long violations, overflow, queued;
+    unsigned long long violations, queued;
     double sum, bound_sum;
     float max, max_bound;
     int argmax_i, argmax_j;
@@ -162,71 +181,83 @@ struct WarpTotals {
 
 static_assert(sizeof(WarpTotals) <= 64, "per-warp totals exceed their shared-memory slot");
 
-// Classifies the kPiece pairs (i, j0 + c0 + c) of one tile row from their Gram
-// entries (Eq. 2), without data-dependent branches, so the compiler
-// interleaves the independent pairs.  With p = dx2 dy2 and r = 1/sqrt(p):
+// The fast value of one pair from its Gram entries (Eq. 2), shared by the
+// classification and the argmax search so that both see the same bits.  With
+// p = dx2 dy2 and r = 1/sqrt(p):
 //   delta = |sqrt(dy2 / dx2) - 1| = |dy2 - dx2| / (dx2 + p r)   (no cancellation)
-// The Gram error bounds are ex = q4x_i q4x_j + cx (n2x_i + n2x_j), likewise ey,
-// and the distortion error is at most
-//   B = 0.55 rho (ex / dx2 + ey / dy2) + 1e-6 delta + 1e-9,  rho = dy2 r,
-// written as 0.55 dy2 r^3 (ex dy2 + ey dx2) + ...; the last two terms cover
-// the approximate reciprocal square root and reciprocal.  The fast value is
-// used when the Gram values are well enough conditioned to bound
-// (dx2 > 8 ex and dy2 > 8 ey) and
-//   B <= min(1e-5, max(1e-6, distance of delta to the nearest bin edge or eps)),
+// ex, ey (0.56 x the Gram error bounds, q4_i q4_j + c (n2_i + n2_j)) give
+//   s = (ex dy2 + ey dx2) r^2 = 0.56 (ex / dx2 + ey / dy2),
+//   B = rho s + 1.25e-6 delta + 1e-9,  rho = dy2 r,
+// a bound on the distortion's error when s <= 0.56 / 8 and dx2, dy2 > 0 (the
+// last two terms cover the approximate reciprocal square root and division,
+// and the rounding of t and of the bin edges, about 2e-7 delta).
+// The fast value counts when, in addition,
+//   B <= min(1e-5, max(1e-6, distance of delta to the nearest real bin edge
+//                      (and, off the standard range, to eps)))
 // i.e. B is within the maximum's tolerance, and either B <= 1e-6 or no edge
-// and not eps lies within B of delta; every other pair is flagged (bit c of
-// q8, the piece's queue mask) for the recompute.  A NaN Gram entry (how the
-// caller marks a column that is not a real pair) fails the test: the pair is
-// flagged and adds nothing to the statistics, and the caller clears its
-// queue bit.
-template <bool DUMP>
+// lies within B of delta; every other pair is recomputed.  A NaN Gram entry
+// (how the caller marks a column that is not a real pair) fails the test.
+struct PairVal {
+    float delta, B, t;
+    bool ok;
+};
+
+template <bool STD, bool DUMP>
+__device__ __forceinline__ PairVal pair_value(float gx, float gy, const float4 ri, const float4 rj,
+                                              const EpiConst &k, float4 *dump) {
+    const float sx = __fadd_rn(ri.x, rj.x), sy = __fadd_rn(ri.y, rj.y);
+    const float dx2 = fmaf(k.m2sx, gx, sx), dy2 = fmaf(k.m2sy, gy, sy);
+    const float ex = fmaf(ri.z, rj.z, __fmul_rn(k.cx, sx)), ey = fmaf(ri.w, rj.w, __fmul_rn(k.cy, sy));
+    if (DUMP) *dump = make_float4(dx2, dy2, ex * (1.0f / kBoundCoef), ey * (1.0f / kBoundCoef));
+    const float pp = __fmul_rn(dx2, dy2);
+    const float r = rsqrtf(pp);
+    PairVal v;
+    v.delta = __fdividef(fabsf(__fsub_rn(dy2, dx2)), fmaf(pp, r, dx2));
+    const float rho = __fmul_rn(dy2, r);
+    const float sab = __fmul_rn(fmaf(ex, dy2, __fmul_rn(ey, dx2)), __fmul_rn(r, r));
+    v.B = fmaf(rho, sab, fmaf(1.25e-6f, v.delta, 1e-9f));
+    v.t = STD ? __fmul_rn(v.delta, k.inv_w) : fmaf(v.delta, k.inv_w, k.t0);
+    // distance to the nearest real edge: edges lie at integer t in [tlo + 0.5, 64]
+    const float tc = fminf(fmaxf(v.t, k.tlo), (float)kBins + 0.5f);
+    const float dedge = __fmul_rn(fabsf(__fsub_rn(tc, rintf(tc))), k.w);
+    const float near = STD ? dedge : fminf(dedge, fabsf(__fsub_rn(v.delta, k.eps)));
+    const float lim = fminf(kMaxTol, fmaxf(kExempt, near));
+    v.ok = (fminf(dx2, dy2) > 0.0f) & (sab <= kCondMax) & (v.B <= lim);
+    return v;
+}
+
+// Classifies the kPiece pairs (i, j0 + c0 + c) of one tile row, without
+// data-dependent branches, so the compiler interleaves the independent
+// pairs.  Counted pairs go into their histogram bin (bin 64: outside the
+// range) and the row statistics; the others set bit c of q8 (the piece's
+// queue mask).
+template <bool DUMP, bool STD>
 __device__ __forceinline__ void classify_piece(const float (&gx)[kPiece], const float (&gy)[kPiece],
                                                const float4 ri, const float4 *__restrict__ rsj,
-                                               int c0, const EpiConst &k, uint32_t *hrow, RowAcc &a,
-                                               uint32_t &q8, float4 *dump_row) {
+                                               const EpiConst &k, uint32_t *hrow, RowAcc &a,
+                                               float &pm, uint32_t &q8, float4 *dump_row) {
 #pragma unroll
     for (int c = 0; c < kPiece; ++c) {
         const float4 rj = __ldg(rsj + c);
-        const float sx = ri.x + rj.x, sy = ri.y + rj.y;
-        const float dx2 = fmaf(k.m2sx, gx[c], sx), dy2 = fmaf(k.m2sy, gy[c], sy);
-        const float ex = fmaf(ri.z, rj.z, k.cx * sx), ey = fmaf(ri.w, rj.w, k.cy * sy);
-        if (DUMP) dump_row[c] = make_float4(dx2, dy2, ex, ey);
-        const float pp = dx2 * dy2;
-        const float r = rsqrtf(pp);
-        const float delta = __fdividef(fabsf(dy2 - dx2), fmaf(pp, r, dx2));
-        const float B = fmaf((0.55f * dy2) * (r * r * r), fmaf(ex, dy2, ey * dx2),
-                             fmaf(1e-6f, delta, 1e-9f));
-        const float t = fmaf(delta, k.inv_w, k.t0);
-        // distance to the nearest real edge: edges lie at integer t in [0, 64]
-        const float tc = fminf(fmaxf(t, -0.5f), (float)kBins + 0.5f);
-        const float dedge = fabsf(tc - rintf(tc)) * k.w;
-        const float lim = fminf(kMaxTol, fmaxf(kExempt, fminf(dedge, fabsf(delta - k.eps))));
-        const float cond = fminf(fmaf(-8.0f, ex, dx2), fmaf(-8.0f, ey, dy2));
-        const bool ok = (cond > 0.0f) & (B <= lim);
-        q8 |= ok ? 0u : (1u << c);
-        const bool in_range = (t >= 0.0f) & (t < (float)kBins);
-        const bool binned = ok & in_range;
-        const int bin = (int)t;
-        // pairs not counted in a bin add 0 (to bin 0's word)
-        atomicAdd(hrow + (binned ? (bin >> 1) : 0) * (32 * kEpiWarps),
-                  binned ? (1u << ((bin & 1) << 4)) : 0u);
-        const bool viol = ok & (delta > k.eps);
-        a.over += (ok & !in_range) ? 1 : 0;
-        a.viol += viol ? 1 : 0;
-        a.certain += (viol & (delta - B > k.eps)) ? 1 : 0;
-        const float bok = ok ? B : 0.0f;
-        a.sum += ok ? delta : 0.0f;
-        a.bsum += bok;
-        a.mxb = fmaxf(a.mxb, bok);
-        const bool better = ok & (delta > a.mx);
-        a.mx = better ? delta : a.mx;
-        a.arg = better ? c0 + c : a.arg;
+        const PairVal v = pair_value<STD, DUMP>(gx[c], gy[c], ri, rj, k, DUMP ? dump_row + c : nullptr);
+        q8 |= v.ok ? 0u : (1u << c);
+        int bin;
+        if (STD) {
+            bin = min((int)v.t, kBins);
+        } else {
+            bin = ((v.t >= 0.0f) & (v.t < (float)kBins)) ? (int)v.t : kBins;
+            a.viol += (v.ok & (v.delta > k.eps)) ? 1 : 0;
+        }
+        atomicAdd(hrow + bin * kHRows, v.ok ? 1u : 0u);
+        const float dok = v.ok ? v.delta : 0.0f;
+        a.sum = __fadd_rn(a.sum, dok);
+        pm = fmaxf(pm, dok);
+        a.mxb = fmaxf(a.mxb, v.ok ? v.B : 0.0f);
     }
 }
 
 // ---------------------------------------------------------------- the kernel
-template <bool DUMP, bool PAIR>
+template <bool DUMP, bool PAIR, bool STD>
 __global__ void __launch_bounds__(kThreads, 1)
     cert_tc_kernel(const __grid_constant__ CUtensorMap map_xh, const __grid_constant__ CUtensorMap map_xl,
                    const __grid_constant__ CUtensorMap map_yh, const __grid_constant__ CUtensorMap map_yl,
@@ -258,6 +289,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t bar_done = bar_sempty + 8 * kSlots;        // MMA drain
     const uint32_t bar_dfull = bar_done + 8;                  // [2] pair: decision posted (peer)
     const uint32_t bar_dempty = bar_dfull + 16;               // [2] pair: decision taken (leader)
+    const uint32_t bar_epi = bar_dempty + 16;                 // every epilogue thread is done
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -275,12 +307,13 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(bar_dfull + 8 * q, 1);
             mbar_init(bar_dempty + 8 * q, 1);
         }
+        mbar_init(bar_epi, 32 * kEpiWarps);
         for (int q = 0; q < 16; ++q) s_cmd[q] = 0;
         for (int q = 0; q < 4; ++q) s_dec[q] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
-    for (int e = threadIdx.x; e < kHistWords * 32 * kEpiWarps; e += kThreads) s_hist[e] = 0;
+    for (int e = threadIdx.x; e < kHBins * kHRows; e += kThreads) s_hist[e] = 0;
     if (warp == 1) {
         if (PAIR) {
             // collective with the peer CTA's warp 1: the same columns in both
@@ -524,97 +557,158 @@ __global__ void __launch_bounds__(kThreads, 1)
             k.inv_w = p.cc.inv_w;
             k.t0 = -p.cc.lo * p.cc.inv_w;
             k.w = p.cc.w;
+            // with lo <= 0 the lower edge is no boundary (distortions are >= 0)
+            k.tlo = p.cc.lo_is_floor ? 0.5f : -0.5f;
             k.eps = p.cc.eps;
         }
         WarpTotals *wt = reinterpret_cast<WarpTotals *>(smem + L::totals) + ew;
         if (lane == 0) {
-            wt->violations = wt->overflow = wt->queued = 0;
+            wt->violations = wt->queued = 0;
             wt->sum = wt->bound_sum = 0.0;
             wt->max = -1.0f;
             wt->max_bound = 0.0f;
             wt->argmax_i = wt->argmax_j = 0x7fffffff;
         }
-        uint32_t *hrow = s_hist + ew * 32 + lane;  // bins 2w, 2w+1 at hrow[w * 256]
-        int tiles_since_flush = 0;
+        uint32_t *hrow = s_hist + r;  // bin b of this tile row at hrow[b * kHRows]
         // the tile waiting for (or in) classification
-        bool pend = false;
+        bool pend = false, pend_full = false;
         int pend_pieces = 0;
         long long pend_u = 0;
         int pend_i = 0, pend_j0 = 0;
         float4 pend_ri = make_float4(0.f, 0.f, 0.f, 0.f);
         unsigned long long pend_vmask = 0ull, qmask = 0ull;
-        RowAcc acc{0.0f, 0.0f, 0.0f, -1.0f, 0, 0, 0, 0};
+        RowAcc acc{0.0f, 0.0f, -1.0f, 0, 0};
 
+        // the pending tile's Gram entries of one piece (NaN where not a pair)
+        auto load_piece = [&](int c0, float (&px)[kPiece], float (&py)[kPiece]) {
+            uint32_t ux[kPiece], uy[kPiece];
+            tmem_ld8x2_wait(gx_stage + c0, gy_run + c0, ux, uy);
+            if (pend_full) {
+#pragma unroll
+                for (int c = 0; c < kPiece; ++c) {
+                    px[c] = __uint_as_float(ux[c]);
+                    py[c] = __uint_as_float(uy[c]);
+                }
+            } else {
+                // this piece's valid-pair bits; bit c is a constant after unrolling
+                const uint32_t v8 = (uint32_t)(pend_vmask >> c0) & 0xFFu;
+#pragma unroll
+                for (int c = 0; c < kPiece; ++c) {
+                    const bool valid = (v8 >> c) & 1u;
+                    px[c] = valid ? __uint_as_float(ux[c]) : __int_as_float(0x7fc00000);
+                    py[c] = __uint_as_float(uy[c]);
+                }
+            }
+        };
         // classifies the next 8-column piece of the pending tile
         auto classify_next = [&]() {
             const int c0 = pend_pieces * kPiece;
-            uint32_t ux[kPiece], uy[kPiece];
-            tmem_ld8x2_wait(gx_stage + c0, gy_run + c0, ux, uy);
-            // this piece's valid-pair bits; bit c is a constant after unrolling
-            const uint32_t v8 = (uint32_t)(pend_vmask >> c0) & 0xFFu;
             float px[kPiece], py[kPiece];
-#pragma unroll
-            for (int c = 0; c < kPiece; ++c) {
-                const bool valid = (v8 >> c) & 1u;
-                px[c] = valid ? __uint_as_float(ux[c]) : __int_as_float(0x7fc00000);
-                py[c] = __uint_as_float(uy[c]);
-            }
+            load_piece(c0, px, py);
             uint32_t q8 = 0u;
-            if (DUMP && p.dump && pend_u < p.dump_tiles) {
-                float4 *drow = p.dump + (size_t)pend_u * kTile * kTile + r * kTile + h * kEpiCols + c0;
-                classify_piece<DUMP>(px, py, pend_ri, p.rs + pend_j0 + c0, c0, k, hrow, acc, q8, drow);
+            float pm = -1.0f;
+            if (DUMP && p.dump && pend_u % p.dump_stride == 0 && pend_u / p.dump_stride < p.dump_tiles) {
+                float4 *drow = p.dump + (size_t)(pend_u / p.dump_stride) * kTile * kTile + r * kTile +
+                               h * kEpiCols + c0;
+                classify_piece<DUMP, STD>(px, py, pend_ri, p.rs + pend_j0 + c0, k, hrow, acc, pm, q8, drow);
             } else {
-                classify_piece<false>(px, py, pend_ri, p.rs + pend_j0 + c0, c0, k, hrow, acc, q8,
-                                      nullptr);
+                classify_piece<false, STD>(px, py, pend_ri, p.rs + pend_j0 + c0, k, hrow, acc, pm, q8,
+                                           nullptr);
             }
+            const bool better = pm > acc.mx;
+            acc.mx = better ? pm : acc.mx;
+            acc.mp = better ? pend_pieces : acc.mp;
             qmask |= (unsigned long long)q8 << c0;
             ++pend_pieces;
+        };
+        // the first column at or after piece `from` of this lane's row where a
+        // counted pair has distortion `target` (-1: none); every lane takes
+        // part (the TMEM loads are warp-wide), lane `who` searches
+        auto find_column = [&](int from, float target, int who) -> int {
+            int found = -1;
+            for (int piece = from; piece < kPieces; ++piece) {
+                const int c0 = piece * kPiece;
+                float px[kPiece], py[kPiece];
+                load_piece(c0, px, py);
+#pragma unroll
+                for (int c = 0; c < kPiece; ++c) {
+                    const PairVal v = pair_value<STD, false>(px[c], py[c], pend_ri,
+                                                             __ldg(p.rs + pend_j0 + c0 + c), k, nullptr);
+                    if (found < 0 && v.ok && v.delta == target) found = c0 + c;
+                }
+                found = __shfl_sync(0xffffffffu, found, who);
+                if (found >= 0) break;
+            }
+            return found;
         };
         // queue pushes and warp totals of the fully classified pending tile
         auto finish_pending = [&]() {
             while (pend_pieces < kPieces) classify_next();
             qmask &= pend_vmask;
             int nq = __popcll(qmask);
+            const int nok = __popcll(pend_vmask & ~qmask);
             while (__any_sync(0xffffffffu, qmask != 0ull)) {
                 const bool has = qmask != 0ull;
                 const int c = has ? __ffsll((long long)qmask) - 1 : 0;
                 if (has) qmask &= qmask - 1;
                 queue_push(has, pend_i, pend_j0 + c, p.queue, p.qcount, p.qcap);
             }
-            int aj_t = pend_j0 + acc.arg, ai_t = pend_i;
+            float sum = acc.sum, mxb = acc.mxb, tmax = acc.mx;
+            // >= the sum of the row's bounds
+            float bsum = __fmul_rn((float)nok, acc.mxb);
+            int viol = acc.viol;
             for (int o = 16; o > 0; o >>= 1) {
-                acc.viol += __shfl_xor_sync(0xffffffffu, acc.viol, o);
-                acc.over += __shfl_xor_sync(0xffffffffu, acc.over, o);
-                acc.certain += __shfl_xor_sync(0xffffffffu, acc.certain, o);
+                if (!STD) viol += __shfl_xor_sync(0xffffffffu, viol, o);
                 nq += __shfl_xor_sync(0xffffffffu, nq, o);
-                acc.sum += __shfl_xor_sync(0xffffffffu, acc.sum, o);
-                acc.bsum += __shfl_xor_sync(0xffffffffu, acc.bsum, o);
-                acc.mxb = fmaxf(acc.mxb, __shfl_xor_sync(0xffffffffu, acc.mxb, o));
-                const float om = __shfl_xor_sync(0xffffffffu, acc.mx, o);
-                const int oi = __shfl_xor_sync(0xffffffffu, ai_t, o);
-                const int oj = __shfl_xor_sync(0xffffffffu, aj_t, o);
-                if (better_max(om, oi, oj, acc.mx, ai_t, aj_t)) { acc.mx = om; ai_t = oi; aj_t = oj; }
+                sum += __shfl_xor_sync(0xffffffffu, sum, o);
+                bsum += __shfl_xor_sync(0xffffffffu, bsum, o);
+                mxb = fmaxf(mxb, __shfl_xor_sync(0xffffffffu, mxb, o));
+                tmax = fmaxf(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+            }
+            // the maximum and its pair: searched for only when this tile can
+            // hold the warp's maximum (ties included: the lexicographically
+            // smallest pair wins).  Rows grow with the lane, so the first lane
+            // whose row holds a counted pair at tmax has the smallest i.
+            float wmax = -1.0f;
+            int wi = 0x7fffffff, wj = 0x7fffffff;
+            if (lane == 0) {
+                wmax = wt->max;
+                wi = wt->argmax_i;
+                wj = wt->argmax_j;
+            }
+            wmax = __shfl_sync(0xffffffffu, wmax, 0);
+            if (tmax >= wmax) {
+                unsigned cand = __ballot_sync(0xffffffffu, acc.mx == tmax);
+                while (cand) {
+                    const int l = __ffs(cand) - 1;
+                    cand &= cand - 1;
+                    const int from = __shfl_sync(0xffffffffu, acc.mp, l);
+                    const int c = find_column(from, tmax, l);
+                    if (c >= 0) {
+                        const int fi = __shfl_sync(0xffffffffu, pend_i, l);
+                        const int fj = pend_j0 + c;
+                        wi = __shfl_sync(0xffffffffu, wi, 0);
+                        wj = __shfl_sync(0xffffffffu, wj, 0);
+                        if (lane == 0 && better_max(tmax, fi, fj, wmax, wi, wj)) {
+                            wt->max = tmax;
+                            wt->argmax_i = fi;
+                            wt->argmax_j = fj;
+                        }
+                        break;
+                    }
+                }
             }
             if (lane == 0) {
-                wt->violations += (unsigned)acc.viol;
-                wt->overflow += (unsigned)acc.over;
+                if (!STD) wt->violations += (unsigned)viol;
                 wt->queued += (unsigned)nq;
-                wt->sum += (double)acc.sum;
-                wt->bound_sum += (double)acc.bsum;
-                wt->max_bound = fmaxf(wt->max_bound, acc.mxb);
-                if (acc.mx >= 0.0f && better_max(acc.mx, ai_t, aj_t, wt->max, wt->argmax_i, wt->argmax_j)) {
-                    wt->max = acc.mx;
-                    wt->argmax_i = ai_t;
-                    wt->argmax_j = aj_t;
-                }
-                // a certain violation: delta - B > eps for some pair
-                if (p.stop_flag && acc.certain > 0) atomicExch(p.stop_flag, 1);
+                wt->sum += (double)sum;
+                wt->bound_sum += (double)bsum;
+                wt->max_bound = fmaxf(wt->max_bound, mxb);
+                // a certain violation: a counted pair with delta - B > eps
+                // (its B is at most the maximum's tolerance)
+                if (p.stop_flag && tmax > k.eps + kMaxTol) atomicExch(p.stop_flag, 1);
             }
             pend = false;
-            if (++tiles_since_flush == kHistFlushTiles) {
-                tiles_since_flush = 0;
-                fold_hist(s_hist, ew, mine);
-            }
         };
 
         // the producer's static tile sequence
@@ -708,7 +802,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             // pair of rows: in L1 by the time the next tile's drains begin
             asm volatile("prefetch.global.L1 [%0];" ::"l"(p.rs + pend_j0 + 2 * lane));
             pend_vmask = ~0ull;
-            if (!((Ib < J) && (J * kTile + kTile <= p.n))) {
+            pend_full = (Ib < J) && (J * kTile + kTile <= p.n);
+            if (!pend_full) {
                 // diagonal, below-diagonal or ragged tile: columns that are not
                 // pairs i < j < n get a NaN Gram entry and their queue bit is cleared
                 for (int c = 0; c < kEpiCols; ++c) {
@@ -717,18 +812,19 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
             }
             qmask = 0ull;
-            acc = RowAcc{0.0f, 0.0f, 0.0f, -1.0f, 0, 0, 0, 0};
+            acc = RowAcc{0.0f, 0.0f, -1.0f, 0, 0};
             t += PAIR ? (long long)ncluster_x() : (long long)gridDim.x;
         }
         // the last tile (its sums are complete in TMEM)
         if (ok && pend) finish_pending();
-        // ---- this warp's partial: the rest of its histogram and its totals
-        fold_hist(s_hist, ew, mine);
+        // every epilogue thread is done with the shared histogram counters
+        mbar_arrive(bar_epi);
+        mbar_wait(bar_epi, 0, p.status, 4);
+        // ---- this warp's partial: its share of the histogram and its totals
+        fold_hist<STD>(s_hist, ew, p.eps_bin, mine);
         if (lane == 0) {
-            mine->violations = wt->violations;
+            if (!STD) mine->violations = wt->violations;
             mine->queued = wt->queued;
-            mine->overflow = wt->overflow;
-            mine->pairs += wt->overflow;  // fold_hist added the binned pairs
             mine->degenerate = 0;
             mine->sum = wt->sum;
             mine->bound_sum = wt->bound_sum;
@@ -759,10 +855,13 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (PAIR) cluster_sync();
 }
 
+// (|xc|^2, |yc|^2, sqrt(0.56) q4x, sqrt(0.56) q4y) per row: the q4 terms of
+// the Gram bounds carry the kernel's bound coefficient (rounded up)
 __global__ void pack_row_stats(const RowStat *__restrict__ rx, const RowStat *__restrict__ ry,
                                int64_t n_pad, float4 *__restrict__ out) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (r < n_pad) out[r] = make_float4(rx[r].n2, ry[r].n2, rx[r].q4, ry[r].q4);
+    const float sc = 0.74833152f;  // sqrt(0.56) = 0.748331477..., rounded up
+    if (r < n_pad) out[r] = make_float4(rx[r].n2, ry[r].n2, sc * rx[r].q4, sc * ry[r].q4);
 }
 
 // Band orders of the upper triangle.  Single: bands of `band` tile rows; in a
@@ -800,10 +899,12 @@ static int tile_blocks(int64_t n) { return (int)(pad_rows(n) / kTile); }
 
 // raises the kernels' dynamic shared-memory limit (once per device)
 void cert_tc_init() {
-    set_max_dyn_smem((const void *)cert_tc_kernel<true, false>, (int)Layout<false>::smem);
-    set_max_dyn_smem((const void *)cert_tc_kernel<false, false>, (int)Layout<false>::smem);
-    set_max_dyn_smem((const void *)cert_tc_kernel<true, true>, (int)Layout<true>::smem);
-    set_max_dyn_smem((const void *)cert_tc_kernel<false, true>, (int)Layout<true>::smem);
+    set_max_dyn_smem((const void *)cert_tc_kernel<true, false, true>, (int)Layout<false>::smem);
+    set_max_dyn_smem((const void *)cert_tc_kernel<false, false, true>, (int)Layout<false>::smem);
+    set_max_dyn_smem((const void *)cert_tc_kernel<false, false, false>, (int)Layout<false>::smem);
+    set_max_dyn_smem((const void *)cert_tc_kernel<true, true, true>, (int)Layout<true>::smem);
+    set_max_dyn_smem((const void *)cert_tc_kernel<false, true, true>, (int)Layout<true>::smem);
+    set_max_dyn_smem((const void *)cert_tc_kernel<false, true, false>, (int)Layout<true>::smem);
 }
 
 static cudaLaunchConfig_t pair_config(unsigned ctas, cudaStream_t st, cudaLaunchAttribute *at) {
@@ -829,7 +930,7 @@ static int pair_capacity(adagio_ctx *ctx) {
     cudaLaunchAttribute at[1];
     cudaLaunchConfig_t cfg = pair_config((unsigned)(ctx->num_sms / 2 * 2), nullptr, at);
     int nc = 0;
-    if (cudaOccupancyMaxActiveClusters(&nc, (const void *)cert_tc_kernel<false, true>, &cfg) != cudaSuccess) {
+    if (cudaOccupancyMaxActiveClusters(&nc, (const void *)cert_tc_kernel<false, true, true>, &cfg) != cudaSuccess) {
         cudaGetLastError();
         nc = 0;
     }
@@ -953,9 +1054,10 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
                                                                      (float4 *)L.rs_xy);
     ADAGIO_CHECK_LAUNCH();
     // ex = q4_i q4_j + (c_acc + c_r)(n2_i + n2_j) dominates the split model's
-    // q1 term, because 2 |a| |b| <= |a|^2 + |b|^2
-    a.cx = x.bm.cacc + L.cc.c_r;
-    a.cy = y.bm.cacc + L.cc.c_r;
+    // q1 term, because 2 |a| |b| <= |a|^2 + |b|^2; the kernel takes it times
+    // the bound coefficient 0.56 (q4 scaled by sqrt(0.56) in the row stats)
+    a.cx = kBoundCoef * (x.bm.cacc + L.cc.c_r);
+    a.cy = kBoundCoef * (y.bm.cacc + L.cc.c_r);
     a.scale_x = x.scale;
     a.scale_y = y.scale;
     const int T = (int)(x.n_pad / kTile);
@@ -993,6 +1095,15 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     a.status = L.status;
     a.dump = reinterpret_cast<float4 *>(L.dump);
     a.dump_tiles = L.dump_tiles;
+    a.dump_stride = std::max(1ll, L.dump_stride);
+    // the standard range: lo = 0 and eps on a bin edge (the default [0, 2 eps)
+    // puts it on edge 32); then the violations are read off the histogram
+    const double span = (double)L.cc.hi - (double)L.cc.lo;
+    const double te = ((double)L.cc.eps - (double)L.cc.lo) / span * kBins;
+    const long eb = std::lround(te);
+    const bool std_range = L.cc.lo == 0.0f && eb >= 1 && eb <= kBins && std::fabs(te - (double)eb) <= 1e-6;
+    a.eps_bin = std_range ? (int)eb : kBins;
+    if (L.dump && !std_range) fail(ADAGIO_E_CUDA, "internal: the per-pair dump needs the standard range");
     ADAGIO_CUDA(cudaMemsetAsync(L.partials, 0, sizeof(CertPartial) * L.grid, st));
     cert_tc_init();
     const unsigned ctas = (unsigned)(L.grid / kEpiWarps);
@@ -1000,17 +1111,25 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
         cudaLaunchAttribute at[1];
         const cudaLaunchConfig_t cfg = pair_config(ctas, st, at);
         if (L.dump)
-            ADAGIO_CUDA(cudaLaunchKernelEx(&cfg, cert_tc_kernel<true, true>, mxh, mxl, myh, myl, bxh, bxl,
-                                           byh, byl, a));
+            ADAGIO_CUDA(cudaLaunchKernelEx(&cfg, cert_tc_kernel<true, true, true>, mxh, mxl, myh, myl, bxh,
+                                           bxl, byh, byl, a));
+        else if (std_range)
+            ADAGIO_CUDA(cudaLaunchKernelEx(&cfg, cert_tc_kernel<false, true, true>, mxh, mxl, myh, myl, bxh,
+                                           bxl, byh, byl, a));
         else
-            ADAGIO_CUDA(cudaLaunchKernelEx(&cfg, cert_tc_kernel<false, true>, mxh, mxl, myh, myl, bxh, bxl,
-                                           byh, byl, a));
+            ADAGIO_CUDA(cudaLaunchKernelEx(&cfg, cert_tc_kernel<false, true, false>, mxh, mxl, myh, myl, bxh,
+                                           bxl, byh, byl, a));
     } else {
         const size_t sm = Layout<false>::smem;
         if (L.dump)
-            cert_tc_kernel<true, false><<<ctas, kThreads, sm, st>>>(mxh, mxl, myh, myl, bxh, bxl, byh, byl, a);
+            cert_tc_kernel<true, false, true><<<ctas, kThreads, sm, st>>>(mxh, mxl, myh, myl, bxh, bxl, byh,
+                                                                          byl, a);
+        else if (std_range)
+            cert_tc_kernel<false, false, true><<<ctas, kThreads, sm, st>>>(mxh, mxl, myh, myl, bxh, bxl, byh,
+                                                                           byl, a);
         else
-            cert_tc_kernel<false, false><<<ctas, kThreads, sm, st>>>(mxh, mxl, myh, myl, bxh, bxl, byh, byl, a);
+            cert_tc_kernel<false, false, false><<<ctas, kThreads, sm, st>>>(mxh, mxl, myh, myl, bxh, bxl,
+                                                                            byh, byl, a);
     }
     ADAGIO_CHECK_LAUNCH();
     return true;
