@@ -48,7 +48,7 @@ void cert_init() {
 
 static int partial_slots(adagio_ctx *ctx, int64_t n, int precision) {
     if (precision == ADAGIO_PREC_FP32) return ctx->num_sms;  // 1 CTA / SM (64 KB hist + regs)
-    return cert_tc_ctas(ctx, n) * 8;                          // one slot per epilogue warp
+    return cert_tc_ctas(ctx, n) * cert_tc_slots_per_cta();    // one slot per epilogue warp
 }
 
 static int recompute_grid(adagio_ctx *ctx) { return ctx->num_sms * 3; }  // resident: 3 x 256 threads / SM

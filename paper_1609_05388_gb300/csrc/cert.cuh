@@ -72,6 +72,8 @@ void launch_finalize(const CertPartial *fast, int nfast, const CertPartial *rec,
                      const unsigned long long *qcount, const unsigned *flags, const int *status,
                      const int *stop_flag, CertDevResult *out, cudaStream_t st);
 int cert_tc_ctas(adagio_ctx *ctx, int64_t n);
+// partial records one tensor-core tile CTA writes (one per epilogue warp)
+int cert_tc_slots_per_cta();
 
 // Full certificate of (X, Y) given device pointers.  Fills `out`; returns the
 // status (ADAGIO_OK, ADAGIO_E_NONFINITE, ...).  stop_early: the tile kernels

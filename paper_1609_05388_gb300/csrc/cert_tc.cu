@@ -63,7 +63,7 @@ constexpr int kThreads = 64 + 32 * kEpiWarps;               // producer, MMA, ep
 constexpr int kSlots = 2;                                   // TMEM chunk accumulators
 constexpr int kTile = 128;
 constexpr int kKStep = 64;                                  // fp16 elements per stage row
-constexpr int kEpiCols = 64;                                // columns per epilogue warp
+constexpr int kEpiCols = kTile * 4 / kEpiWarps;             // columns per epilogue warp
 constexpr uint32_t kAPlane = kTile * kKStep * 2;            // 16 KB: 128 rows of one plane
 constexpr uint32_t kStageCol = kSlots * kTile;              // finished Gram sums (gx | gy)
 constexpr uint32_t kTmemCols = kStageCol + 2 * kTile;       // 512
@@ -153,6 +153,19 @@ __device__ __forceinline__ void fold_hist(const uint32_t *s_hist, int ew, int ep
     }
     __syncwarp();
 }
+
+// a0 += b0, a1 += b1 in one packed FP32 instruction (each lane rounded to
+// nearest, the same bits as two scalar adds)
+__device__ __forceinline__ void add2_f32(float &a0, float &a1, uint32_t b0, uint32_t b1) {
+    asm("{\n\t.reg .b64 ra, rb;\n\tmov.b64 ra, {%0, %1};\n\tmov.b64 rb, {%2, %3};\n\t"
+        "add.rn.f32x2 ra, ra, rb;\n\tmov.b64 {%0, %1}, ra;\n\t}"
+        : "+f"(a0), "+f"(a1)
+        : "r"(b0), "r"(b1));
+}
+
+// this warp's kEpiCols TMEM columns into registers, one wait
+__device__ __forceinline__ void tmem_ld_cols(uint32_t ta, uint32_t (&v)[32]) { tmem_ld32_wait(ta, v); }
+__device__ __forceinline__ void tmem_ld_cols(uint32_t ta, uint32_t (&v)[64]) { tmem_ld64_wait(ta, v); }
 
 struct EpiConst {
     float m2sx, m2sy;      // -2 / scale^2 of the split planes
@@ -300,7 +313,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_init(bar_sfull + 8 * s, 1);
             // one arrival per epilogue warp (of both CTAs of a pair)
             // every epilogue thread arrives (a pair: one arrival per warp of both CTAs)
-            mbar_init(bar_sempty + 8 * s, PAIR ? 2 * kEpiWarps : 32 * kEpiWarps);
+            mbar_init(bar_sempty + 8 * s, PAIR ? 2 * kEpiWarps : kEpiWarps);
         }
         mbar_init(bar_done, 1);
         for (int q = 0; q < 2; ++q) {
@@ -714,10 +727,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         // the producer's static tile sequence
         long long t = PAIR ? (long long)cluster_id_x() : (long long)blockIdx.x;
         bool ok = true;
-        while (ok) {
-            float gx[kEpiCols];
+        // this warp's kEpiCols sums into TMEM columns starting at `dst`
+        auto park = [&](const float (&v)[kEpiCols], uint32_t dst) {
 #pragma unroll
-            for (int c = 0; c < kEpiCols; ++c) gx[c] = 0.0f;
+            for (int qd = 0; qd < kEpiCols / 16; ++qd) {
+                uint32_t u[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) u[c] = __float_as_uint(v[qd * 16 + c]);
+                tmem_st16(dst + qd * 16, u);
+            }
+            tmem_wait_st();
+        };
+        while (ok) {
+            // the tile's X sums, then (once they are parked) its Y sums
+            float g[kEpiCols];
+#pragma unroll
+            for (int c = 0; c < kEpiCols; ++c) g[c] = 0.0f;
             bool stop = false;
             for (int ks = 0; ks < ksteps; ++ks) {
                 ok = warp_wait<PAIR>(bar_sfull + 8 * slot, sphase, p.status, 3);
@@ -731,43 +756,32 @@ __global__ void __launch_bounds__(kThreads, 1)
                         break;
                     }
                 }
-                const uint32_t ta = tmem_base + lane_addr + (uint32_t)(slot * kTile + h * kEpiCols);
-                if (ks < p.kx_steps) {
-                    // X chunk: registers, all 64 columns behind one wait
-                    uint32_t v[64];
-                    tmem_ld64_wait(ta, v);
+                if (ks == p.kx_steps) {
+                    // the first Y chunk: the pending tile's classification ends
+                    // here (it reads the staging columns), then the X sums are
+                    // parked there and the registers take the Y sums
+                    if (pend) finish_pending();
+                    park(g, gx_stage);
 #pragma unroll
-                    for (int c = 0; c < kEpiCols; ++c) gx[c] += __uint_as_float(v[c]);
-                } else {
-                    // Y chunk: the running columns (the first Y chunk starts them)
-                    if (ks == p.kx_steps && pend) finish_pending();
-                    const bool first = ks == p.kx_steps;
-#pragma unroll
-                    for (int hh = 0; hh < kEpiCols / 32; ++hh) {
-                        uint32_t v[32], w[32];
-                        if (first) {
-                            tmem_ld16x2_wait(ta + hh * 32, ta + hh * 32 + 16,
-                                             *reinterpret_cast<uint32_t(*)[16]>(v),
-                                             *reinterpret_cast<uint32_t(*)[16]>(v + 16));
-                        } else {
-                            tmem_ld32x2_wait(ta + hh * 32, gy_run + hh * 32, v, w);
-#pragma unroll
-                            for (int c = 0; c < 32; ++c)
-                                v[c] = __float_as_uint(__uint_as_float(v[c]) + __uint_as_float(w[c]));
-                        }
-                        tmem_st16(gy_run + hh * 32, *reinterpret_cast<uint32_t(*)[16]>(v));
-                        tmem_st16(gy_run + hh * 32 + 16, *reinterpret_cast<uint32_t(*)[16]>(v + 16));
-                    }
-                    tmem_wait_st();
+                    for (int c = 0; c < kEpiCols; ++c) g[c] = 0.0f;
                 }
-                // the slot is drained: every thread arrives (a pair: one
-                // arrival per warp on the leader's barrier)
+                // the chunk's Gram partial sums, added in order (round to
+                // nearest; the packed adds round each lane like scalar adds)
+                const uint32_t ta = tmem_base + lane_addr + (uint32_t)(slot * kTile + h * kEpiCols);
+                {
+                    uint32_t v[kEpiCols];
+                    tmem_ld_cols(ta, v);
+#pragma unroll
+                    for (int c = 0; c < kEpiCols; c += 2) add2_f32(g[c], g[c + 1], v[c], v[c + 1]);
+                }
+                // the slot is drained: one arrival per warp (a pair: on the
+                // leader's barrier)
                 tc_fence_before();
+                __syncwarp();
                 if (PAIR) {
-                    __syncwarp();
                     if (lane == 0) mbar_arrive_cluster(sempty_tgt + 8 * slot);
                 } else {
-                    mbar_arrive(bar_sempty + 8 * slot);
+                    if (lane == 0) mbar_arrive(bar_sempty + 8 * slot);
                 }
                 if (++slot == kSlots) {
                     slot = 0;
@@ -777,17 +791,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 if (ks < p.kx_steps && pend && pend_pieces < kPieces) classify_next();
             }
             if (!ok || stop) break;
-            // this tile's Y chunks have started the running columns, so the
-            // previous tile is finished (kx_steps >= 1 always precedes them)
-            // ---- park gx in the staging columns; the tile is now pending
-#pragma unroll
-            for (int qd = 0; qd < kEpiCols / 16; ++qd) {
-                uint32_t vx[16];
-#pragma unroll
-                for (int c = 0; c < 16; ++c) vx[c] = __float_as_uint(gx[qd * 16 + c]);
-                tmem_st16(gx_stage + qd * 16, vx);
-            }
-            tmem_wait_st();
+            // ---- park the Y sums in the running columns; the tile is now pending
+            park(g, gy_run);
             const uint32_t packed = p.sched[t];
             const int I = (int)(packed >> 16), J = (int)(packed & 0xFFFF);
             // this CTA's 128-row block of the tile
@@ -800,7 +805,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             pend_j0 = J * kTile + h * kEpiCols;
             // the 64 column statistics the classification reads, one lane per
             // pair of rows: in L1 by the time the next tile's drains begin
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.rs + pend_j0 + 2 * lane));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.rs + pend_j0 + (lane * kEpiCols) / 32));
             pend_vmask = ~0ull;
             pend_full = (Ib < J) && (J * kTile + kTile <= p.n);
             if (!pend_full) {
@@ -993,6 +998,8 @@ void tc_prepare(adagio_ctx *ctx, int64_t n) {
     long long c;
     (void)schedule_for(ctx, tile_blocks(n), tc_config(ctx, n), &c);
 }
+
+int cert_tc_slots_per_cta() { return kEpiWarps; }
 
 // CTAs of one certificate launch: one per SM (the shared-memory footprint
 // allows one), never more than there are tiles, so that small problems of a
