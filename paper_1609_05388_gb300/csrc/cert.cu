@@ -63,7 +63,7 @@ size_t cert_job_bytes(adagio_ctx *ctx, int64_t n, int m, int precision) {
     size_t b = prep_bytes(n, m, !tc, tc);
     b += align_up(sizeof(CertPartial) * (partial_slots(ctx, n, precision) + recompute_grid(ctx)), 256);
     b += 4 * 256 + align_up(sizeof(CertDevResult), 256);
-    if (tc) b += align_up((size_t)pad_rows(n) * sizeof(float4), 256);
+    if (tc) b += align_up(2 * (size_t)pad_rows(n) * sizeof(float4), 256);
     return b + 1024;
 }
 
@@ -89,7 +89,7 @@ void cert_job_setup(adagio_ctx *ctx, CertJob &job, int2 *queue, unsigned long lo
     job.dres = ws_array<CertDevResult>(ctx, 1);
     const bool tc = job.opt.precision != ADAGIO_PREC_FP32;
     const int64_t n_pad = pad_rows(job.n);
-    job.rs_xy = tc ? ws_array<float4>(ctx, (size_t)n_pad) : nullptr;
+    job.rs_xy = tc ? ws_array<float4>(ctx, 2 * (size_t)n_pad) : nullptr;
     job.queue = queue;
     job.qcap = qcap;
 }

@@ -23,7 +23,7 @@ struct CertLaunch {
     void *dump = nullptr;             // optional per-pair (dx2, dy2, ex, ey) dump
     long long dump_tiles = 0;         // tile pairs to dump (schedule order)
     long long dump_stride = 1;        // every dump_stride-th tile pair
-    void *rs_xy = nullptr;            // tensor path: packed per-row statistics (n_pad float4)
+    void *rs_xy = nullptr;            // tensor path: per-row statistics (2 n_pad float4: by row, by column pair)
     // tiles [t_begin, t_end) of the row-major upper triangle of 128 x 128
     // tiles (a shard); t_end < 0: all of them
     long long t_begin = 0, t_end = -1;

@@ -50,6 +50,7 @@
 #include "tc_ptx.cuh"
 
 #include <cmath>
+#include <type_traits>
 #include <vector>
 
 namespace adagio {
@@ -58,18 +59,19 @@ using namespace tc;
 
 namespace {
 
-constexpr int kEpiWarps = 8;                                // two per TMEM lane quarter
+// Epilogue warps: 8 (two per TMEM lane quarter, 64 columns each) or 12 (three
+// per quarter: 48, 40 and 40 columns)
+constexpr int kEpiWarps = 8;
+static_assert(kEpiWarps == 8 || kEpiWarps == 12, "8 or 12 epilogue warps");
 constexpr int kThreads = 64 + 32 * kEpiWarps;               // producer, MMA, epilogue
 constexpr int kSlots = 2;                                   // TMEM chunk accumulators
 constexpr int kTile = 128;
 constexpr int kKStep = 64;                                  // fp16 elements per stage row
-constexpr int kEpiCols = kTile * 4 / kEpiWarps;             // columns per epilogue warp
 constexpr uint32_t kAPlane = kTile * kKStep * 2;            // 16 KB: 128 rows of one plane
 constexpr uint32_t kStageCol = kSlots * kTile;              // finished Gram sums (gx | gy)
 constexpr uint32_t kTmemCols = kStageCol + 2 * kTile;       // 512
 static_assert(kTmemCols == 512, "TMEM holds 512 columns");
 constexpr int kPiece = 8;                                   // columns classified per step
-constexpr int kPieces = kEpiCols / kPiece;
 // Histogram counters in shared memory: 64 bins plus an overflow bin (64),
 // one u32 counter per (bin, tile row), shared by the two epilogue warps of a
 // lane quarter (atomic adds; lane l of a warp always hits bank l).
@@ -84,6 +86,9 @@ constexpr float kCondMax = kBoundCoef * 0.125f;
 
 struct TcArgs {
     const float4 *rs;          // per row: (|xc|^2, |yc|^2, sqrt(0.56) q4x, sqrt(0.56) q4y)
+    // the same statistics interleaved by column pair (2q, 2q+1): element 2q =
+    // (|xc|^2, |xc|^2, |yc|^2, |yc|^2), element 2q+1 = the two q4x, the two q4y
+    const ulonglong2 *rs2;
     float cx, cy;              // 0.56 x bound coefficients of (n2_i + n2_j) per side
     const float *scale_x, *scale_y;
     const uint32_t *sched;     // (I << 16) | J per tile (pair variant: I counts 256-row blocks)
@@ -163,8 +168,9 @@ __device__ __forceinline__ void add2_f32(float &a0, float &a1, uint32_t b0, uint
         : "r"(b0), "r"(b1));
 }
 
-// this warp's kEpiCols TMEM columns into registers, one wait
-__device__ __forceinline__ void tmem_ld_cols(uint32_t ta, uint32_t (&v)[32]) { tmem_ld32_wait(ta, v); }
+// this warp's TMEM columns into registers, one wait
+__device__ __forceinline__ void tmem_ld_cols(uint32_t ta, uint32_t (&v)[40]) { tmem_ld40_wait(ta, v); }
+__device__ __forceinline__ void tmem_ld_cols(uint32_t ta, uint32_t (&v)[48]) { tmem_ld48_wait(ta, v); }
 __device__ __forceinline__ void tmem_ld_cols(uint32_t ta, uint32_t (&v)[64]) { tmem_ld64_wait(ta, v); }
 
 struct EpiConst {
@@ -239,6 +245,104 @@ __device__ __forceinline__ PairVal pair_value(float gx, float gy, const float4 r
     return v;
 }
 
+// Two FP32 values in one 64-bit register pair, for the packed (f32x2)
+// instructions: each lane is rounded to nearest exactly like the scalar
+// instruction, so a packed evaluation gives the scalar one's bits.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk2(float a, float b) {
+    f2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f2 v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f2 fadd2(f2 a, f2 b) {
+    f2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fsub2(f2 a, f2 b) {
+    f2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ f2 fmul2(f2 a, f2 b) {
+    f2 r;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+// a b + c, one rounding per lane
+__device__ __forceinline__ f2 ffma2(f2 a, f2 b, f2 c) {
+    f2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
+// The row's statistics and the kernel constants, each twice (one per lane of
+// a packed value).
+struct RowPk {
+    f2 n2x, n2y, q4x, q4y;
+};
+struct EpiPk {
+    f2 m2sx, m2sy, cx, cy, inv_w, t0, w, c_rel, c_abs;
+};
+
+// pair_value for the two columns of a column pair: `ja` holds their
+// (|xc|^2, |yc|^2) and `jb` their scaled q4 pairs (the pair-interleaved row
+// statistics).  The same operations as pair_value, two lanes at a time, so
+// both return the same bits for the same pair.
+template <bool STD, bool DUMP>
+__device__ __forceinline__ void pair_value2(f2 gx, f2 gy, const RowPk &ri, const ulonglong2 ja,
+                                            const ulonglong2 jb, const EpiConst &k, const EpiPk &kp,
+                                            PairVal (&v)[2], float4 *dump) {
+    const f2 sx = fadd2(ri.n2x, ja.x), sy = fadd2(ri.n2y, ja.y);
+    const f2 dx2 = ffma2(kp.m2sx, gx, sx), dy2 = ffma2(kp.m2sy, gy, sy);
+    const f2 ex = ffma2(ri.q4x, jb.x, fmul2(kp.cx, sx)), ey = ffma2(ri.q4y, jb.y, fmul2(kp.cy, sy));
+    float dx[2], dy[2];
+    upk2(dx2, dx[0], dx[1]);
+    upk2(dy2, dy[0], dy[1]);
+    if (DUMP) {
+        float e[2], f[2];
+        upk2(ex, e[0], e[1]);
+        upk2(ey, f[0], f[1]);
+        for (int q = 0; q < 2; ++q)
+            dump[q] = make_float4(dx[q], dy[q], e[q] * (1.0f / kBoundCoef), f[q] * (1.0f / kBoundCoef));
+    }
+    const f2 pp = fmul2(dx2, dy2);
+    float pq[2], num[2], den[2];
+    upk2(pp, pq[0], pq[1]);
+    const f2 r = pk2(rsqrtf(pq[0]), rsqrtf(pq[1]));
+    upk2(fsub2(dy2, dx2), num[0], num[1]);
+    upk2(ffma2(pp, r, dx2), den[0], den[1]);
+    const f2 delta = pk2(__fdividef(fabsf(num[0]), den[0]), __fdividef(fabsf(num[1]), den[1]));
+    const f2 rho = fmul2(dy2, r);
+    const f2 sab = fmul2(ffma2(ex, dy2, fmul2(ey, dx2)), fmul2(r, r));
+    const f2 B = ffma2(rho, sab, ffma2(kp.c_rel, delta, kp.c_abs));
+    const f2 t = STD ? fmul2(delta, kp.inv_w) : ffma2(delta, kp.inv_w, kp.t0);
+    float tq[2], sq[2];
+    upk2(delta, v[0].delta, v[1].delta);
+    upk2(B, v[0].B, v[1].B);
+    upk2(t, tq[0], tq[1]);
+    upk2(sab, sq[0], sq[1]);
+    float tc[2], rn[2];
+    for (int q = 0; q < 2; ++q) {
+        v[q].t = tq[q];
+        // distance to the nearest real edge: edges lie at integer t in [tlo + 0.5, 64]
+        tc[q] = fminf(fmaxf(tq[q], k.tlo), (float)kBins + 0.5f);
+        rn[q] = rintf(tc[q]);
+    }
+    float dd[2], de[2];
+    upk2(fsub2(pk2(tc[0], tc[1]), pk2(rn[0], rn[1])), dd[0], dd[1]);
+    upk2(fmul2(pk2(fabsf(dd[0]), fabsf(dd[1])), kp.w), de[0], de[1]);
+    for (int q = 0; q < 2; ++q) {
+        const float near = STD ? de[q] : fminf(de[q], fabsf(__fsub_rn(v[q].delta, k.eps)));
+        const float lim = fminf(kMaxTol, fmaxf(kExempt, near));
+        v[q].ok = (fminf(dx[q], dy[q]) > 0.0f) & (sq[q] <= kCondMax) & (v[q].B <= lim);
+    }
+}
+
 // Classifies the kPiece pairs (i, j0 + c0 + c) of one tile row, without
 // data-dependent branches, so the compiler interleaves the independent
 // pairs.  Counted pairs go into their histogram bin (bin 64: outside the
@@ -246,26 +350,34 @@ __device__ __forceinline__ PairVal pair_value(float gx, float gy, const float4 r
 // queue mask).
 template <bool DUMP, bool STD>
 __device__ __forceinline__ void classify_piece(const float (&gx)[kPiece], const float (&gy)[kPiece],
-                                               const float4 ri, const float4 *__restrict__ rsj,
+                                               const float4 ri, const ulonglong2 *__restrict__ rsj2,
                                                const EpiConst &k, uint32_t *hrow, RowAcc &a,
                                                float &pm, uint32_t &q8, float4 *dump_row) {
+    const RowPk rp{pk2(ri.x, ri.x), pk2(ri.y, ri.y), pk2(ri.z, ri.z), pk2(ri.w, ri.w)};
+    const EpiPk kp{pk2(k.m2sx, k.m2sx), pk2(k.m2sy, k.m2sy), pk2(k.cx, k.cx),   pk2(k.cy, k.cy),
+                   pk2(k.inv_w, k.inv_w), pk2(k.t0, k.t0),   pk2(k.w, k.w),     pk2(1.25e-6f, 1.25e-6f),
+                   pk2(1e-9f, 1e-9f)};
 #pragma unroll
-    for (int c = 0; c < kPiece; ++c) {
-        const float4 rj = __ldg(rsj + c);
-        const PairVal v = pair_value<STD, DUMP>(gx[c], gy[c], ri, rj, k, DUMP ? dump_row + c : nullptr);
-        q8 |= v.ok ? 0u : (1u << c);
-        int bin;
-        if (STD) {
-            bin = min((int)v.t, kBins);
-        } else {
-            bin = ((v.t >= 0.0f) & (v.t < (float)kBins)) ? (int)v.t : kBins;
-            a.viol += (v.ok & (v.delta > k.eps)) ? 1 : 0;
+    for (int c = 0; c < kPiece; c += 2) {
+        PairVal v[2];
+        pair_value2<STD, DUMP>(pk2(gx[c], gx[c + 1]), pk2(gy[c], gy[c + 1]), rp, __ldg(rsj2 + c),
+                               __ldg(rsj2 + c + 1), k, kp, v, DUMP ? dump_row + c : nullptr);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            q8 |= v[q].ok ? 0u : (1u << (c + q));
+            int bin;
+            if (STD) {
+                bin = min((int)v[q].t, kBins);
+            } else {
+                bin = ((v[q].t >= 0.0f) & (v[q].t < (float)kBins)) ? (int)v[q].t : kBins;
+                a.viol += (v[q].ok & (v[q].delta > k.eps)) ? 1 : 0;
+            }
+            atomicAdd(hrow + bin * kHRows, v[q].ok ? 1u : 0u);
+            const float dok = v[q].ok ? v[q].delta : 0.0f;
+            a.sum = __fadd_rn(a.sum, dok);
+            pm = fmaxf(pm, dok);
+            a.mxb = fmaxf(a.mxb, v[q].ok ? v[q].B : 0.0f);
         }
-        atomicAdd(hrow + bin * kHRows, v.ok ? 1u : 0u);
-        const float dok = v.ok ? v.delta : 0.0f;
-        a.sum = __fadd_rn(a.sum, dok);
-        pm = fmaxf(pm, dok);
-        a.mxb = fmaxf(a.mxb, v.ok ? v.B : 0.0f);
     }
 }
 
@@ -497,12 +609,14 @@ __global__ void __launch_bounds__(kThreads, 1)
                     ok = warp_wait<PAIR>(bar_sempty + 8 * slot, sphase ^ 1, p.status, 2);
                     if (!ok) break;
                     tc_fence_after();
-                    if (lane == 0) {
-                        const uint32_t d = tmem_base + (uint32_t)(slot * kTile);
-                        const uint32_t a0 = sbase + L::stages + stage * L::kStageBytes;
-                        const uint64_t ah = sw128_desc(a0), al = sw128_desc(a0 + kAPlane);
-                        const uint64_t bh = sw128_desc(a0 + 2 * kAPlane);
-                        const uint64_t bl = sw128_desc(a0 + 2 * kAPlane + L::kBPlane);
+                    // the descriptors are warp-uniform values; one elected
+                    // lane issues the MMAs and the commits
+                    const uint32_t d = tmem_base + (uint32_t)(slot * kTile);
+                    const uint32_t a0 = sbase + L::stages + stage * L::kStageBytes;
+                    const uint64_t ah = sw128_desc(a0), al = sw128_desc(a0 + kAPlane);
+                    const uint64_t bh = sw128_desc(a0 + 2 * kAPlane);
+                    const uint64_t bl = sw128_desc(a0 + 2 * kAPlane + L::kBPlane);
+                    if (elect_one()) {
 #pragma unroll
                         for (int kk = 0; kk < kKStep / 16; ++kk) {
                             const uint64_t off = (uint64_t)(kk * 32) >> 4;  // 16 elements = 32 bytes
@@ -539,24 +653,29 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
     } else {
         // --------------------------------------------------------- epilogue
-        // Warp e owns TMEM lane quarter (warp % 4), i.e. tile row r, and the
-        // column half h of the tile.  The K chunks of a tile come X first, then
-        // Y.  The X chunks are summed in registers (gx); the Y chunks are summed
-        // in this warp's TMEM running columns (gy, read + add + write back).  At
-        // the end of a tile gx is parked in the TMEM staging columns.  The
+        // Three warps per TMEM lane quarter (warp % 4), i.e. tile row r; warp
+        // part h of the quarter owns columns [col0, col0 + NC) of the tile
+        // (48, 40, 40 columns).  The K chunks of a tile come X first, then Y.
+        // The chunks are summed in registers: the X sums are parked in the
+        // TMEM staging columns at the first Y chunk, the Y sums in the running
+        // columns at the end of the tile, and the tile is then pending.  The
         // classification of a tile is software-pipelined into the next one: it
         // runs piece by piece between the next tile's X-chunk drains, while the
-        // MMA warp computes that tile, and is finished before the next tile's Y
-        // chunks overwrite the running columns.
-        const int ew = warp - 2;                 // 0..7
+        // MMA warp computes that tile, and is finished at the next tile's first
+        // Y chunk, before its X sums overwrite the staging columns.
+        const int ew = warp - 2;                 // 0 .. kEpiWarps - 1
         const int quarter = warp & 3;
-        const int h = ew >> 2;                   // column half
+        const int h = ew >> 2;                   // part of the quarter: 0, 1, 2
+        const int col0 = kEpiWarps == 8 ? 64 * h : (h == 0 ? 0 : (h == 1 ? 48 : 88));
         const int r = quarter * 32 + lane;       // tile row of this thread
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-        const uint32_t gx_stage = tmem_base + lane_addr + kStageCol + (uint32_t)(h * kEpiCols);
+        const uint32_t gx_stage = tmem_base + lane_addr + kStageCol + (uint32_t)col0;
         const uint32_t gy_run = gx_stage + kTile;
         // the slot-drained barrier is the leader's
         const uint32_t sempty_tgt = PAIR ? mapa(bar_sempty, 0) : bar_sempty;
+        auto epilogue = [&](auto ncols) {
+        constexpr int NC = decltype(ncols)::value;
+        constexpr int NP = NC / kPiece;          // pieces of a tile row
         CertPartial *mine = p.partials + (size_t)blockIdx.x * kEpiWarps + ew;
         int slot = 0;
         uint32_t sphase = 0;
@@ -622,10 +741,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             float pm = -1.0f;
             if (DUMP && p.dump && pend_u % p.dump_stride == 0 && pend_u / p.dump_stride < p.dump_tiles) {
                 float4 *drow = p.dump + (size_t)(pend_u / p.dump_stride) * kTile * kTile + r * kTile +
-                               h * kEpiCols + c0;
-                classify_piece<DUMP, STD>(px, py, pend_ri, p.rs + pend_j0 + c0, k, hrow, acc, pm, q8, drow);
+                               col0 + c0;
+                classify_piece<DUMP, STD>(px, py, pend_ri, p.rs2 + pend_j0 + c0, k, hrow, acc, pm, q8, drow);
             } else {
-                classify_piece<false, STD>(px, py, pend_ri, p.rs + pend_j0 + c0, k, hrow, acc, pm, q8,
+                classify_piece<false, STD>(px, py, pend_ri, p.rs2 + pend_j0 + c0, k, hrow, acc, pm, q8,
                                            nullptr);
             }
             const bool better = pm > acc.mx;
@@ -639,7 +758,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         // part (the TMEM loads are warp-wide), lane `who` searches
         auto find_column = [&](int from, float target, int who) -> int {
             int found = -1;
-            for (int piece = from; piece < kPieces; ++piece) {
+            for (int piece = from; piece < NP; ++piece) {
                 const int c0 = piece * kPiece;
                 float px[kPiece], py[kPiece];
                 load_piece(c0, px, py);
@@ -656,7 +775,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         };
         // queue pushes and warp totals of the fully classified pending tile
         auto finish_pending = [&]() {
-            while (pend_pieces < kPieces) classify_next();
+            while (pend_pieces < NP) classify_next();
             qmask &= pend_vmask;
             int nq = __popcll(qmask);
             const int nok = __popcll(pend_vmask & ~qmask);
@@ -724,25 +843,40 @@ __global__ void __launch_bounds__(kThreads, 1)
             pend = false;
         };
 
-        // the producer's static tile sequence
+        // the producer's static tile sequence; its entries are read a tile
+        // ahead, so the row statistic a tile needs at its end is requested at
+        // its start and neither load's latency is exposed
         long long t = PAIR ? (long long)cluster_id_x() : (long long)blockIdx.x;
+        const long long tstep = PAIR ? (long long)ncluster_x() : (long long)gridDim.x;
+        uint32_t nxt_packed = t < p.ntp ? __ldg(p.sched + t) : 0u;
         bool ok = true;
-        // this warp's kEpiCols sums into TMEM columns starting at `dst`
-        auto park = [&](const float (&v)[kEpiCols], uint32_t dst) {
+        // this warp's NC sums into TMEM columns starting at `dst`
+        auto park = [&](const float (&v)[NC], uint32_t dst) {
 #pragma unroll
-            for (int qd = 0; qd < kEpiCols / 16; ++qd) {
+            for (int qd = 0; qd < NC / 16; ++qd) {
                 uint32_t u[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) u[c] = __float_as_uint(v[qd * 16 + c]);
                 tmem_st16(dst + qd * 16, u);
             }
+            if constexpr (NC % 16 != 0) {
+                uint32_t u[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) u[c] = __float_as_uint(v[NC - 8 + c]);
+                tmem_st8(dst + NC - 8, u);
+            }
             tmem_wait_st();
         };
         while (ok) {
+            const uint32_t cur_packed = nxt_packed;
+            nxt_packed = t + tstep < p.ntp ? __ldg(p.sched + t + tstep) : 0u;
+            // this CTA's 128-row block of the tile and the row statistic of this thread's row
+            const int cur_ib = PAIR ? 2 * (int)(cur_packed >> 16) + (int)rank : (int)(cur_packed >> 16);
+            const float4 cur_ri = __ldg(p.rs + cur_ib * kTile + r);
             // the tile's X sums, then (once they are parked) its Y sums
-            float g[kEpiCols];
+            float g[NC];
 #pragma unroll
-            for (int c = 0; c < kEpiCols; ++c) g[c] = 0.0f;
+            for (int c = 0; c < NC; ++c) g[c] = 0.0f;
             bool stop = false;
             for (int ks = 0; ks < ksteps; ++ks) {
                 ok = warp_wait<PAIR>(bar_sfull + 8 * slot, sphase, p.status, 3);
@@ -763,16 +897,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                     if (pend) finish_pending();
                     park(g, gx_stage);
 #pragma unroll
-                    for (int c = 0; c < kEpiCols; ++c) g[c] = 0.0f;
+                    for (int c = 0; c < NC; ++c) g[c] = 0.0f;
                 }
                 // the chunk's Gram partial sums, added in order (round to
                 // nearest; the packed adds round each lane like scalar adds)
-                const uint32_t ta = tmem_base + lane_addr + (uint32_t)(slot * kTile + h * kEpiCols);
+                const uint32_t ta = tmem_base + lane_addr + (uint32_t)(slot * kTile + col0);
                 {
-                    uint32_t v[kEpiCols];
+                    uint32_t v[NC];
                     tmem_ld_cols(ta, v);
 #pragma unroll
-                    for (int c = 0; c < kEpiCols; c += 2) add2_f32(g[c], g[c + 1], v[c], v[c + 1]);
+                    for (int c = 0; c < NC; c += 2) add2_f32(g[c], g[c + 1], v[c], v[c + 1]);
                 }
                 // the slot is drained: one arrival per warp (a pair: on the
                 // leader's barrier)
@@ -787,38 +921,38 @@ __global__ void __launch_bounds__(kThreads, 1)
                     slot = 0;
                     sphase ^= 1;
                 }
-                // one piece of the previous tile between X-chunk drains
-                if (ks < p.kx_steps && pend && pend_pieces < kPieces) classify_next();
+                // the previous tile's pieces, spread evenly over the X chunks
+                while (ks < p.kx_steps && pend && pend_pieces < NP &&
+                       pend_pieces * p.kx_steps < (ks + 1) * NP)
+                    classify_next();
             }
             if (!ok || stop) break;
             // ---- park the Y sums in the running columns; the tile is now pending
             park(g, gy_run);
-            const uint32_t packed = p.sched[t];
-            const int I = (int)(packed >> 16), J = (int)(packed & 0xFFFF);
-            // this CTA's 128-row block of the tile
-            const int Ib = PAIR ? 2 * I + (int)rank : I;
+            const int J = (int)(cur_packed & 0xFFFF);
+            const int Ib = cur_ib;
             pend = true;
             pend_pieces = 0;
             pend_u = PAIR ? 2 * t + (long long)rank : t;
             pend_i = Ib * kTile + r;
-            pend_ri = __ldg(p.rs + pend_i);
-            pend_j0 = J * kTile + h * kEpiCols;
+            pend_ri = cur_ri;
+            pend_j0 = J * kTile + col0;
             // the 64 column statistics the classification reads, one lane per
             // pair of rows: in L1 by the time the next tile's drains begin
-            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.rs + pend_j0 + (lane * kEpiCols) / 32));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.rs + pend_j0 + (lane * NC) / 32));
             pend_vmask = ~0ull;
             pend_full = (Ib < J) && (J * kTile + kTile <= p.n);
             if (!pend_full) {
                 // diagonal, below-diagonal or ragged tile: columns that are not
                 // pairs i < j < n get a NaN Gram entry and their queue bit is cleared
-                for (int c = 0; c < kEpiCols; ++c) {
+                for (int c = 0; c < NC; ++c) {
                     const int j = pend_j0 + c;
                     if (!((pend_i < j) & (j < p.n))) pend_vmask &= ~(1ull << c);
                 }
             }
             qmask = 0ull;
             acc = RowAcc{0.0f, 0.0f, -1.0f, 0, 0};
-            t += PAIR ? (long long)ncluster_x() : (long long)gridDim.x;
+            t += tstep;
         }
         // the last tile (its sums are complete in TMEM)
         if (ok && pend) finish_pending();
@@ -837,6 +971,15 @@ __global__ void __launch_bounds__(kThreads, 1)
             mine->max_bound = wt->max_bound;
             mine->argmax_i = wt->argmax_i;
             mine->argmax_j = wt->argmax_j;
+        }
+            };
+        if constexpr (kEpiWarps == 8) {
+            epilogue(std::integral_constant<int, 64>{});
+        } else {
+            if (h == 0)
+                epilogue(std::integral_constant<int, 48>{});
+            else
+                epilogue(std::integral_constant<int, 40>{});
         }
     }
 
@@ -862,11 +1005,19 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // (|xc|^2, |yc|^2, sqrt(0.56) q4x, sqrt(0.56) q4y) per row: the q4 terms of
 // the Gram bounds carry the kernel's bound coefficient (rounded up)
+// and the same interleaved by column pair into out2 (see TcArgs::rs2)
 __global__ void pack_row_stats(const RowStat *__restrict__ rx, const RowStat *__restrict__ ry,
-                               int64_t n_pad, float4 *__restrict__ out) {
+                               int64_t n_pad, float4 *__restrict__ out, float *__restrict__ out2) {
     const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const float sc = 0.74833152f;  // sqrt(0.56) = 0.748331477..., rounded up
-    if (r < n_pad) out[r] = make_float4(rx[r].n2, ry[r].n2, sc * rx[r].q4, sc * ry[r].q4);
+    if (r >= n_pad) return;
+    const float4 v = make_float4(rx[r].n2, ry[r].n2, sc * rx[r].q4, sc * ry[r].q4);
+    out[r] = v;
+    float *e = out2 + (r & ~1ll) * 4 + (r & 1);  // element 2q starts at float 8q
+    e[0] = v.x;
+    e[2] = v.y;
+    e[4] = v.z;
+    e[6] = v.w;
 }
 
 // Band orders of the upper triangle.  Single: bands of `band` tile rows; in a
@@ -1057,8 +1208,9 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     const CUtensorMap byl = plane_map(y.lo, y.n_pad, y.Kp16, kKStep, brows, bf16);
     TcArgs a;
     a.rs = reinterpret_cast<const float4 *>(L.rs_xy);
-    pack_row_stats<<<(unsigned)ceil_div(x.n_pad, 256), 256, 0, st>>>(x.rs, y.rs, x.n_pad,
-                                                                     (float4 *)L.rs_xy);
+    a.rs2 = reinterpret_cast<const ulonglong2 *>(reinterpret_cast<const float4 *>(L.rs_xy) + x.n_pad);
+    pack_row_stats<<<(unsigned)ceil_div(x.n_pad, 256), 256, 0, st>>>(
+        x.rs, y.rs, x.n_pad, (float4 *)L.rs_xy, (float *)(reinterpret_cast<float4 *>(L.rs_xy) + x.n_pad));
     ADAGIO_CHECK_LAUNCH();
     // ex = q4_i q4_j + (c_acc + c_r)(n2_i + n2_j) dominates the split model's
     // q1 term, because 2 |a| |b| <= |a|^2 + |b|^2; the kernel takes it times
