@@ -40,11 +40,26 @@ EPS = 0.1
 # the certified dimension stays within 1 % of the one at 1e-4 (24 iterations).
 PCA_TOL = 1e-3
 WORKLOAD = "mnist_like 60000x784 (10 clusters, rank-50, ~80% zeros, k/255), eps=0.1"
+# The dimension the learned path returns on this workload (m = 421, s = 210);
+# the reference arm certifies the oracle's map of that dimension.
+M_REF = 421
+# Shards of the certificate whose first one the oracle recomputes to state the
+# certificate's error (about 1.2e8 of the 1.8e9 pairs).
+ORACLE_SHARDS = 15
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one tile-kernel
-# launch on this workload from one ncu capture of the full launch
-# (profiles/cert_tc_mnist.md), or None once the kernel has changed since.
-TRAFFIC_BYTES = 8054875136 + 37042176
+# launch on this workload, from one ncu capture of the full launch
+# (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:cert_tc_kernel
+# -c 1 python -m paper_1609_05388_gb300.profile_cert --n 60000 --m 421 --reps 1),
+# or None once the kernel has changed since.
+TRAFFIC_BYTES = None
+
+
+def workload_config():
+    """The workload both arms measure (the same dictionary in both lines)."""
+    return {"workload": WORKLOAD, "n": 60000, "d": 784, "eps": EPS,
+            "pairs": 60000 * 59999 // 2, "pca_tol": PCA_TOL,
+            "l2": "inputs larger than L2 (X 188 MB fp32; split planes 308 MB)"}
 
 
 def parse():
@@ -54,7 +69,10 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="adagio", choices=["adagio", "reference"])
     p.add_argument("--precision", default="auto")
-    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true",
+                   help="skip the oracle leg (its errors against the oracle and the CPU baseline)")
+    p.add_argument("--no-legs", action="store_true",
+                   help="skip the BF16x3, 200000 x 2048 and 64-instance batched legs")
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-predictor", action="store_true",
                    help="time the plain search as the headline step")
@@ -165,33 +183,139 @@ def fp32_alu_peak_tflops(sm_mhz, sms=152):
     return sms * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-def cpu_baseline(X, eps, m, budget_s=15.0):
-    """The FP64 oracle certificate on a bounded row band of the same workload."""
+def errors_vs_oracle(ctx, lib, X, X_host, A, m, s, prec):
+    """Errors of the returned map and its certificate against the FP64 oracle
+    (and the oracle's rate on the host cores, the CPU baseline).
+
+    * Y = X A^T (Algorithm 1) on 4096 sampled rows against FP64 X A^T;
+    * P = A[:s] (Sec. 2 PCA): orthonormality, and the energy it captures,
+      tr(P C P^T), against the exact top-s eigenvalue sum of C = Xc^T Xc;
+    * the JL part A[s:] against S (I - P^T P) with the oracle's S;
+    * the certificate (Eq. 2, Eq. 3): shard 0 of ORACLE_SHARDS computed by the
+      library against the oracle's certificate of the same tiles."""
+    import torch
     from oracle import adagio as O
-    from oracle.certificate import certificate, default_threads
+    from oracle.certificate import certificate_tiles, default_threads
+    n, d = X_host.shape
+    Y = ctx.embed(A, X)
+    torch.cuda.synchronize()
+    Yh = Y.cpu().numpy()
+    Ah = A.cpu().numpy().astype(np.float64) if hasattr(A, "cpu") else np.asarray(A, np.float64)
+    rows = np.random.default_rng(0).choice(n, 4096, replace=False)
+    ref = X_host[rows].astype(np.float64) @ Ah.T
+    y_err = float(np.max(np.linalg.norm(Yh[rows] - ref, axis=1) /
+                         np.maximum(np.linalg.norm(ref, axis=1), 1e-30)))
+    P = Ah[:s]
+    orth = float(np.abs(P @ P.T - np.eye(s)).max())
+    _, Xc = O.centre(X_host)
+    C = O.covariance(Xc)
+    del Xc
+    theta = np.sort(np.linalg.eigvalsh(C))[::-1]
+    deficit = float(1.0 - np.trace(P @ C @ P.T) / theta[:s].sum())
+    Sm = O.jl_matrix(11, m - s, d)
+    jl_err = float(np.abs(Ah[s:] - Sm @ (np.eye(d) - P.T @ P)).max())
+    part = ctx.distortion_shard(X, Y, EPS, 0, ORACLE_SHARDS, precision=prec)
+    B = 2 * (-(-n // 256))
+    t1 = (B * (B + 1) // 2) // ORACLE_SHARDS
     t0 = time.time()
-    pr = O.pca(X[:8000].astype(np.float64), m // 2)
-    f = O.fit(X[:8000].astype(np.float64), m, 7, pca_result=pr)
-    Y = O.embed(f.A, X)
-    fit_s = time.time() - t0
-    n = X.shape[0]
-    rows, pairs, el = 2, 0, 0.0
-    while True:
-        t0 = time.time()
-        c = certificate(X, Y, eps, rows=(0, rows))
-        el = time.time() - t0
-        pairs = c.pairs
-        if el > budget_s / 4 or rows >= n:
-            break
-        rows *= 4
-    return {"value": pairs / el, "unit": "pairs/s", "cores": default_threads(), "kind": "oracle",
-            "sample": f"FP64 direct-difference certificate of rows [0,{rows}) x all j>i "
-                      f"({pairs} pairs, m={m}); excludes the oracle's exact-PCA fit ({fit_s:.1f} s) "
-                      f"and search"}
+    o = certificate_tiles(X_host, Yh, EPS, 0, t1, blocks=B)
+    el = time.time() - t0
+    g_mean = part.sum / max(part.pairs - part.degenerate, 1)
+    g_hist = np.array(part.hist[:], dtype=np.int64)
+    err = {"embedding_max_rel_row_err": y_err,
+           "pca_orthonormality_max_abs": orth,
+           "pca_captured_energy_rel_deficit": deficit,
+           "jl_rows_max_abs_err": jl_err,
+           "certificate_sample": f"tiles [0,{t1}) of {B * (B + 1) // 2} (shard 0 of {ORACLE_SHARDS}): "
+                                 f"{o.pairs} pairs",
+           "pairs_equal": bool(part.pairs == o.pairs),
+           "hist_abs_diff": int(np.abs(g_hist - o.hist).sum()),
+           "violations_diff": int(part.violations) - o.violations,
+           "overflow_diff": int(part.overflow) - o.overflow,
+           "near_edge_pairs": o.near_edge,
+           "max_abs_err": abs(part.max - o.max),
+           "mean_abs_err": abs(g_mean - o.mean)}
+    cpu = {"value": o.pairs / el, "unit": "pairs/s", "cores": default_threads(), "kind": "oracle",
+           "sample": f"FP64 direct-difference certificate of {o.pairs} pairs (tiles [0,{t1}) of the "
+                     f"returned map, m={m}), {el:.1f} s; excludes the oracle's exact PCA and search"}
+    return err, cpu
+
+
+def cert_leg(ctx, lib, X, Y, eps, precision, reps=2):
+    """Tile-kernel time, recompute time and queue of one certificate of (X, Y)."""
+    ctx.set_timing(True)
+    tile, rec = [], []
+    for _ in range(reps):
+        c = ctx.distortion(X, Y, eps, precision=precision)
+        st = ctx.last_cert_stats()
+        tile.append(st["tile_ms"])
+        rec.append(st["recompute_ms"])
+    ctx.set_timing(False)
+    return c, min(tile), min(rec), st["queued"]
+
+
+def tensor_frac(pairs, d, m, tile_ms, peak):
+    flops = pairs * 2.0 * (d + m)
+    achieved = flops / (tile_ms / 1e3) / 1e12
+    return achieved, achieved / peak
+
+
+def large_leg(ctx, lib, peak, prec):
+    """The 200 000 x 2048 workload (power-law spectrum, 5 % Laplace outliers):
+    one exhaustive certificate (2.0e10 pairs) of a JL map of 300 rows."""
+    import torch
+    from paper_1609_05388_gb300 import synth
+    wl = synth.large(seed=4)
+    n, d, m = wl.X.shape[0], wl.X.shape[1], 300
+    Xd = torch.from_numpy(wl.X).cuda()
+    S = torch.from_numpy(ctx.jl_matrix(9, m, d)).cuda()
+    Y = ctx.embed(S, Xd)
+    c, tile_ms, rec_ms, q = cert_leg(ctx, lib, Xd, Y, 0.1, prec)
+    pairs = n * (n - 1) // 2
+    ach, frac = tensor_frac(pairs, d, m, tile_ms, peak)
+    out = {"workload": "large 200000x2048 (power-law 1/i, 5% Laplace outliers), JL map m=300, eps=0.1",
+           "pairs": pairs, "tile_ms": tile_ms, "recompute_ms": rec_ms, "queued": q,
+           "certificate_pairs_per_s": pairs / ((tile_ms + rec_ms) / 1e3),
+           "tile_pairs_per_s": pairs / (tile_ms / 1e3), "achieved_tflops": ach, "frac": frac,
+           "max": c.max, "violations": c.violations}
+    del Xd, Y
+    torch.cuda.empty_cache()
+    return out
+
+
+def batched_leg(ctx, lib, prec):
+    """The 64-instance ragged workload fitted and certified in one batched call
+    (n log-uniform in [500, 20000], d in {128, ..., 1024}, eps in {0.1, 0.2, 0.3})."""
+    import torch
+    from paper_1609_05388_gb300 import synth
+    wls = synth.batched()
+    dX = [torch.from_numpy(w.X).cuda() for w in wls]
+    epss = [w.eps for w in wls]
+    ctx.fit_batched(dX[:2], epss[:2], precision=prec, graph=True)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = ctx.fit_batched(dX, epss, precision=prec, graph=True)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    pairs = sum(w.X.shape[0] * (w.X.shape[0] - 1) // 2 for w in wls)
+    st = ctx.last_batch_stats()
+    return {"workload": "batched: 64 instances, n log-uniform [500, 20000], d in {128,256,512,1024}, "
+                        "power-law spectra, eps in {0.1,0.2,0.3}",
+            "instances": len(wls), "pairs_per_certificate_set": pairs, "seconds": el,
+            "certified": sum(1 for r in res if r["status"] == 0),
+            "full_certificates": sum(r["full_certs"] for r in res),
+            "probes": sum(r["probes"] for r in res),
+            "rounds": st["rounds"], "graphs": st["graphs"],
+            "certified_pairs_per_s": pairs / el}
 
 
 def run_reference(args, rank, world, pg):
-    """--impl reference: the FP64 CPU oracle as it stands, on the host cores."""
+    """--impl reference: the FP64 CPU oracle as it stands, on the host cores.
+
+    The oracle's own map of the workload (exact PCA of all 60 000 points,
+    Algorithm 1 at m = M_REF, the same JL seed as the GPU fit) is certified
+    by the oracle's direct-difference certificate, one bounded band of rows
+    per step (every pair (i, j), j > i, of those rows)."""
     if rank != 0:
         return
     from paper_1609_05388_gb300 import synth
@@ -199,9 +323,7 @@ def run_reference(args, rank, world, pg):
     from oracle import adagio as O
     wl = synth.mnist_like(seed=1)
     X = wl.X
-    m = 250
-    pr = O.pca(X[:8000].astype(np.float64), m // 2)
-    f = O.fit(X[:8000].astype(np.float64), m, 7, pca_result=pr)
+    f = O.fit(X.astype(np.float64), M_REF, 11)
     Y = O.embed(f.A, X)
     rows = 16
     for _ in range(args.warmup):
@@ -214,14 +336,14 @@ def run_reference(args, rank, world, pg):
         pairs += c.pairs
     tot = sum(times)
     v = pairs / tot
+    sample = (f"FP64 certificate of {rows} rows x all j>i per step of the oracle's map "
+              f"(exact PCA of all {X.shape[0]} points, m={M_REF})")
     line = {"metric": "certified pairs/s", "value": v, "unit": "pairs/s", "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": f"{rows} rows x all j>i per step"},
+            "data": "synthetic", "impl": "reference", "config": workload_config(),
             "cpu_baseline": {"kind": "oracle", "cores": default_threads(), "value": v,
-                             "unit": "pairs/s",
-                             "sample": f"FP64 certificate of {rows} rows x all j>i per step, m={m}"},
+                             "unit": "pairs/s", "sample": sample},
             "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -359,9 +481,24 @@ def main():
            "h2d_bytes_per_step": int(X_host.nbytes), "d2h_bytes_per_step": int(mh * d * 4 + 712),
            "seconds_per_step": e2e_s}
 
-    cpu = None
+    # errors against the FP64 oracle (and the oracle's own rate), then the
+    # other workloads: BF16x3 tiles on this map, the 200 000 x 2048 workload,
+    # the 64-instance batch
+    cpu = err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(X_host, EPS, m)
+        err, cpu = errors_vs_oracle(ctx, lib, X, X_host, A, m, s, prec)
+    legs = None
+    if rank == 0 and not args.no_legs and prec != lib.PREC_FP32:
+        legs = {}
+        cb, bt, br, bq = cert_leg(ctx, lib, X, Y, EPS, lib.PREC_BF16X3)
+        ach, fr = tensor_frac(pairs, d, m, bt, peak)
+        legs["bf16x3_same_map"] = {"tile_ms": bt, "recompute_ms": br, "queued": bq,
+                                   "achieved_tflops": ach, "frac": fr, "max": cb.max,
+                                   "certificate_pairs_per_s": pairs / ((bt + br) / 1e3)}
+        del Y
+        torch.cuda.empty_cache()
+        legs["large_200000x2048"] = large_leg(ctx, lib, peak, prec)
+        legs["batched_64"] = batched_leg(ctx, lib, prec)
 
     if rank == 0:
         line = {
@@ -370,20 +507,18 @@ def main():
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {lib.PREC_FP32: "f32", lib.PREC_FP16X3: "f16x3", lib.PREC_BF16X3: "bf16x3"}[prec],
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "n": n, "d": d, "eps": EPS, "pairs": pairs,
-                       "parallelism": "replicas" if world > 1 else "single-gpu",
-                       "l2": "inputs larger than L2 (X 188 MB fp32; split planes 200 MB)",
-                       "search": ("learned guess verified by the exhaustive certificate, then "
-                                  "doubling and bisection from it on failure" if learned else
-                                  "doubling 16,32,64,... then bisection") +
-                                 "; failing probes stop at the first certain violation",
-                       "tile_config": tile_cfg,
-                       "predictor": os.path.basename(PREDICTOR) if learned else None,
-                       "pca_tol": PCA_TOL},
+            "config": workload_config(),
+            "parallelism": "replicas" if world > 1 else "single-gpu",
+            "search": ("learned guess verified by the exhaustive certificate, then "
+                       "doubling and bisection from it on failure" if learned else
+                       "doubling 16,32,64,... then bisection") +
+                      "; failing probes stop at the first certain violation",
+            "tile_config": tile_cfg,
+            "predictor": os.path.basename(PREDICTOR) if learned else None,
             "time_to_certified_embedding_s": ms / 1e3,
             "result": {"m": m, "s": s, "max": cert.max, "mean": cert.mean,
                        "violations": cert.violations, "recomputed": cert.recomputed,
-                       "max_err_bound": cert.max_err_bound},
+                       "max_err_bound": cert.max_err_bound, "err_vs_oracle": err},
             "fit_stats": fit_stats,
             "certificate_only": {"value": pairs / (tile_ms / 1e3), "unit": "pairs/s (tile kernel)"},
             "plain_search": plain_search,
@@ -393,6 +528,7 @@ def main():
             "clocks": clk,
             "e2e": e2e,
             "cpu_baseline": cpu,
+            "legs": legs,
         }
         print(json.dumps(line), flush=True)
     ctx.close()

@@ -191,8 +191,11 @@ int adagio_distortion(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t
  * take a part: the introduction's list of contributions and the conclusion
  * call the method amenable to distributed implementation).
  * The pairs are grouped in 128 x 128 tiles of the upper triangle, numbered
- * row by row; shard s takes the tiles [T s / nshards, T (s + 1) / nshards) of
- * the T tiles.  The partition depends only on n, so shards computed on
+ * row by row: with B = 2 ceil(n / 256) block rows of 128 points (the last
+ * ones partly or wholly past n), block row I holds the tiles (I, J),
+ * J = I .. B - 1, and tile (I, J) the pairs (i, j), i in block I, j in block
+ * J, i < j < n.  Shard s takes the tiles [T s / nshards, T (s + 1) / nshards)
+ * of the T = B (B + 1) / 2 tiles.  The partition depends only on n, so shards computed on
  * different GPUs (whatever their tuned tile configuration) cover every pair
  * exactly once.  Arguments as adagio_distortion; 0 <= shard < nshards.
  * Writes `out`; synchronises `stream`.  ADAGIO_E_INVALID_ARG on bad sizes or
@@ -459,7 +462,7 @@ int adagio_last_cert_stats(const adagio_ctx *ctx, adagio_cert_stats *out);
  *                                 (SINGLE where such clusters cannot be
  *                                 resident on the device)
  *   band     tile rows (of 128 points) per band of the tile schedule, whose I
- *            tiles stay in L2 while the J tiles stream: 1 to 32, or 0 for the
+ *            tiles stay in L2 while the J tiles stream: 1 to 64, or 0 for the
  *            autotuned value, else 8
  * Returns ADAGIO_E_INVALID_ARG for any other value.  Adopted by the next call.
  */
@@ -472,7 +475,7 @@ int adagio_set_tile_kernel(adagio_ctx *ctx, int variant, int band);
  * Autotuner of the certificate's tile configuration.  Runs the certificate
  * of (X, Y) (host or device arrays, as adagio_distortion takes them) with
  * every candidate: each tile kernel the device runs (single CTA, CTA pair)
- * with schedule bands of 4, 8 and 16 tile rows; times the tile kernel with
+ * with schedule bands of 4, 8, 16, 32 and 64 tile rows; times the tile kernel with
  * CUDA events (one warm-up and three timed runs each, the fastest counts);
  * keeps the fastest on ctx for the size class of n (the number of 128-row
  * tile blocks rounded up to a power of two), where later certificates of

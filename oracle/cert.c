@@ -186,6 +186,131 @@ int oracle_certificate(const double *X, int64_t ldx, const double *Y, int64_t ld
     return 0;
 }
 
+/* One row's pairs of a tile range: (i, j) for j in [jb, je). */
+typedef struct {
+    int64_t i, jb, je;
+} segment_t;
+
+typedef struct {
+    const double *X, *Y;
+    int64_t ldx, ldy;
+    const segment_t *seg;
+    int64_t nseg;
+    int d, m, nbins, tid, nthreads;
+    double eps, lo, hi, edge_tol;
+    oracle_cert_t res;
+} seg_job_t;
+
+static void *seg_worker(void *arg) {
+    seg_job_t *jb = (seg_job_t *)arg;
+    oracle_cert_t *r = &jb->res;
+    memset(r, 0, sizeof(*r));
+    r->argmax_i = r->argmax_j = -1;
+    for (int64_t q = jb->tid; q < jb->nseg; q += jb->nthreads) {
+        const segment_t *sg = &jb->seg[q];
+        const double *xi = jb->X + sg->i * jb->ldx;
+        const double *yi = jb->Y + sg->i * jb->ldy;
+        for (int64_t j = sg->jb; j < sg->je; ++j) {
+            double dx2 = sqdist(xi, jb->X + j * jb->ldx, jb->d);
+            double dy2 = sqdist(yi, jb->Y + j * jb->ldy, jb->m);
+            record(r, sg->i, j, dx2, dy2, jb->eps, jb->lo, jb->hi, jb->nbins, jb->edge_tol);
+        }
+    }
+    return NULL;
+}
+
+/*
+ * Certificate over the pairs held by the tiles [t0, t1) of the upper triangle
+ * of `tile` x `tile` blocks of the points, numbered row by row: with T block
+ * rows (blocks <= 0: ceil(n / tile); more rows than that are blocks past n),
+ * block row I holds the tiles (I, J), J = I .. T - 1, and tile (I, J) holds
+ * the pairs (i, j) with i in block I, j in block J and i < j < n.  This is
+ * the pair set of one shard of the GPU library's sharded certificate; the
+ * definitions of every statistic are those of oracle_certificate.
+ */
+int oracle_certificate_tiles(const double *X, int64_t ldx, const double *Y, int64_t ldy,
+                             int64_t n, int d, int m, double eps, double lo, double hi,
+                             int nbins, int64_t tile, int64_t blocks, int64_t t0, int64_t t1,
+                             int nthreads, double edge_tol, oracle_cert_t *out) {
+    if (!X || !Y || !out || n < 0 || d < 1 || m < 1 || nbins < 1 || nbins > ORACLE_MAX_BINS ||
+        !(hi > lo) || tile < 1 || t0 < 0 || t1 < t0 || ldx < d || ldy < m)
+        return -1;
+    if (nthreads < 1) nthreads = 1;
+    const int64_t T = blocks > 0 ? blocks : (n + tile - 1) / tile;
+    if (T * tile < n || t1 > T * (T + 1) / 2) return -1;
+    /* the row segments: for each block row I, the block columns [Ja, Jb) of
+       the range, hence j in [max(i + 1, Ja tile), min(n, Jb tile)) */
+    int64_t cap = 0;
+    for (int64_t I = 0, off = 0; I < T; off += T - I, ++I) {
+        int64_t a = t0 > off ? t0 : off, b = t1 < off + (T - I) ? t1 : off + (T - I);
+        if (a < b) cap += tile;
+    }
+    segment_t *seg = (segment_t *)calloc((size_t)(cap > 0 ? cap : 1), sizeof(segment_t));
+    seg_job_t *jobs = (seg_job_t *)calloc((size_t)nthreads, sizeof(seg_job_t));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!seg || !jobs || !th) {
+        free(seg);
+        free(jobs);
+        free(th);
+        return -1;
+    }
+    int64_t nseg = 0;
+    for (int64_t I = 0, off = 0; I < T; off += T - I, ++I) {
+        int64_t a = t0 > off ? t0 : off, b = t1 < off + (T - I) ? t1 : off + (T - I);
+        if (a >= b) continue;
+        const int64_t Ja = I + (a - off), Jb = I + (b - off);
+        for (int64_t i = I * tile; i < (I + 1) * tile && i < n; ++i) {
+            int64_t jb = Ja * tile > i + 1 ? Ja * tile : i + 1;
+            int64_t je = Jb * tile < n ? Jb * tile : n;
+            if (jb < je) {
+                seg[nseg].i = i;
+                seg[nseg].jb = jb;
+                seg[nseg].je = je;
+                ++nseg;
+            }
+        }
+    }
+    for (int t = 0; t < nthreads; ++t) {
+        seg_job_t *jb = &jobs[t];
+        jb->X = X; jb->Y = Y; jb->ldx = ldx; jb->ldy = ldy; jb->seg = seg; jb->nseg = nseg;
+        jb->d = d; jb->m = m; jb->nbins = nbins; jb->tid = t; jb->nthreads = nthreads;
+        jb->eps = eps; jb->lo = lo; jb->hi = hi; jb->edge_tol = edge_tol;
+    }
+    for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, seg_worker, &jobs[t]);
+    seg_worker(&jobs[0]);
+    for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+    memset(out, 0, sizeof(*out));
+    out->argmax_i = out->argmax_j = -1;
+    for (int t = 0; t < nthreads; ++t) {
+        oracle_cert_t *r = &jobs[t].res;
+        out->pairs += r->pairs;
+        out->degenerate += r->degenerate;
+        out->violations += r->violations;
+        out->overflow += r->overflow;
+        out->near_edge += r->near_edge;
+        for (int b = 0; b < nbins; ++b) out->hist[b] += r->hist[b];
+        neumaier_add(&out->sum, &out->sum_c, r->sum);
+        neumaier_add(&out->sum, &out->sum_c, r->sum_c);
+        if (r->argmax_i >= 0) {
+            int better = out->argmax_i < 0 || r->max > out->max ||
+                         (r->max == out->max &&
+                          (r->argmax_i < out->argmax_i ||
+                           (r->argmax_i == out->argmax_i && r->argmax_j < out->argmax_j)));
+            if (better) {
+                out->max = r->max;
+                out->argmax_i = r->argmax_i;
+                out->argmax_j = r->argmax_j;
+            }
+        }
+    }
+    out->sum += out->sum_c;
+    out->sum_c = 0.0;
+    free(seg);
+    free(jobs);
+    free(th);
+    return 0;
+}
+
 /*
  * Squared distances ||x_i - x_j||^2 and ||y_i - y_j||^2 (FP64, direct
  * differences) for an explicit list of pairs; used to check sampled outputs of

@@ -86,6 +86,12 @@ def _load():
             ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
             ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int64,
             ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_Cert)]
+        lib.oracle_certificate_tiles.restype = ctypes.c_int
+        lib.oracle_certificate_tiles.argtypes = [
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+            ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+            ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
+            ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_Cert)]
         lib.oracle_pair_sqdist.restype = ctypes.c_int
         lib.oracle_pair_sqdist.argtypes = [
             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
@@ -126,6 +132,34 @@ def certificate(X: np.ndarray, Y: np.ndarray, eps: float, lo: float = 0.0,
         float(hi), nbins, a, b, threads or default_threads(), float(edge_tol), ctypes.byref(res))
     if rc != 0:
         raise ValueError("oracle_certificate: bad arguments")
+    return OracleCert(int(res.pairs), int(res.degenerate), int(res.violations),
+                      int(res.overflow), np.array(res.hist[:nbins], dtype=np.int64),
+                      float(res.max), int(res.argmax_i), int(res.argmax_j),
+                      float(res.sum), float(eps), float(lo), float(hi), int(res.near_edge))
+
+
+def certificate_tiles(X: np.ndarray, Y: np.ndarray, eps: float, t0: int, t1: int,
+                      tile: int = 128, blocks: int = 0, lo: float = 0.0,
+                      hi: float | None = None, nbins: int = 64, threads: int | None = None,
+                      edge_tol: float = 1e-6) -> OracleCert:
+    """The certificate over the pairs of tiles [t0, t1) of the upper triangle of
+    tile x tile blocks, numbered row by row over ``blocks`` block rows (0:
+    ceil(n / tile)) (``cert.c``): the pair set of one shard of the GPU
+    library's sharded certificate."""
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    Y = np.ascontiguousarray(Y, dtype=np.float64)
+    if X.shape[0] != Y.shape[0]:
+        raise ValueError("X and Y must have the same number of rows")
+    if hi is None:
+        hi = 2.0 * eps
+    n, d = X.shape
+    m = Y.shape[1]
+    res = _Cert()
+    rc = _load().oracle_certificate_tiles(
+        X.ctypes.data, d, Y.ctypes.data, m, n, d, m, float(eps), float(lo), float(hi), nbins,
+        tile, blocks, t0, t1, threads or default_threads(), float(edge_tol), ctypes.byref(res))
+    if rc != 0:
+        raise ValueError("oracle_certificate_tiles: bad arguments")
     return OracleCert(int(res.pairs), int(res.degenerate), int(res.violations),
                       int(res.overflow), np.array(res.hist[:nbins], dtype=np.int64),
                       float(res.max), int(res.argmax_i), int(res.argmax_j),

@@ -1125,7 +1125,7 @@ bool tc_pair_supported(adagio_ctx *ctx) { return pair_capacity(ctx) > 0; }
 // a synchronous upload, so callers that capture graphs make it resident first
 // with tc_prepare).
 static const uint32_t *schedule_for(adagio_ctx *ctx, int T, TileConfig cfg, long long *count) {
-    const int key = (T << 8) | (cfg.band << 2) | cfg.variant;
+    const int key = (T << 10) | (cfg.band << 2) | cfg.variant;
     const int variant = cfg.variant;
     auto it = ctx->tc_sched.find(key);
     if (it != ctx->tc_sched.end()) {

@@ -267,7 +267,7 @@ int adagio_set_timing(adagio_ctx *ctx, int enable) {
 }
 
 int adagio_set_tile_kernel(adagio_ctx *ctx, int variant, int band) {
-    if (!ctx || variant < ADAGIO_TILES_AUTO || variant > ADAGIO_TILES_PAIR || band < 0 || band > 32)
+    if (!ctx || variant < ADAGIO_TILES_AUTO || variant > ADAGIO_TILES_PAIR || band < 0 || band > 64)
         return ADAGIO_E_INVALID_ARG;
     ctx->tc_variant = variant;
     ctx->tc_band = band;

@@ -96,7 +96,7 @@ int adagio_autotune_tiles(adagio_ctx *ctx, const float *X, int64_t n, int d, int
     } restore{ctx, saved_variant, saved_band, saved_timing};
     ctx->collect_timing = 1;
     for (int v : variants)
-        for (int band : {4, 8, 16}) {
+        for (int band : {4, 8, 16, 32, 64}) {
             ctx->tc_variant = v;
             ctx->tc_band = band;
             const double ms = time_config(ctx, dX, lx, dY, ly, n, d, m, co, st);

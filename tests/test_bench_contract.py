@@ -27,3 +27,7 @@ def test_reference_arm_json_line():
     assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["e2e"]["d2h_bytes_per_step"] == 0
     assert j["e2e"]["value"] == j["value"] and j["e2e"]["unit"] == j["unit"]
     assert "workload" in j["config"]
+    # the same workload dictionary as the main arm's line
+    sys.path.insert(0, ROOT)
+    import bench
+    assert j["config"] == bench.workload_config()

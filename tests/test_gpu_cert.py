@@ -4,7 +4,7 @@ import pytest
 
 from gpu_helpers import CERT_MODES, assert_cert_parity
 from oracle import adagio as O
-from oracle.certificate import certificate, pair_distortion
+from oracle.certificate import certificate, certificate_tiles, pair_distortion
 from paper_1609_05388_gb300 import synth
 
 torch = pytest.importorskip("torch")
@@ -304,6 +304,20 @@ def test_sharded_certificate_matches_whole(ctx, prec):
         assert (g.max, g.argmax_i, g.argmax_j) == (whole.max, whole.argmax_i, whole.argmax_j)
         assert abs(g.mean - whole.mean) <= 1e-12 * whole.mean
         assert_cert_parity(g, o, wl.X, Y)
+        # every shard against the oracle's certificate of the same tiles
+        n = wl.X.shape[0]
+        B = 2 * (-(-n // 256))
+        ntp = B * (B + 1) // 2
+        for sh, part in enumerate(parts):
+            t0, t1 = ntp * sh // k, ntp * (sh + 1) // k
+            os_ = certificate_tiles(wl.X, Y, 0.1, t0, t1, blocks=B)
+            assert (part.pairs, part.degenerate) == (os_.pairs, os_.degenerate)
+            hist = np.array(part.hist[:], dtype=np.int64)
+            assert int(np.abs(hist - os_.hist).sum()) <= 2 * os_.near_edge
+            assert abs(part.violations - os_.violations) <= os_.near_edge
+            assert abs(part.max - os_.max) <= 1e-5
+            good = part.pairs - part.degenerate
+            assert abs(part.sum / good - os_.mean) <= 1e-6
     with pytest.raises(lib.AdagioError):
         ctx.distortion_shard(X, Yd, 0.1, 3, 3, precision=prec)
 

@@ -28,7 +28,7 @@ def test_autotune_choice_and_certificates_after_it(data, tmp_path):
     with lib.Context(0) as ctx:
         best = ctx.autotune_tiles(X, Y, 0.1, precision=lib.PREC_FP16X3)
         assert best["variant"] in (lib.TILES_SINGLE, lib.TILES_PAIR)
-        assert best["band"] in (4, 8, 16) and best["tile_ms"] > 0.0
+        assert best["band"] in (4, 8, 16, 32, 64) and best["tile_ms"] > 0.0
         T = -(-n // 256) * 2
         assert best["size_class"] == int(np.ceil(np.log2(T)))
         # later certificates of this size class use the tuned configuration

@@ -167,3 +167,36 @@ def test_near_edge_counts_pairs_within_1e6_of_an_edge_or_eps(offset, near, targe
     if target == "edge":
         assert int(np.argmax(c.hist)) == (20 if offset > 0 else 19)
     assert c.violations == (1 if delta > eps else 0)
+
+
+def test_tile_ranges_partition_the_pairs_and_match_row_ranges():
+    """Tile ranges of the row-major tile triangle partition the pairs: any cut
+    of [0, T(T+1)/2) into ranges gives parts that add up to the whole
+    certificate, and the tiles of whole block rows are exactly a row range."""
+    rng = np.random.default_rng(9)
+    n, tile = 53, 8                               # 7 block rows, a ragged last block
+    X = rng.standard_normal((n, 4))
+    Y = X @ rng.standard_normal((4, 3))
+    from oracle.certificate import certificate_tiles
+    full = certificate(X, Y, eps=0.4)
+    T = (n + tile - 1) // tile
+    ntp = T * (T + 1) // 2
+    cuts = [0, 3, 4, 11, 19, ntp]
+    parts = [certificate_tiles(X, Y, 0.4, a, b, tile=tile) for a, b in zip(cuts[:-1], cuts[1:])]
+    assert sum(p.pairs for p in parts) == full.pairs == n * (n - 1) // 2
+    assert sum(p.violations for p in parts) == full.violations
+    np.testing.assert_array_equal(sum(p.hist for p in parts), full.hist)
+    assert max(p.max for p in parts) == full.max
+    # block rows 0..1 are tiles [0, T + T - 1): rows [0, 2 tile)
+    a = certificate_tiles(X, Y, 0.4, 0, T + (T - 1), tile=tile)
+    b = certificate(X, Y, eps=0.4, rows=(0, 2 * tile))
+    assert (a.pairs, a.violations, a.max) == (b.pairs, b.violations, b.max)
+    np.testing.assert_array_equal(a.hist, b.hist)
+    # a single tile (I, J) = (1, 3): 8 x 8 pairs
+    t13 = T + (3 - 1)
+    one = certificate_tiles(X, Y, 0.4, t13, t13 + 1, tile=tile)
+    assert one.pairs == tile * tile
+    # more block rows than the points need (blocks past n hold no pairs)
+    T2 = T + 1
+    whole = certificate_tiles(X, Y, 0.4, 0, T2 * (T2 + 1) // 2, tile=tile, blocks=T2)
+    assert whole.pairs == full.pairs and whole.max == full.max
