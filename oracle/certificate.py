@@ -14,6 +14,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "cert.c")
+_SRCS = [_SRC, os.path.join(_HERE, "knn.c")]
 _OUT_DIR = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_OUT_DIR, "liboracle_cert.so")
 MAX_BINS = 256
@@ -59,15 +60,15 @@ class OracleCert:
 
 
 def build(force: bool = False) -> str:
-    """Compile cert.c (gcc, -O2, pthreads).  Returns the library path."""
+    """Compile cert.c and knn.c (gcc, -O2, pthreads).  Returns the library path."""
     os.makedirs(_OUT_DIR, exist_ok=True)
     if (not force and os.path.exists(_LIB_PATH)
-            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+            and all(os.path.getmtime(_LIB_PATH) >= os.path.getmtime(f) for f in _SRCS)):
         return _LIB_PATH
     tmp = _LIB_PATH + f".tmp{os.getpid()}"
     # -ffp-contract=off keeps every FP64 operation individually rounded
     cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-std=c11",
-           "-o", tmp, _SRC, "-lm", "-lpthread"]
+           "-o", tmp, *_SRCS, "-lm", "-lpthread"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
@@ -92,6 +93,11 @@ def _load():
             ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_double,
             ctypes.c_double, ctypes.c_double, ctypes.c_int, ctypes.c_int64, ctypes.c_int64,
             ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.POINTER(_Cert)]
+        lib.oracle_knn.restype = ctypes.c_int
+        lib.oracle_knn.argtypes = [
+            ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
+            ctypes.c_int64, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+            ctypes.c_void_p, ctypes.c_void_p]
         lib.oracle_pair_sqdist.restype = ctypes.c_int
         lib.oracle_pair_sqdist.argtypes = [
             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,

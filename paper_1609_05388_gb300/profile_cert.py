@@ -29,6 +29,8 @@ def main():
     ap.add_argument("--reps", type=int, default=2)
     ap.add_argument("--tiles", default="auto", choices=["auto", "single", "pair"],
                     help="tile kernel of the split-precision certificate")
+    ap.add_argument("--band", type=int, default=0,
+                    help="schedule band in tile rows (0: the default)")
     a = ap.parse_args()
     prec = {"fp32": lib.PREC_FP32, "fp16x3": lib.PREC_FP16X3, "bf16x3": lib.PREC_BF16X3}[a.precision]
     wl = synth.mnist_like(seed=1, n=a.n)
@@ -40,7 +42,7 @@ def main():
         A = torch.from_numpy(ctx.assemble(P, S)).cuda()
         Y = ctx.embed(A, X)
         ctx.set_tile_kernel({"auto": lib.TILES_AUTO, "single": lib.TILES_SINGLE,
-                             "pair": lib.TILES_PAIR}[a.tiles])
+                             "pair": lib.TILES_PAIR}[a.tiles], a.band)
         ctx.set_timing(True)
         tile_ms = []
         for _ in range(a.reps):

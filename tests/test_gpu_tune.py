@@ -59,4 +59,4 @@ def test_tile_table_of_another_device_or_malformed_is_rejected(tmp_path):
                 ctx.tune_load(str(p))
             assert ei.value.code == lib.E_INVALID_ARG
         with pytest.raises(lib.AdagioError):
-            ctx.set_tile_kernel(lib.TILES_SINGLE, 33)
+            ctx.set_tile_kernel(lib.TILES_SINGLE, 65)
