@@ -517,6 +517,33 @@ int adagio_debug_tile_bounds(adagio_ctx *ctx, const float *X, int64_t n, int d, 
                              const float *Y, int m, int64_t ldy, int precision, int64_t tiles,
                              int64_t stride, float *out, int *tile_ij, void *stream);
 
+/*
+ * k nearest neighbours in an embedded space: the searches of the paper's
+ * applications (Sec. 4.6, a 10-nearest-neighbour vote on embedded
+ * descriptors; Sec. 4.7, a k = 30 nearest-neighbour graph of the embedded
+ * points).  For every query row q of Q (nq x m, leading dimension ldq), the k
+ * rows b of B (nb x m, ldb) with the smallest Euclidean distance ||q - b||
+ * of the FP32 values, nearest first; equal distances are ordered by the
+ * smaller base index; with exclude_self, base row i is not a neighbour of
+ * query row i (the graph of one point set: pass the same array as Q and B).
+ *  idx  nq x k base indices (row-major int64), d2  nq x k squared distances
+ *       (FP64, from coordinate differences).  Host or device arrays.
+ *  1 <= k <= 48, k <= nb (k <= nb - 1 with exclude_self).
+ * Computed from tensor-core Gram blocks (split-precision FP16), with the
+ * candidates re-ranked by exact FP64 distances; a row whose candidate list
+ * cannot be shown complete from the Gram error bound is searched again over
+ * every base point (adagio_knn_last_exact_rows counts them).  The answer is
+ * the exact one.  Synchronises `stream`.
+ * Errors: INVALID_ARG, WORKSPACE, CUDA, TIMEOUT.
+ */
+int adagio_knn(adagio_ctx *ctx, const float *Q, int64_t nq, int64_t ldq, const float *B,
+               int64_t nb, int64_t ldb, int m, int k, int exclude_self, int64_t *idx,
+               double *d2, void *stream);
+
+/* Query rows of the last adagio_knn on ctx that were searched again over
+ * every base point (their candidate list could not be shown complete). */
+int64_t adagio_knn_last_exact_rows(const adagio_ctx *ctx);
+
 /* Number of kernels this library has launched in this process (all contexts,
  * all devices); a difference of two readings counts the launches between. */
 uint64_t adagio_launch_count(void);

@@ -196,6 +196,8 @@ def _load() -> ctypes.CDLL:
         "adagio_distortion_shard": (i32, [vp, vp, i64, i32, i64, vp, i32, i64, f64, f64, f64, i32,
                                           i32, i32, ctypes.POINTER(CertPartStruct), vp]),
         "adagio_cert_merge": (i32, [ctypes.POINTER(CertPartStruct), i32, ctypes.POINTER(CertStruct)]),
+        "adagio_knn": (i32, [vp, vp, i64, i64, vp, i64, i64, i32, i32, i32, vp, vp, vp]),
+        "adagio_knn_last_exact_rows": (i64, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -220,7 +222,8 @@ def exported_symbols() -> list[str]:
                         "adagio_mlp_save", "adagio_mlp_load", "adagio_fit_batched",
                         "adagio_last_batch_stats", "adagio_set_tile_kernel",
                         "adagio_tile_kernel_for", "adagio_autotune_tiles", "adagio_tune_save",
-                        "adagio_tune_load", "adagio_distortion_shard", "adagio_cert_merge")
+                        "adagio_tune_load", "adagio_distortion_shard", "adagio_cert_merge",
+                        "adagio_knn", "adagio_knn_last_exact_rows")
             if hasattr(LIB, n)]
 
 
@@ -415,6 +418,33 @@ class Context:
                                                   y.cols, y.ld, eps, hist_lo, hist_hi,
                                                   ctypes.byref(c), _stream(x, y)))
         return Certificate.from_struct(c)
+
+    # ---------------------------------------------------------------- neighbours
+    def knn(self, Q, k: int, B=None, exclude_self: bool | None = None):
+        """The k nearest rows of B (default: Q itself, without each row's own
+        index) for every row of Q: (idx int64 nq x k, d2 float64 nq x k),
+        nearest first, ties by index.  Device arrays give device results."""
+        q = _Arr(Q)
+        b = q if B is None else _Arr(B)
+        if exclude_self is None:
+            exclude_self = B is None
+        if q.cols != b.cols:
+            raise ValueError("Q and B need the same number of columns")
+        if q.cuda and b.cuda:
+            import torch
+            idx = torch.empty((q.rows, k), dtype=torch.int64, device=q.keep.device)
+            d2 = torch.empty((q.rows, k), dtype=torch.float64, device=q.keep.device)
+            pi, pd = idx.data_ptr(), d2.data_ptr()
+        else:
+            idx = np.empty((q.rows, k), dtype=np.int64)
+            d2 = np.empty((q.rows, k), dtype=np.float64)
+            pi, pd = idx.ctypes.data, d2.ctypes.data
+        self._check(LIB.adagio_knn(self.h, q.ptr, q.rows, q.ld, b.ptr, b.rows, b.ld, q.cols, k,
+                                   1 if exclude_self else 0, pi, pd, _stream(q, b)))
+        return idx, d2
+
+    def knn_last_exact_rows(self) -> int:
+        return int(LIB.adagio_knn_last_exact_rows(self.h))
 
     # -------------------------------------------------------------------- embed
     def embed(self, A, X, Y=None):

@@ -117,6 +117,8 @@ struct adagio_ctx {
     void *batch_host = nullptr;
     size_t batch_host_bytes = 0;
     adagio_batch_stats last_batch{0, 0, 0, 0.0};
+    // query rows of the last adagio_knn searched again over every base point
+    int64_t last_knn_redo = 0;
 };
 
 namespace adagio {
