@@ -260,6 +260,23 @@ def tensor_frac(pairs, d, m, tile_ms, peak):
     return achieved, achieved / peak
 
 
+def knn_leg(ctx, Y, peak, k=30):
+    """The k = 30 nearest-neighbour graph of the returned embedding (Sec. 4.7),
+    exact: 60 000 queries against the same 60 000 points."""
+    import torch
+    ctx.knn(Y[:1024], k, B=Y)           # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    idx, _ = ctx.knn(Y, k)
+    el = time.perf_counter() - t0
+    n, m = Y.shape
+    gram_flops = 2.0 * n * n * m
+    return {"workload": f"k={k} nearest-neighbour graph of the embedding ({n} x {m})",
+            "seconds": el, "queries_per_s": n / el,
+            "gram_tflops": gram_flops / el / 1e12, "gram_frac_of_bf16_peak": gram_flops / el / 1e12 / peak,
+            "rows_searched_exactly": ctx.knn_last_exact_rows()}
+
+
 def large_leg(ctx, lib, peak, prec):
     """The 200 000 x 2048 workload (power-law spectrum, 5 % Laplace outliers):
     one exhaustive certificate (2.0e10 pairs) of a JL map of 300 rows."""
@@ -495,6 +512,7 @@ def main():
         legs["bf16x3_same_map"] = {"tile_ms": bt, "recompute_ms": br, "queued": bq,
                                    "achieved_tflops": ach, "frac": fr, "max": cb.max,
                                    "certificate_pairs_per_s": pairs / ((bt + br) / 1e3)}
+        legs["knn_graph_k30"] = knn_leg(ctx, Y, peak)
         del Y
         torch.cuda.empty_cache()
         legs["large_200000x2048"] = large_leg(ctx, lib, peak, prec)
