@@ -534,7 +534,7 @@ int adagio_debug_tile_bounds(adagio_ctx *ctx, const float *X, int64_t n, int d, 
  * cannot be shown complete from the Gram error bound is searched again over
  * every base point (adagio_knn_last_exact_rows counts them).  The answer is
  * the exact one.  Synchronises `stream`.
- * Errors: INVALID_ARG, WORKSPACE, CUDA, TIMEOUT.
+ * Errors: INVALID_ARG, NONFINITE (NaN or Inf in Q or B), WORKSPACE, CUDA, TIMEOUT.
  */
 int adagio_knn(adagio_ctx *ctx, const float *Q, int64_t nq, int64_t ldq, const float *B,
                int64_t nb, int64_t ldb, int m, int k, int exclude_self, int64_t *idx,

@@ -8,11 +8,12 @@
 // ties (equal distances) broken by the smaller base index, query i's own index
 // left out when `exclude_self` (the graph of one point set).
 //
-// Steps, per block of 512 query rows:
+// Steps, per block of 1024 query rows:
 //   1. Gram block G = Q_blk B^T on tcgen05 tensor cores (the split-precision
 //      GEMM of tcgemm.cu: per-row power-of-two FP16 hi + lo planes, three
-//      products per term, FP32 accumulation), 512 x nb floats that stay in L2;
-//   2. one warp per query row scans its Gram row, forms the approximate squared
+//      products per term, FP32 accumulation), 1024 x nb floats;
+//   2. one warp per query row scans its Gram row (each lane loading kUnroll
+//      columns ahead of filtering them), forms the approximate squared
 //      distances d~ = |q|^2 + |b|^2 - 2 q.b and keeps the 64 smallest (d~, j)
 //      in a sorted list (kCand = k_max + 16 candidates);
 //   3. the candidates' distances are recomputed exactly from coordinate
@@ -37,7 +38,8 @@ namespace {
 
 constexpr int kMaxK = 48;                 // largest k served
 constexpr int kCand = 64;                 // candidates kept per query (two per lane)
-constexpr int kBlockQ = 512;              // query rows per Gram block
+constexpr int kBlockQ = 1024;             // query rows per Gram block
+constexpr int kUnroll = 8;                // columns a lane loads before filtering them
 constexpr int kSelWarps = 8;              // warps (query rows) per selection CTA
 constexpr float kDistErr = 128.0f * 5.9604645e-08f;  // c: 128 u
 
@@ -174,24 +176,42 @@ __global__ void __launch_bounds__(32 * kSelWarps)
     int *lj = s_j[w];
     int cnt = 0;
     float tau = INFINITY;  // smallest approximate distance not kept (this lane's share)
-    for (int64_t base = 0; base < p.nb; base += 32) {
-        const int64_t j = base + lane;
-        const bool valid = j < p.nb && !(p.exclude_self && j == i);
-        const float d = valid ? fmaf(-2.0f, g[j], __fadd_rn(nq, p.n2b[j])) : INFINITY;
-        // the list's last key: a point must come before it to enter a full list
-        const float td = cnt == kCand ? ld[kCand - 1] : INFINITY;
-        const int tj = cnt == kCand ? lj[kCand - 1] : 0x7fffffff;
-        const bool want = valid && (cnt < kCand || key_before(d, (int)j, td, tj));
-        if (valid && !want) tau = fminf(tau, d);
-        unsigned mask = __ballot_sync(0xffffffffu, want);
-        while (mask) {
-            const int l = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const float dl = __shfl_sync(0xffffffffu, d, l);
-            const int jl = (int)__shfl_sync(0xffffffffu, (unsigned)j, l);
-            float out;
-            list_insert(ld, lj, cnt, dl, jl, out);
-            if (lane == 0) tau = fminf(tau, out);
+    // the list's last key: a point must come before it to enter a full list
+    float td = INFINITY;
+    int tj = 0x7fffffff;
+    for (int64_t base = 0; base < p.nb; base += 32 * kUnroll) {
+        float d[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int64_t j = base + 32 * u + lane;
+            const bool valid = j < p.nb && !(p.exclude_self && j == i);
+            d[u] = valid ? fmaf(-2.0f, __ldg(g + j), __fadd_rn(nq, __ldg(p.n2b + j))) : INFINITY;
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+            const int jj = (int)(base + 32 * u + lane);
+            const bool valid = d[u] < INFINITY;
+            const bool want = valid && key_before(d[u], jj, td, tj);
+            if (valid && !want) tau = fminf(tau, d[u]);
+            unsigned mask = __ballot_sync(0xffffffffu, want);
+            if (!mask) continue;
+            while (mask) {
+                const int l = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const float dl = __shfl_sync(0xffffffffu, d[u], l);
+                const int jl = __shfl_sync(0xffffffffu, jj, l);
+                if (cnt == kCand && !key_before(dl, jl, td, tj)) {
+                    if (lane == 0) tau = fminf(tau, dl);
+                    continue;
+                }
+                float out;
+                list_insert(ld, lj, cnt, dl, jl, out);
+                if (lane == 0) tau = fminf(tau, out);
+                if (cnt == kCand) {
+                    td = ld[kCand - 1];
+                    tj = lj[kCand - 1];
+                }
+            }
         }
     }
     for (int o = 16; o > 0; o >>= 1) tau = fminf(tau, __shfl_xor_sync(0xffffffffu, tau, o));
@@ -321,7 +341,7 @@ extern "C" int adagio_knn(adagio_ctx *ctx, const float *Q, int64_t nq, int64_t l
             pq.Kp = Kp;
             pq.scale = qs;
             pq.scale_stride = 1;
-            knn_norms_kernel<<<(unsigned)ceil_div(nq, 8), 256, 0, st>>>(dQ, nq, m, lq, nqq, nullptr);
+            knn_norms_kernel<<<(unsigned)ceil_div(nq, 8), 256, 0, st>>>(dQ, nq, m, lq, nqq, n2b_max + 1);
             ADAGIO_CHECK_LAUNCH();
             n2q = nqq;
         }
@@ -364,8 +384,13 @@ extern "C" int adagio_knn(adagio_ctx *ctx, const float *Q, int64_t nq, int64_t l
         }
         // rows whose candidate list could not be shown final: an exact search
         unsigned long long hred = 0;
+        unsigned hmax[2] = {0u, 0u};
         ADAGIO_CUDA(cudaMemcpyAsync(&hred, nredo, sizeof(hred), cudaMemcpyDeviceToHost, st));
+        ADAGIO_CUDA(cudaMemcpyAsync(hmax, n2b_max, sizeof(hmax), cudaMemcpyDeviceToHost, st));
         ADAGIO_CUDA(cudaStreamSynchronize(st));
+        // a NaN or infinite squared norm (bits at or above those of +inf)
+        if (hmax[0] >= 0x7f800000u || hmax[1] >= 0x7f800000u)
+            fail(ADAGIO_E_NONFINITE, "input holds NaN or Inf (or values whose squared norm overflows)");
         if (hred > 0) {
             std::vector<int64_t> rows((size_t)hred);
             ADAGIO_CUDA(cudaMemcpy(rows.data(), redo, hred * sizeof(int64_t), cudaMemcpyDeviceToHost));

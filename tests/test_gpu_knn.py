@@ -97,3 +97,8 @@ def test_bad_arguments(ctx):
         assert ei.value.code == lib.E_INVALID_ARG
     idx, _ = ctx.knn(np.arange(10, dtype=np.float32).reshape(10, 1), 9)
     assert idx.shape == (10, 9)
+    Z = np.ones((40, 3), dtype=np.float32)
+    Z[7, 1] = np.nan
+    with pytest.raises(lib.AdagioError) as ei:
+        ctx.knn(Z, 3)
+    assert ei.value.code == lib.E_NONFINITE
