@@ -311,18 +311,52 @@ int oracle_certificate_tiles(const double *X, int64_t ldx, const double *Y, int6
     return 0;
 }
 
+typedef struct {
+    const double *X, *Y;
+    int64_t ldx, ldy;
+    int d, m;
+    const int64_t *I, *J;
+    int64_t begin, end;
+    double *dx2, *dy2;
+} pairs_job_t;
+
+static void *pairs_worker(void *arg) {
+    pairs_job_t *jb = (pairs_job_t *)arg;
+    for (int64_t p = jb->begin; p < jb->end; ++p) {
+        jb->dx2[p] = sqdist(jb->X + jb->I[p] * jb->ldx, jb->X + jb->J[p] * jb->ldx, jb->d);
+        jb->dy2[p] = sqdist(jb->Y + jb->I[p] * jb->ldy, jb->Y + jb->J[p] * jb->ldy, jb->m);
+    }
+    return NULL;
+}
+
 /*
  * Squared distances ||x_i - x_j||^2 and ||y_i - y_j||^2 (FP64, direct
  * differences) for an explicit list of pairs; used to check sampled outputs of
- * full-size runs one pair at a time.
+ * full-size runs one pair at a time.  The list is split evenly over nthreads.
  */
 int oracle_pair_sqdist(const double *X, int64_t ldx, const double *Y, int64_t ldy,
                        int d, int m, const int64_t *I, const int64_t *J,
-                       int64_t npairs, double *dx2, double *dy2) {
+                       int64_t npairs, double *dx2, double *dy2, int nthreads) {
     if (!X || !Y || !I || !J || !dx2 || !dy2 || d < 1 || m < 1) return -1;
-    for (int64_t p = 0; p < npairs; ++p) {
-        dx2[p] = sqdist(X + I[p] * ldx, X + J[p] * ldx, d);
-        dy2[p] = sqdist(Y + I[p] * ldy, Y + J[p] * ldy, m);
+    if (nthreads < 1) nthreads = 1;
+    pairs_job_t *jobs = (pairs_job_t *)calloc((size_t)nthreads, sizeof(pairs_job_t));
+    pthread_t *th = (pthread_t *)calloc((size_t)nthreads, sizeof(pthread_t));
+    if (!jobs || !th) {
+        free(jobs);
+        free(th);
+        return -1;
     }
+    for (int t = 0; t < nthreads; ++t) {
+        pairs_job_t *jb = &jobs[t];
+        jb->X = X; jb->Y = Y; jb->ldx = ldx; jb->ldy = ldy; jb->d = d; jb->m = m;
+        jb->I = I; jb->J = J; jb->dx2 = dx2; jb->dy2 = dy2;
+        jb->begin = npairs * t / nthreads;
+        jb->end = npairs * (t + 1) / nthreads;
+    }
+    for (int t = 1; t < nthreads; ++t) pthread_create(&th[t], NULL, pairs_worker, &jobs[t]);
+    pairs_worker(&jobs[0]);
+    for (int t = 1; t < nthreads; ++t) pthread_join(th[t], NULL);
+    free(jobs);
+    free(th);
     return 0;
 }

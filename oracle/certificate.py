@@ -102,7 +102,7 @@ def _load():
         lib.oracle_pair_sqdist.argtypes = [
             ctypes.c_void_p, ctypes.c_int64, ctypes.c_void_p, ctypes.c_int64,
             ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
-            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p]
+            ctypes.c_int64, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]
         _lib = lib
     return _lib
 
@@ -183,7 +183,7 @@ def pair_sqdist(X: np.ndarray, Y: np.ndarray, I, J):
     rc = _load().oracle_pair_sqdist(X.ctypes.data, X.shape[1], Y.ctypes.data,
                                     Y.shape[1], X.shape[1], Y.shape[1],
                                     I.ctypes.data, J.ctypes.data, I.shape[0],
-                                    dx2.ctypes.data, dy2.ctypes.data)
+                                    dx2.ctypes.data, dy2.ctypes.data, default_threads())
     if rc != 0:
         raise ValueError("oracle_pair_sqdist: bad arguments")
     return dx2, dy2

@@ -396,14 +396,20 @@ class Context:
                                                 nshards, ctypes.byref(part), _stream(x, y)))
         return part
 
-    def debug_tile_bounds(self, X, Y, tiles: int, precision: int = PREC_FP16X3, stride: int = 1):
+    def debug_tile_bounds(self, X, Y, tiles: int, precision: int = PREC_FP16X3, stride: int = 1,
+                          out=None):
         """(dump[tiles,128,128,4] = (dx2, dy2, ex, ey), tile_ij[tiles,2]) of the fast path,
-        for every stride-th tile pair the tile kernel visits."""
+        for every stride-th tile pair the tile kernel visits.  `out` may be a
+        device tensor of that shape (float32) that receives the dump."""
         x, y = _Arr(X), _Arr(Y)
-        out = np.empty((tiles, 128, 128, 4), dtype=np.float32)
+        if out is None:
+            out = np.empty((tiles, 128, 128, 4), dtype=np.float32)
+            optr = out.ctypes.data
+        else:
+            optr = out.data_ptr()
         ij = np.empty((tiles, 2), dtype=np.int32)
         self._check(LIB.adagio_debug_tile_bounds(self.h, x.ptr, x.rows, x.cols, x.ld, y.ptr, y.cols,
-                                                 y.ld, precision, tiles, stride, out.ctypes.data,
+                                                 y.ld, precision, tiles, stride, optr,
                                                  ij.ctypes.data, _stream(x, y)))
         return out, ij
 
