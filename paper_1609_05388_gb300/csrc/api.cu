@@ -130,7 +130,7 @@ int adagio_debug_tile_bounds(adagio_ctx *ctx, const float *X, int64_t n, int d, 
     ADAGIO_REQUIRE(n >= 2 && n < (1ll << 31) - 256 && d >= 1 && m >= 1 && ldx >= d && ldy >= m,
                    "bad sizes");
     check_precision(precision);
-    const int T = (int)((n + 127) / 128);
+    const int T = (int)(pad_rows(n) / 128);  // the tile grid the kernels visit
     const long long ntp = (long long)T * (T + 1) / 2;
     ADAGIO_REQUIRE(stride >= 1 && tiles >= 1 && (tiles - 1) * stride < ntp,
                    "need stride >= 1 and tiles >= 1 with (tiles - 1) * stride < %lld", ntp);
