@@ -218,6 +218,52 @@ int adagio_distortion_shard(adagio_ctx *ctx, const float *X, int64_t n, int d, i
 int adagio_cert_merge(const adagio_cert_part *parts, int count, adagio_cert *out);
 
 /*
+ * Verdict of one JL prefix in adagio_distortion_prefixes.
+ *  k            JL rows the candidate keeps (kc)
+ *  verdict      1: every pair's distortion is certainly <= eps (the candidate
+ *               is certified); 0: some pair's distortion certainly exceeds
+ *               eps; -1: undecided (no certain violation, but the error bound
+ *               of some pair straddles eps: certify the candidate in full)
+ *  certain_violations   pairs whose distortion certainly exceeds eps
+ *  unsettled_pairs      pairs whose bound interval contains eps
+ *  max_lower, max_upper the candidate's largest distortion lies in
+ *               [max_lower, max_upper] (lower and upper ends of the pairs'
+ *               bound intervals)
+ *  Pairs whose distortion the fast tiles cannot bound (x_i == x_j, or too
+ *  ill-conditioned) count as unsettled and make max_upper +inf.
+ */
+typedef struct {
+    int32_t k;
+    int32_t verdict;
+    uint64_t certain_violations, unsettled_pairs;
+    double max_lower, max_upper;
+} adagio_prefix_cert;
+
+/*
+ * Several target dimensions of the search of Algorithm 1 checked in one pass
+ * over the pairs.  Y (n x (s + k), leading dimension ldy) is the embedding of
+ * the map with s PCA rows and k JL rows (Lemma 2), the PCA coordinates first.
+ * Candidate c keeps the PCA rows and the first kc[c] JL rows, rescaled to the
+ * JL map with kc[c] rows (entries +-1/sqrt(kc[c]), so its squared distances
+ * are |dP|^2 + (k / kc[c]) |dJ[:kc[c]]|^2).  Either every kc[c] is a multiple
+ * of 64 or equal to k, or every k - kc[c] is a multiple of 64 (k, k - 64,
+ * k - 128, ...: the prefixes below a dimension already fitted);
+ * 1 <= kc[c] <= k; 1 <= count <= 4.  The pass computes `full`, the certificate of
+ * the whole map (as adagio_distortion with hist [0, 2 eps)), and out[c], the
+ * verdict of each candidate against eps from per-pair bounds on its
+ * distortion (the pass shares the tensor-core Gram sums; no pair of a
+ * candidate is recomputed, so a verdict may stay undecided).
+ *  precision    ADAGIO_PREC_FP16X3 or ADAGIO_PREC_BF16X3.
+ * X, Y host or device; full and out host.  Synchronises `stream`.
+ * Errors: INVALID_ARG (sizes, kc, count, eps in (0, 1), precision),
+ * NONFINITE, WORKSPACE, QUEUE_OVERFLOW, UNSUPPORTED, CUDA.
+ */
+int adagio_distortion_prefixes(adagio_ctx *ctx, const float *X, int64_t n, int d, int64_t ldx,
+                               const float *Y, int s, int k, int64_t ldy, double eps, const int *kc,
+                               int count, int precision, adagio_cert *full, adagio_prefix_cert *out,
+                               void *stream);
+
+/*
  * Allocation-free certificate (the paper has no counterpart; this is a
  * deployment variant of adagio_distortion).  For callers that cannot let a
  * library allocate device memory during a call -- a service whose device

@@ -67,6 +67,15 @@ class CertPartStruct(ctypes.Structure):
     ]
 
 
+class PrefixCertStruct(ctypes.Structure):
+    """adagio_prefix_cert: the verdict of one JL prefix."""
+    _fields_ = [
+        ("k", ctypes.c_int32), ("verdict", ctypes.c_int32),
+        ("certain_violations", ctypes.c_uint64), ("unsettled_pairs", ctypes.c_uint64),
+        ("max_lower", ctypes.c_double), ("max_upper", ctypes.c_double),
+    ]
+
+
 class FitOptsStruct(ctypes.Structure):
     _fields_ = [
         ("eps", ctypes.c_double), ("m", ctypes.c_int), ("s", ctypes.c_int),
@@ -198,6 +207,10 @@ def _load() -> ctypes.CDLL:
         "adagio_cert_merge": (i32, [ctypes.POINTER(CertPartStruct), i32, ctypes.POINTER(CertStruct)]),
         "adagio_knn": (i32, [vp, vp, i64, i64, vp, i64, i64, i32, i32, i32, vp, vp, vp]),
         "adagio_knn_last_exact_rows": (i64, [vp]),
+        "adagio_distortion_prefixes": (i32, [vp, vp, i64, i32, i64, vp, i32, i32, i64, f64,
+                                             ctypes.POINTER(i32), i32, i32,
+                                             ctypes.POINTER(CertStruct),
+                                             ctypes.POINTER(PrefixCertStruct), vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -223,7 +236,8 @@ def exported_symbols() -> list[str]:
                         "adagio_last_batch_stats", "adagio_set_tile_kernel",
                         "adagio_tile_kernel_for", "adagio_autotune_tiles", "adagio_tune_save",
                         "adagio_tune_load", "adagio_distortion_shard", "adagio_cert_merge",
-                        "adagio_knn", "adagio_knn_last_exact_rows")
+                        "adagio_knn", "adagio_knn_last_exact_rows",
+                        "adagio_distortion_prefixes")
             if hasattr(LIB, n)]
 
 
@@ -395,6 +409,27 @@ class Context:
                                                 y.ld, eps, hist_lo, hist_hi, precision, shard,
                                                 nshards, ctypes.byref(part), _stream(x, y)))
         return part
+
+    def distortion_prefixes(self, X, Y, s: int, eps: float, kc,
+                            precision: int = PREC_FP16X3):
+        """(certificate of the whole map, [verdict dict per JL prefix]).
+
+        Y = [PCA part (s columns) | k JL columns]; prefix c keeps kc[c] JL
+        columns rescaled by sqrt(k / kc[c]).  verdict 1 = certified at eps,
+        0 = certainly violated, -1 = undecided."""
+        x, y = _Arr(X), _Arr(Y)
+        if x.rows != y.rows:
+            raise ValueError("X and Y must have the same number of rows")
+        kc = [int(v) for v in kc]
+        ks = (ctypes.c_int * max(1, len(kc)))(*kc)
+        outs = (PrefixCertStruct * max(1, len(kc)))()
+        c = CertStruct()
+        self._check(LIB.adagio_distortion_prefixes(self.h, x.ptr, x.rows, x.cols, x.ld, y.ptr, s,
+                                                   y.cols - s, y.ld, eps, ks, len(kc), precision,
+                                                   ctypes.byref(c), outs, _stream(x, y)))
+        res = [{f: getattr(outs[i], f) for f, _ in PrefixCertStruct._fields_}
+               for i in range(len(kc))]
+        return Certificate.from_struct(c), res
 
     def debug_tile_bounds(self, X, Y, tiles: int, precision: int = PREC_FP16X3, stride: int = 1,
                           out=None):

@@ -125,6 +125,9 @@ void cert_job_enqueue(adagio_ctx *ctx, CertJob &job, cudaStream_t st, cudaEvent_
     L.dump = opt.dump;
     L.dump_tiles = opt.dump_tiles;
     L.dump_stride = opt.dump_stride;
+    L.multi = opt.multi;
+    L.ysrc = job.Y;
+    L.ldy_src = job.ldy;
     L.rs_xy = job.rs_xy;
     if (opt.nshards > 1) shard_range(job.n, opt.shard, opt.nshards, &L.t_begin, &L.t_end);
     if (tc) {

@@ -8,6 +8,23 @@
 
 namespace adagio {
 
+// JL-prefix candidates of the multi-candidate certificate (one pass of the
+// single-CTA tensor tiles): Y holds the PCA part in its first s_pad = pad64(s)
+// columns (zeros after s), zeros up to column jo and k JL columns from jo;
+// candidate c keeps the first kc[c] JL columns scaled by sqrt(k / kc[c]), and
+// jo + kc[c] is a multiple of 64 or kc[c] = k.  The kernel writes one verdict
+// record per epilogue warp and candidate into `out` (device); `cs` (device)
+// receives the candidates' row statistics.
+struct MultiSpec {
+    int count = 0;
+    int s = 0, s_pad = 0, jo = 0, k = 0;
+    int kc[4] = {0, 0, 0, 0};
+    double eps = 0.0;          // the candidates' violation threshold (FP64, as given)
+    void *cs = nullptr;        // count x n_pad float4
+    void *out = nullptr;       // slots x count verdict records (32 B each)
+    int slots = 0;             // records per candidate (CTAs x epilogue warps)
+};
+
 struct CertLaunch {
     adagio_ctx *ctx = nullptr;
     const PrepMat *x = nullptr;
@@ -27,6 +44,9 @@ struct CertLaunch {
     // tiles [t_begin, t_end) of the row-major upper triangle of 128 x 128
     // tiles (a shard); t_end < 0: all of them
     long long t_begin = 0, t_end = -1;
+    const MultiSpec *multi = nullptr;  // multi-candidate pass (single-CTA tensor tiles)
+    const float *ysrc = nullptr;       // Y as given (the candidates' row statistics)
+    int64_t ldy_src = 0;
 };
 
 // Device-side result of the finaliser (host copies it back).
@@ -88,6 +108,7 @@ struct CertOptions {
     long long dump_tiles = 0;
     long long dump_stride = 1;
     int shard = 0, nshards = 1;  // this shard of the tiles (adagio_distortion_shard)
+    const MultiSpec *multi = nullptr;  // JL-prefix candidates checked in the same pass
 };
 
 // Tiles [*t0, *t1) of shard `shard` of `nshards` (row-major upper triangle of

@@ -77,12 +77,49 @@ constexpr int kPiece = 8;                                   // columns classifie
 // lane quarter (atomic adds; lane l of a warp always hits bank l).
 constexpr int kHBins = kBins + 1;
 constexpr int kHRows = kTile;
+// Candidates of the multi-candidate certificate served by one pass.
+constexpr int kMaxCand = 4;
+
+// A JL-prefix candidate's verdict data, per epilogue warp.  Its pairs are
+// judged on r = |f(x_i) - f(x_j)|^2 / |x_i - x_j|^2: the distortion of Eq. 2
+// is |sqrt(r) - 1|, so it exceeds eps exactly when r lies outside
+// [(1 - eps)^2, (1 + eps)^2], and error bounds on the two squared distances
+// bound r without a square root or a division per pair.
+struct CandPartial {
+    float rmax_hi, rmax_lo;            // largest upper / lower bound on a pair's r
+    float rmin_lo, rmin_hi;            // smallest lower / upper bound on a pair's r
+    unsigned long long certain, open;  // pairs certainly beyond eps / on an open side
+};
 // Bound coefficient: with s = ex / dx2 + ey / dy2 <= 1/8 the square root of
 // the ratio moves by at most ((1 - s)^(-1/2) - 1) <= 0.5523 s relative; the
 // kernel carries ex, ey pre-multiplied by 0.56 (the row statistics' q4 by
 // sqrt(0.56), the (n2_i + n2_j) coefficients by 0.56).
 constexpr float kBoundCoef = 0.56f;
 constexpr float kCondMax = kBoundCoef * 0.125f;
+
+// JL-prefix candidates of one pass (the multi-candidate certificate): Y holds
+// the PCA part in its first py_chunks 64-column chunks and k JL columns after
+// it; candidate c keeps the first kc JL columns, scaled by sqrt(k / kc), and
+// is complete after Y chunk end[c].
+struct TcMulti {
+    int count;                 // candidates (0: none)
+    int py_chunks;             // Y chunks of the PCA part
+    int end[kMaxCand];         // last Y chunk of each candidate's prefix
+    float lam[kMaxCand];       // k / kc
+    // raw bound coefficients (rounded up): the (n2_i + n2_j) terms of the X
+    // side, the PCA part and the whole prefix, and 2^-24 for g - gP
+    float cxr, cypr, cycr[kMaxCand], u2r;
+    float kraw;                // 1 / 0.56 rounded up: raw q4 from the sqrt(0.56)-scaled ones
+    // thresholds on r (rounding slack included): certainly beyond eps when
+    // r > uv or r < lv, certainly within when lf <= r <= uf
+    float uv, lv, uf, lf;
+    long long n_pad;           // rows of each candidate's statistics
+    // [count][n_pad] interleaved by row pair (2q, 2q+1): element 2q = the two
+    // |yP|^2 and the two q4 of the PCA part, element 2q + 1 = the two |yJc|^2
+    // and the two q4 of the whole prefix (q4 times sqrt(0.56))
+    const ulonglong2 *cs;
+    CandPartial *out;          // [gridDim.x * kEpiWarps][count]
+};
 
 struct TcArgs {
     const float4 *rs;          // per row: (|xc|^2, |yc|^2, sqrt(0.56) q4x, sqrt(0.56) q4y)
@@ -105,13 +142,15 @@ struct TcArgs {
     float4 *dump;              // optional: (dx2, dy2, ex, ey) of 128 x 128 tile units
     long long dump_tiles;      // u = q * dump_stride, q < dump_tiles, into slot q
     long long dump_stride;
+    TcMulti multi;             // JL-prefix candidates (the multi-candidate kernel only)
 };
 
 // Shared-memory layout of one CTA.  The pair variant loads half of the J rows
 // per CTA, so its stages are smaller and there are four of them.
-template <bool PAIR>
+template <bool PAIR, bool MULTI = false>
 struct Layout {
-    static constexpr int kStages = PAIR ? 4 : 3;
+    // the multi-candidate kernel trades a stage for its per-thread verdict data
+    static constexpr int kStages = PAIR ? 4 : (MULTI ? 2 : 3);
     static constexpr int kBRows = PAIR ? kTile / 2 : kTile;                   // J rows loaded here
     static constexpr uint32_t kBPlane = kBRows * kKStep * 2;
     static constexpr uint32_t kStageBytes = 2 * kAPlane + 2 * kBPlane;
@@ -123,7 +162,8 @@ struct Layout {
     static constexpr uint32_t dec = cmd + 64;                                 // int [4]
     static constexpr uint32_t tmem_ptr = dec + 16;
     static constexpr uint32_t totals = tmem_ptr + 16;                         // WarpTotals [8]
-    static constexpr uint32_t total = totals + 64 * kEpiWarps;
+    static constexpr uint32_t cand = totals + 64 * kEpiWarps;                 // CandRun fields per thread
+    static constexpr uint32_t total = cand + (MULTI ? kMaxCand * (4 * 4 + 2 * 8) * 32 * kEpiWarps : 0);
     static constexpr size_t smem = total + 1024;                              // + alignment slack
     static_assert(smem <= 232448, "tile kernel exceeds the 227 KB shared-memory limit");
     static_assert(totals % 8 == 0, "per-warp totals need 8-byte alignment");
@@ -280,6 +320,115 @@ __device__ __forceinline__ f2 ffma2(f2 a, f2 b, f2 c) {
     return r;
 }
 
+// A JL-prefix candidate's running data in one epilogue thread while it
+// judges one tile row.  nrmh = -(largest upper bound on a pair's r) and rnl =
+// smallest lower bound, each in both lanes of a packed value; rml and rnh are
+// the other-side bounds of the pairs that set those records (lower bounds on
+// the largest distortion that some pair certainly has).
+struct CandRun {
+    f2 nrmh, rnl;
+    float rml, rnh;
+    unsigned certain, open;
+};
+// The row's statistics for one candidate, each twice: the X row's |xc|^2 and
+// q4 (times kraw, so the X bound comes out raw), the candidate's |yP|^2,
+// PCA-part q4, |yJc|^2 and whole-prefix q4.
+struct CandRow {
+    f2 nx, qx, nP, qP, nJ, qT;
+};
+// The candidate's constants, each twice.
+struct CandK {
+    f2 m2sx, m2sy, cxr, lam, cypr, cyc, u2r, nuf, lf;
+};
+
+// Entry c of a candidate array in the kernel parameters, read with constant
+// indices (a computed index would copy the parameters to local memory).
+template <typename T>
+__device__ __forceinline__ T cand_sel(const T (&v)[kMaxCand], int c) {
+    static_assert(kMaxCand == 4, "cand_sel selects among four");
+    return c == 0 ? v[0] : (c == 1 ? v[1] : (c == 2 ? v[2] : v[3]));
+}
+
+// Bounds xl <= dx2 <= xh and yl <= dy2 <= yh of two pairs (columns j, j + 1
+// of one row) under one candidate, yl returned negated.  gx, gP, g: the
+// pairs' X Gram sums, PCA-part Y sums and running prefix sums; xa, xb: the
+// columns' pair-interleaved X statistics (|xc|^2 pair, q4x pair); ca, cb: the
+// candidate's.  dy2 = dP + lam dJ with dP from gP and dJ from g - gP; its
+// error bound eP + lam (eT + eP + u2 sT) takes the PCA part's bound eP, the
+// whole prefix's eT (the error of g) and the rounding of g - gP.
+__device__ __forceinline__ void cand_bounds2(f2 gx, f2 gP, f2 g, const CandRow &ri, const ulonglong2 xa,
+                                             const ulonglong2 xb, const ulonglong2 ca, const ulonglong2 cb,
+                                             const CandK &K, f2 &xl, f2 &xh, f2 &yh, f2 &nyl) {
+    const f2 sx = fadd2(ri.nx, xa.x);
+    const f2 dx2 = ffma2(K.m2sx, gx, sx);
+    const f2 ex = ffma2(ri.qx, xb.x, fmul2(K.cxr, sx));
+    const f2 sP = fadd2(ri.nP, ca.x), sJ = fadd2(ri.nJ, cb.x), sT = fadd2(sP, sJ);
+    const f2 dP = ffma2(K.m2sy, gP, sP);
+    const f2 dJ = ffma2(K.m2sy, fsub2(g, gP), sJ);
+    const f2 dy2 = ffma2(K.lam, dJ, dP);
+    const f2 eP = ffma2(ri.qP, ca.y, fmul2(K.cypr, sP));
+    const f2 eT = ffma2(ri.qT, cb.y, fmul2(K.cyc, sT));
+    const f2 ey = ffma2(K.lam, ffma2(K.u2r, sT, fadd2(eT, eP)), eP);
+    xl = fsub2(dx2, ex);
+    xh = fadd2(dx2, ex);
+    yh = fadd2(dy2, ey);
+    nyl = fsub2(ey, dy2);
+}
+
+// The distortion of Eq. 2 is |sqrt(r) - 1| for r = dy2 / dx2, so a pair with
+// xl > 0 certainly stays within eps when yh <= uf xl and yl >= lf xh
+// ((1 + eps)^2 and (1 - eps)^2 with 32 units of rounding slack).  The common
+// path tests that and the two running records of r with four fused
+// multiply-adds per pair (each sign exact): 2 bits per column pair, set where
+// a valid pair needs the full test.
+__device__ __forceinline__ unsigned cand_fast2(f2 xl, f2 xh, f2 yh, f2 nyl, bool v0, bool v1, const CandK &K,
+                                               const CandRun &a) {
+    const f2 C = ffma2(K.nuf, xl, yh);      // yh - uf xl
+    const f2 D = ffma2(K.lf, xh, nyl);      // lf xh - yl
+    const f2 E1 = ffma2(a.nrmh, xl, yh);    // yh - rmh xl
+    const f2 E3 = ffma2(a.rnl, xh, nyl);    // rnl xh - yl
+    float c0, c1, d0, d1, e0, e1, f0, f1;
+    upk2(C, c0, c1);
+    upk2(D, d0, d1);
+    upk2(E1, e0, e1);
+    upk2(E3, f0, f1);
+    // a NaN (only from 0 x inf) compares false below and goes to the full test
+    const bool ok0 = (c0 <= 0.0f) & (d0 <= 0.0f) & (e0 <= 0.0f) & (f0 <= 0.0f);
+    const bool ok1 = (c1 <= 0.0f) & (d1 <= 0.0f) & (e1 <= 0.0f) & (f1 <= 0.0f);
+    return (v0 & !ok0 ? 1u : 0u) | (v1 & !ok1 ? 2u : 0u);
+}
+
+// The full test of one pair: it certainly exceeds eps when yl > uv xh or
+// yh < lv xl, certainly does not when the common-path conditions hold, and is
+// open otherwise; a pair with xl <= 0 (possibly x_i == x_j, which the
+// certificate excludes) stays open and leaves the largest r unbounded.
+__device__ __forceinline__ void cand_slow(float xl, float xh, float yh, float nyl, const TcMulti &m,
+                                          CandRun &a) {
+    const float yl = -nyl;
+    const bool pos = xl > 0.0f;
+    const bool viol = pos & ((fmaf(-m.uv, xh, yl) > 0.0f) | (fmaf(m.lv, xl, -yh) > 0.0f));
+    const bool fine = pos & (fmaf(-m.uf, xl, yh) <= 0.0f) & (fmaf(m.lf, xh, -yl) <= 0.0f);
+    a.certain += viol ? 1u : 0u;
+    a.open += (!viol & !fine) ? 1u : 0u;
+    float nrmh, rnl, u;
+    upk2(a.nrmh, nrmh, u);
+    upk2(a.rnl, rnl, u);
+    if (!pos) {
+        nrmh = -INFINITY;
+    } else {
+        if (fmaf(nrmh, xl, yh) > 0.0f) {  // a new largest upper bound
+            nrmh = fminf(nrmh, -__fdiv_ru(yh, xl));
+            a.rml = fmaxf(a.rml, __fdiv_rd(yl, xh));
+        }
+        if (fmaf(rnl, xh, -yl) > 0.0f) {  // a new smallest lower bound
+            rnl = fminf(rnl, fmaxf(__fdiv_rd(yl, xh), 0.0f));
+            a.rnh = fminf(a.rnh, __fdiv_ru(yh, xl));
+        }
+    }
+    a.nrmh = pk2(nrmh, nrmh);
+    a.rnl = pk2(rnl, rnl);
+}
+
 // The row's statistics and the kernel constants, each twice (one per lane of
 // a packed value).
 struct RowPk {
@@ -382,14 +531,14 @@ __device__ __forceinline__ void classify_piece(const float (&gx)[kPiece], const 
 }
 
 // ---------------------------------------------------------------- the kernel
-template <bool DUMP, bool PAIR, bool STD>
+template <bool DUMP, bool PAIR, bool STD, bool MULTI = false>
 __global__ void __launch_bounds__(kThreads, 1)
     cert_tc_kernel(const __grid_constant__ CUtensorMap map_xh, const __grid_constant__ CUtensorMap map_xl,
                    const __grid_constant__ CUtensorMap map_yh, const __grid_constant__ CUtensorMap map_yl,
                    const __grid_constant__ CUtensorMap bmap_xh, const __grid_constant__ CUtensorMap bmap_xl,
                    const __grid_constant__ CUtensorMap bmap_yh, const __grid_constant__ CUtensorMap bmap_yl,
                    TcArgs p) {
-    using L = Layout<PAIR>;
+    using L = Layout<PAIR, MULTI>;
     constexpr int kStages = L::kStages;
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     // 1024-byte alignment of the stage buffers (128-byte swizzle atoms), by
@@ -850,6 +999,127 @@ __global__ void __launch_bounds__(kThreads, 1)
         const long long tstep = PAIR ? (long long)ncluster_x() : (long long)gridDim.x;
         uint32_t nxt_packed = t < p.ntp ? __ldg(p.sched + t) : 0u;
         bool ok = true;
+        // the JL-prefix candidates' verdict data (multi-candidate kernel): per
+        // epilogue thread and candidate in shared memory, field f of
+        // candidate c at [(c * F + f) * 256 + et]: -rmax_hi, rmax_lo,
+        // rmin_lo, rmin_hi (CandRun), then the two counts
+        const int et = ew * 32 + lane;
+        float *s_cr = reinterpret_cast<float *>(smem + L::cand);  // rmh, rml, rnl, rnh
+        unsigned long long *s_cn =
+            reinterpret_cast<unsigned long long *>(smem + L::cand + kMaxCand * 4 * 32 * kEpiWarps * 4);
+        if constexpr (MULTI) {
+            for (int c = 0; c < p.multi.count; ++c) {
+                s_cr[(c * 4 + 0) * 32 * kEpiWarps + et] = 0.0f;
+                s_cr[(c * 4 + 1) * 32 * kEpiWarps + et] = 0.0f;
+                s_cr[(c * 4 + 2) * 32 * kEpiWarps + et] = INFINITY;
+                s_cr[(c * 4 + 3) * 32 * kEpiWarps + et] = INFINITY;
+                s_cn[(c * 2 + 0) * 32 * kEpiWarps + et] = 0ull;
+                s_cn[(c * 2 + 1) * 32 * kEpiWarps + et] = 0ull;
+            }
+        }
+        // every pair of this thread's row of the current tile under candidate
+        // c: the tile's X sums and PCA-part sums are in the staging and running
+        // columns, its running Y sums in the TMEM columns at tg
+        auto cand_check = [&](int c, uint32_t tg, uint32_t packed, int ib, float4 ri) {
+            const TcMulti &m = p.multi;
+            const int J = (int)(packed & 0xFFFF);
+            const int i = ib * kTile + r;
+            const int j0 = J * kTile + col0;
+            const bool full = (ib < J) && (J * kTile + kTile <= p.n);
+            const ulonglong2 *cs = m.cs + (size_t)c * (size_t)m.n_pad;
+            const float lam_c = cand_sel(m.lam, c), cyc_c = cand_sel(m.cycr, c);
+            CandRow cr;
+            {
+                const ulonglong2 a = __ldg(cs + (i & ~1)), b = __ldg(cs + (i | 1));
+                float v0, v1;
+                const bool odd = (i & 1) != 0;
+                upk2(a.x, v0, v1);
+                cr.nP = pk2(odd ? v1 : v0, odd ? v1 : v0);
+                upk2(a.y, v0, v1);
+                cr.qP = pk2(odd ? v1 : v0, odd ? v1 : v0);
+                upk2(b.x, v0, v1);
+                cr.nJ = pk2(odd ? v1 : v0, odd ? v1 : v0);
+                upk2(b.y, v0, v1);
+                cr.qT = pk2(odd ? v1 : v0, odd ? v1 : v0);
+                cr.nx = pk2(ri.x, ri.x);
+                const float qx = __fmul_ru(ri.z, m.kraw);
+                cr.qx = pk2(qx, qx);
+            }
+            const int base = c * 4 * 32 * kEpiWarps + et;
+            CandRun a;
+            {
+                const float f0 = s_cr[base], f2v = s_cr[base + 64 * kEpiWarps];
+                a.nrmh = pk2(f0, f0);
+                a.rnl = pk2(f2v, f2v);
+                a.rml = s_cr[base + 32 * kEpiWarps];
+                a.rnh = s_cr[base + 96 * kEpiWarps];
+                a.certain = a.open = 0u;
+            }
+            CandK K;
+            K.m2sx = pk2(k.m2sx, k.m2sx);
+            K.m2sy = pk2(k.m2sy, k.m2sy);
+            K.cxr = pk2(m.cxr, m.cxr);
+            K.lam = pk2(lam_c, lam_c);
+            K.cypr = pk2(m.cypr, m.cypr);
+            K.cyc = pk2(cyc_c, cyc_c);
+            K.u2r = pk2(m.u2r, m.u2r);
+            K.nuf = pk2(-m.uf, -m.uf);
+            K.lf = pk2(m.lf, m.lf);
+#pragma unroll
+            for (int pc = 0; pc < NP; ++pc) {
+                uint32_t ux[kPiece], uy[kPiece], ug[kPiece];
+                tmem_ld8x3_wait(gx_stage + pc * kPiece, gy_run + pc * kPiece, tg + pc * kPiece, ux, uy, ug);
+                // the piece's pairs on the common path, branch-free; the
+                // few that need the full test are redone below
+                unsigned flag = 0u;
+#pragma unroll
+                for (int q = 0; q < kPiece; q += 2) {
+                    const int cc = pc * kPiece + q;
+                    const int j = j0 + cc;
+                    const bool v0 = full || ((i < j) && (j < p.n));
+                    const bool v1 = full || ((i < j + 1) && (j + 1 < p.n));
+                    f2 xl, xh, yh, nyl;
+                    cand_bounds2(pk2(__uint_as_float(ux[q]), __uint_as_float(ux[q + 1])),
+                                 pk2(__uint_as_float(uy[q]), __uint_as_float(uy[q + 1])),
+                                 pk2(__uint_as_float(ug[q]), __uint_as_float(ug[q + 1])), cr, __ldg(p.rs2 + j), __ldg(p.rs2 + j + 1), __ldg(cs + j), __ldg(cs + j + 1), K,
+                                 xl, xh, yh, nyl);
+                    flag |= cand_fast2(xl, xh, yh, nyl, v0, v1, K, a) << q;
+                }
+                if (__any_sync(0xffffffffu, flag != 0u)) {
+#pragma unroll
+                    for (int q = 0; q < kPiece; q += 2) {
+                        if (flag & (3u << q)) {
+                            const int cc = pc * kPiece + q;
+                            const int j = j0 + cc;
+                            f2 xl, xh, yh, nyl;
+                            cand_bounds2(pk2(__uint_as_float(ux[q]), __uint_as_float(ux[q + 1])),
+                                         pk2(__uint_as_float(uy[q]), __uint_as_float(uy[q + 1])),
+                                         pk2(__uint_as_float(ug[q]), __uint_as_float(ug[q + 1])), cr,
+                                         __ldg(p.rs2 + j), __ldg(p.rs2 + j + 1),
+                                         __ldg(cs + j), __ldg(cs + j + 1), K, xl, xh, yh, nyl);
+                            float l0, l1, h0, h1, y0, y1, n0, n1;
+                            upk2(xl, l0, l1);
+                            upk2(xh, h0, h1);
+                            upk2(yh, y0, y1);
+                            upk2(nyl, n0, n1);
+                            if (flag & (1u << q)) cand_slow(l0, h0, y0, n0, m, a);
+                            if (flag & (2u << q)) cand_slow(l1, h1, y1, n1, m, a);
+                        }
+                    }
+                }
+            }
+            {
+                float f0, u;
+                upk2(a.nrmh, f0, u);
+                s_cr[base] = f0;
+                s_cr[base + 32 * kEpiWarps] = a.rml;
+                upk2(a.rnl, f0, u);
+                s_cr[base + 64 * kEpiWarps] = f0;
+                s_cr[base + 96 * kEpiWarps] = a.rnh;
+                s_cn[(c * 2 + 0) * 32 * kEpiWarps + et] += a.certain;
+                s_cn[(c * 2 + 1) * 32 * kEpiWarps + et] += a.open;
+            }
+        };
         // this warp's NC sums into TMEM columns starting at `dst`
         auto park = [&](const float (&v)[NC], uint32_t dst) {
 #pragma unroll
@@ -896,6 +1166,16 @@ __global__ void __launch_bounds__(kThreads, 1)
                     // parked there and the registers take the Y sums
                     if (pend) finish_pending();
                     park(g, gx_stage);
+                    if constexpr (MULTI) {
+                        // the column statistics the candidates' checks read
+                        // (8 lines of 128 bytes each per array), into L1
+                        // while the PCA chunks are computed
+                        const int jp = (int)(cur_packed & 0xFFFF) * kTile + col0 + (lane & 7) * 8;
+                        if (lane < 8) asm volatile("prefetch.global.L1 [%0];" ::"l"(p.rs2 + jp));
+                        if ((lane >> 3) < p.multi.count)
+                            asm volatile("prefetch.global.L1 [%0];" ::"l"(p.multi.cs + (size_t)(lane >> 3) *
+                                                                                     (size_t)p.multi.n_pad + jp));
+                    }
 #pragma unroll
                     for (int c = 0; c < NC; ++c) g[c] = 0.0f;
                 }
@@ -907,6 +1187,30 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tmem_ld_cols(ta, v);
 #pragma unroll
                     for (int c = 0; c < NC; c += 2) add2_f32(g[c], g[c + 1], v[c], v[c + 1]);
+                }
+                if constexpr (MULTI) {
+                    if (ks >= p.kx_steps) {
+                        const int yc = ks - p.kx_steps;
+                        // the PCA part's Gram sums, kept beside the running ones
+                        if (yc + 1 == p.multi.py_chunks) park(g, gy_run);
+                        bool due = false;
+                        for (int c = 0; c < p.multi.count; ++c) due |= yc == cand_sel(p.multi.end, c);
+                        if (due) {
+                            // the running sums go to this warp's columns of the
+                            // drained slot (released only after the checks), so
+                            // the checks run with their registers free
+                            park(g, ta);
+                            // one call site: the check is large, and its copies
+                            // would crowd the instruction cache
+#pragma unroll 1
+                            for (int c = 0; c < p.multi.count; ++c)
+                                if (yc == cand_sel(p.multi.end, c)) cand_check(c, ta, cur_packed, cur_ib, cur_ri);
+                            uint32_t v[NC];
+                            tmem_ld_cols(ta, v);
+#pragma unroll
+                            for (int c = 0; c < NC; ++c) g[c] = __uint_as_float(v[c]);
+                        }
+                    }
                 }
                 // the slot is drained: one arrival per warp (a pair: on the
                 // leader's barrier)
@@ -972,6 +1276,32 @@ __global__ void __launch_bounds__(kThreads, 1)
             mine->argmax_i = wt->argmax_i;
             mine->argmax_j = wt->argmax_j;
         }
+        if constexpr (MULTI) {
+            for (int c = 0; c < p.multi.count; ++c) {
+                const int base = c * 4 * 32 * kEpiWarps + et;
+                float rmh = -s_cr[base], rml = s_cr[base + 32 * kEpiWarps];
+                float rnl = s_cr[base + 64 * kEpiWarps], rnh = s_cr[base + 96 * kEpiWarps];
+                unsigned long long ce = s_cn[(c * 2 + 0) * 32 * kEpiWarps + et];
+                unsigned long long op = s_cn[(c * 2 + 1) * 32 * kEpiWarps + et];
+                for (int o = 16; o > 0; o >>= 1) {
+                    rmh = fmaxf(rmh, __shfl_xor_sync(0xffffffffu, rmh, o));
+                    rml = fmaxf(rml, __shfl_xor_sync(0xffffffffu, rml, o));
+                    rnl = fminf(rnl, __shfl_xor_sync(0xffffffffu, rnl, o));
+                    rnh = fminf(rnh, __shfl_xor_sync(0xffffffffu, rnh, o));
+                    ce += __shfl_xor_sync(0xffffffffu, ce, o);
+                    op += __shfl_xor_sync(0xffffffffu, op, o);
+                }
+                if (lane == 0) {
+                    CandPartial &cp = p.multi.out[((size_t)blockIdx.x * kEpiWarps + ew) * p.multi.count + c];
+                    cp.rmax_hi = rmh;
+                    cp.rmax_lo = rml;
+                    cp.rmin_lo = rnl;
+                    cp.rmin_hi = rnh;
+                    cp.certain = ce;
+                    cp.open = op;
+                }
+            }
+        }
             };
         if constexpr (kEpiWarps == 8) {
             epilogue(std::integral_constant<int, 64>{});
@@ -1020,6 +1350,53 @@ __global__ void pack_row_stats(const RowStat *__restrict__ rx, const RowStat *__
     e[6] = v.w;
 }
 
+// Row statistics of the JL-prefix candidates (TcMulti::cs): row r of Y,
+// centred by the preparation's column means in FP32 like the split planes, in
+// FP64 sums: the PCA part's squared norm and 4-norm coefficient, and per
+// candidate the squared norm of its JL prefix and the 4-norm coefficient of
+// the whole prefix (PCA part and JL prefix), q4 = sqrt(2 c4) ||.||_4 (rounded
+// up).  Written interleaved by row pair; rows past n get zeros.
+__global__ void cand_stats_kernel(const float *__restrict__ Y, int64_t n, int64_t n_pad, int64_t ldy,
+                                  const float *__restrict__ mu, int s, int jo, int count, int4 kc4,
+                                  double q4scale, float *__restrict__ cs) {
+    const int lane = threadIdx.x & 31;
+    const int64_t r = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= n_pad) return;
+    const int kc[4] = {kc4.x, kc4.y, kc4.z, kc4.w};
+    double p2 = 0.0, p4 = 0.0;
+    if (r < n)
+        for (int c = lane; c < s; c += 32) {
+            const double v = __fsub_rn(Y[r * ldy + c], mu[c]);
+            p2 = fma(v, v, p2);
+            p4 = fma(v * v, v * v, p4);
+        }
+    for (int o = 16; o > 0; o >>= 1) {
+        p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+        p4 += __shfl_xor_sync(0xffffffffu, p4, o);
+    }
+    for (int q = 0; q < count; ++q) {
+        double j2 = 0.0, j4 = 0.0;
+        if (r < n)
+            for (int t = lane; t < kc[q]; t += 32) {
+                const double v = __fsub_rn(Y[r * ldy + jo + t], mu[jo + t]);
+                j2 = fma(v, v, j2);
+                j4 = fma(v * v, v * v, j4);
+            }
+        for (int o = 16; o > 0; o >>= 1) {
+            j2 += __shfl_xor_sync(0xffffffffu, j2, o);
+            j4 += __shfl_xor_sync(0xffffffffu, j4, o);
+        }
+        if (lane == 0) {
+            // element 2q' (two floats per field) holds rows 2q', 2q' + 1
+            float *e = cs + (int64_t)q * n_pad * 4 + (r & ~1ll) * 4 + (r & 1);
+            e[0] = (float)p2;
+            e[2] = __double2float_ru(q4scale * sqrt(sqrt(p4)));
+            e[4] = (float)j2;
+            e[6] = __double2float_ru(q4scale * sqrt(sqrt(p4 + j4)));
+        }
+    }
+}
+
 // Band orders of the upper triangle.  Single: bands of `band` tile rows; in a
 // band, J runs left to right and I over the band's rows with I <= J, so the
 // band's I tiles stay in L2 while the J tiles stream.  Pair: tiles of 256 I
@@ -1061,6 +1438,7 @@ void cert_tc_init() {
     set_max_dyn_smem((const void *)cert_tc_kernel<true, true, true>, (int)Layout<true>::smem);
     set_max_dyn_smem((const void *)cert_tc_kernel<false, true, true>, (int)Layout<true>::smem);
     set_max_dyn_smem((const void *)cert_tc_kernel<false, true, false>, (int)Layout<true>::smem);
+    set_max_dyn_smem((const void *)cert_tc_kernel<false, false, true, true>, (int)Layout<false, true>::smem);
 }
 
 static cudaLaunchConfig_t pair_config(unsigned ctas, cudaStream_t st, cudaLaunchAttribute *at) {
@@ -1189,9 +1567,10 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     if (!x.hi || !y.hi) return false;
     if (x.n_pad / kTile >= 65536) return false;
     TileConfig cfg = tc_config(L.ctx, x.n);
-    // a shard runs the single-CTA kernel over its own tiles
+    // a shard, and the multi-candidate pass, run the single-CTA kernel
     const bool sharded = L.t_end >= 0;
-    if (sharded) cfg.variant = 1;
+    const bool multi = L.multi && L.multi->count > 0;
+    if (sharded || multi) cfg.variant = 1;
     const bool pair = cfg.variant == 2;
     if (pair && (x.n_pad % (2 * kTile) != 0 || y.n_pad != x.n_pad))
         fail(ADAGIO_E_CUDA, "internal: pair tiles need rows padded to 256 (n_pad %lld)",
@@ -1263,6 +1642,50 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
     const bool std_range = L.cc.lo == 0.0f && eb >= 1 && eb <= kBins && std::fabs(te - (double)eb) <= 1e-6;
     a.eps_bin = std_range ? (int)eb : kBins;
     if (L.dump && !std_range) fail(ADAGIO_E_CUDA, "internal: the per-pair dump needs the standard range");
+    a.multi = TcMulti{};
+    if (multi) {
+        const MultiSpec &ms = *L.multi;
+        if (!std_range || L.dump || sharded || !L.ysrc)
+            fail(ADAGIO_E_CUDA, "internal: the multi-candidate pass needs the standard range, whole");
+        TcMulti &mt = a.multi;
+        mt.count = ms.count;
+        mt.py_chunks = ms.s_pad / kKStep;
+        // raw coefficients, rounded up: the same error model as the pair
+        // bound of the full certificate, without its 0.56 linearisation factor
+        const double cr = L.cc.c_r;
+        auto up = [](double v) { return std::nextafter((float)v, INFINITY); };
+        mt.cxr = up((double)x.bm.cacc + cr);
+        mt.cypr = up((double)bound_model(precision, ms.s_pad).cacc + cr);
+        for (int c = 0; c < kMaxCand; ++c) {
+            mt.end[c] = 0;
+            mt.lam[c] = 1.0f;
+            mt.cycr[c] = 0.0f;
+        }
+        for (int c = 0; c < ms.count; ++c) {
+            mt.end[c] = (ms.jo + ms.kc[c] - 1) / kKStep;
+            mt.lam[c] = (float)ms.k / (float)ms.kc[c];
+            mt.cycr[c] = up((double)bound_model(precision, (mt.end[c] + 1) * kKStep).cacc + cr);
+        }
+        mt.u2r = up(5.9604645e-08);
+        mt.kraw = up(1.0 / (double)kBoundCoef);
+        // thresholds on r from the caller's eps in FP64, with 32 units of
+        // slack for the roundings of the bounds and of these products
+        const double e1 = (1.0 + ms.eps) * (1.0 + ms.eps), e0 = (1.0 - ms.eps) * (1.0 - ms.eps);
+        const double sl = 32.0 * 5.9604645e-08;
+        mt.uv = up(e1 * (1.0 + sl));
+        mt.lv = std::nextafter((float)(e0 * (1.0 - sl)), 0.0f);
+        mt.uf = std::nextafter((float)(e1 * (1.0 - sl)), 0.0f);
+        mt.lf = up(e0 * (1.0 + sl));
+        mt.cs = reinterpret_cast<const ulonglong2 *>(ms.cs);
+        mt.out = reinterpret_cast<CandPartial *>(ms.out);
+        mt.n_pad = y.n_pad;
+        const int4 kc4 = make_int4(ms.kc[0], ms.kc[1], ms.kc[2], ms.kc[3]);
+        const double q4scale = std::sqrt(2.0 * (double)y.bm.c4) * (1.0 + 1e-6);
+        cand_stats_kernel<<<(unsigned)ceil_div(y.n_pad, 8), 256, 0, st>>>(
+            L.ysrc, y.n, y.n_pad, L.ldy_src, y.mu, ms.s, ms.jo, ms.count, kc4, q4scale,
+            reinterpret_cast<float *>(ms.cs));
+        ADAGIO_CHECK_LAUNCH();
+    }
     ADAGIO_CUDA(cudaMemsetAsync(L.partials, 0, sizeof(CertPartial) * L.grid, st));
     cert_tc_init();
     const unsigned ctas = (unsigned)(L.grid / kEpiWarps);
@@ -1280,7 +1703,10 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
                                            bxl, byh, byl, a));
     } else {
         const size_t sm = Layout<false>::smem;
-        if (L.dump)
+        if (multi)
+            cert_tc_kernel<false, false, true, true><<<ctas, kThreads, Layout<false, true>::smem, st>>>(
+                mxh, mxl, myh, myl, bxh, bxl, byh, byl, a);
+        else if (L.dump)
             cert_tc_kernel<true, false, true><<<ctas, kThreads, sm, st>>>(mxh, mxl, myh, myl, bxh, bxl, byh,
                                                                           byl, a);
         else if (std_range)
