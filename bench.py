@@ -48,11 +48,15 @@ M_REF = 421
 ORACLE_SHARDS = 15
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one tile-kernel
-# launch on this workload, from one ncu capture of the full launch
-# (ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum -k regex:cert_tc_kernel
-# -c 1 python -m paper_1609_05388_gb300.profile_cert --n 60000 --m 421 --reps 1),
-# or None once the kernel has changed since.
-TRAFFIC_BYTES = None
+# launch on this workload (single-CTA tiles), by schedule band, each from one
+# ncu capture of the full launch:
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum
+#       --clock-control none -k regex:cert_tc_kernel -c 1
+#       python -m paper_1609_05388_gb300.profile_cert --n 60000 --m 421 --reps 1
+#       --tiles single --band B
+# The traffic depends on the sizes and the schedule only.  A configuration
+# without a capture (or a kernel changed since) reports null.
+TRAFFIC_BYTES = {(1, 4): 15.42e9, (1, 8): 9.32e9, (1, 16): 7.49e9}
 
 
 def workload_config():
@@ -277,6 +281,31 @@ def knn_leg(ctx, Y, peak, k=30):
             "rows_searched_exactly": ctx.knn_last_exact_rows()}
 
 
+def prefix_leg(ctx, X, Y, s, m, eps, reps=2):
+    """The multi-candidate certificate on the returned map: its own
+    certificate plus the verdicts of the JL prefixes k, k - 64, k - 128,
+    k - 192 in one pass, against one plain certificate of the map."""
+    import torch
+    k = m - s
+    kcs = [kc for kc in (k, k - 64, k - 128, k - 192) if kc >= 1]
+    ctx.set_timing(True)
+    t_multi, t_one = [], []
+    for _ in range(reps):
+        full, res = ctx.distortion_prefixes(X, Y, s, eps, kcs)
+        t_multi.append(ctx.last_cert_stats()["tile_ms"])
+        ctx.distortion(X, Y, eps)
+        t_one.append(ctx.last_cert_stats()["tile_ms"])
+    ctx.set_timing(False)
+    torch.cuda.synchronize()
+    return {"workload": f"JL prefixes {kcs} of the returned map (s={s}, k={k}) in one pass",
+            "tile_ms": min(t_multi), "tile_ms_plain_certificate": min(t_one),
+            "full_max": full.max,
+            "prefixes": [{"k": r["k"], "m": s + r["k"], "verdict": r["verdict"],
+                          "max_interval": [r["max_lower"], r["max_upper"]],
+                          "certain_violations": r["certain_violations"],
+                          "unsettled_pairs": r["unsettled_pairs"]} for r in res]}
+
+
 def large_leg(ctx, lib, peak, prec):
     """The 200 000 x 2048 workload (power-law spectrum, 5 % Laplace outliers):
     one exhaustive certificate (2.0e10 pairs) of a JL map of 300 rows."""
@@ -468,7 +497,8 @@ def main():
         roof = {"bound": "tensor", "peak_source": f"bf16_tflops ({peak_src})"}
     achieved = flops / (tile_ms / 1e3) / 1e12
     roof.update({"achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                 "traffic": TRAFFIC_BYTES, "kernel_ms": tile_ms,
+                 "traffic": TRAFFIC_BYTES.get((tile_cfg["variant"], tile_cfg["band"])) if tile_cfg else None,
+                 "kernel_ms": tile_ms,
                  "algorithmic_flops_per_launch": flops,
                  "queued_pairs": cst["queued"]})
     if prec != lib.PREC_FP32:
@@ -513,6 +543,7 @@ def main():
                                    "achieved_tflops": ach, "frac": fr, "max": cb.max,
                                    "certificate_pairs_per_s": pairs / ((bt + br) / 1e3)}
         legs["knn_graph_k30"] = knn_leg(ctx, Y, peak)
+        legs["prefixes"] = prefix_leg(ctx, X, Y, s, m, EPS)
         del Y
         torch.cuda.empty_cache()
         legs["large_200000x2048"] = large_leg(ctx, lib, peak, prec)

@@ -1065,7 +1065,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             K.u2r = pk2(m.u2r, m.u2r);
             K.nuf = pk2(-m.uf, -m.uf);
             K.lf = pk2(m.lf, m.lf);
-#pragma unroll
+            // pieces in a loop, not unrolled: the check's code stays small
+            // enough for the instruction cache beside the main epilogue
+#pragma unroll 1
             for (int pc = 0; pc < NP; ++pc) {
                 uint32_t ux[kPiece], uy[kPiece], ug[kPiece];
                 tmem_ld8x3_wait(gx_stage + pc * kPiece, gy_run + pc * kPiece, tg + pc * kPiece, ux, uy, ug);
