@@ -80,6 +80,8 @@ def parse():
     p.add_argument("--no-plain", action="store_true")
     p.add_argument("--no-predictor", action="store_true",
                    help="time the plain search as the headline step")
+    p.add_argument("--predictor", default="",
+                   help="dimension predictor weights (default: the shipped MNIST-shaped one)")
     return p.parse_args()
 
 
@@ -417,7 +419,7 @@ def main():
 
     learned = 0 if args.no_predictor else 1
     if learned:
-        ctx.mlp_load(PREDICTOR)
+        ctx.mlp_load(args.predictor or PREDICTOR)
 
     def step(precision, use_predictor=learned, Xin=X):
         return ctx.fit(Xin, eps=EPS, m_cap=d, seed=11, precision=precision,
@@ -563,7 +565,7 @@ def main():
                        "doubling 16,32,64,... then bisection") +
                       "; failing probes stop at the first certain violation",
             "tile_config": tile_cfg,
-            "predictor": os.path.basename(PREDICTOR) if learned else None,
+            "predictor": os.path.basename(args.predictor or PREDICTOR) if learned else None,
             "time_to_certified_embedding_s": ms / 1e3,
             "result": {"m": m, "s": s, "max": cert.max, "mean": cert.mean,
                        "violations": cert.violations, "recomputed": cert.recomputed,

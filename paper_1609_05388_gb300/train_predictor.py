@@ -1,6 +1,7 @@
 """Trains the dimension predictor on instances labelled by the certified search.
 
-    python -m paper_1609_05388_gb300.train_predictor --instances 2048 --out predictor.bin
+    python -m paper_1609_05388_gb300.train_predictor --instances 2048 --out predictor.bin \
+        [--record predictor.json] [--save-data labels.npz]
 
 Instances come from the MNIST-shaped family (synth.mnist_like_family: rank,
 cluster count, sparsity and eps vary) with n log-uniform in [n_lo, n_hi].
@@ -11,7 +12,9 @@ Instances that are not certifiable at m = d carry no label and are dropped.
 The network is trained full-batch with Adam on y = log m; the last
 `--holdout` instances are kept out of training and reported.  Synthetic data
 is generated by a pool of worker processes (started with `spawn`, before the
-first GPU call) while the GPU labels the previous batch.
+first GPU call) while the GPU labels the previous batch.  --record writes the
+training record (instance counts, timings, holdout errors) as JSON beside the
+weights; --save-data keeps the labelled features.
 """
 from __future__ import annotations
 
@@ -43,6 +46,8 @@ def main():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--workers", type=int, default=12)
     ap.add_argument("--out", required=True)
+    ap.add_argument("--record", default="", help="write the training record (JSON) here")
+    ap.add_argument("--save-data", default="", help="save the labelled features (npz) here")
     a = ap.parse_args()
     pool = mp.get_context("spawn").Pool(a.workers)
     jobs = [(a.seed * 1_000_003 + k, a.n_lo, a.n_hi) for k in range(a.instances)]
@@ -75,6 +80,8 @@ def main():
         pool.close()
         F = np.array(feats, dtype=np.float32)
         t = np.array(labels, dtype=np.float32)
+        if a.save_data:
+            np.savez_compressed(a.save_data, feats=F, log_m=t, n=np.array(ns))
         N = len(t)
         tr = slice(0, N - a.holdout)
         ho = slice(N - a.holdout, N)
@@ -87,12 +94,19 @@ def main():
         m_pred = np.ceil(1.05 * np.exp(y))
         m_true = np.exp(t[ho].astype(np.float64))
         ctx.mlp_save(a.out)
-    print(json.dumps({"instances": a.instances, "labelled": N, "dropped_not_certifiable": dropped,
-                      "label_seconds": label_s, "gpu_label_seconds": gpu_s, "train_loss": loss,
-                      "holdout": a.holdout,
-                      "holdout_mean_abs_log_err": float(np.mean(np.abs(y - t[ho]))),
-                      "holdout_mean_ratio_pred_over_true": float(np.mean(m_pred / m_true)),
-                      "holdout_under_predicted": int(np.sum(m_pred < m_true))}))
+    rec = {"family": "synth.mnist_like_family", "n_range": [a.n_lo, a.n_hi], "seed": a.seed,
+           "instances": a.instances, "labelled": N, "dropped_not_certifiable": dropped,
+           "label": "dimension returned by the plain certified search (FP16x3 tiles)",
+           "label_seconds": label_s, "gpu_label_seconds": gpu_s, "adam_steps": a.steps,
+           "train_loss": loss, "holdout": a.holdout,
+           "holdout_mean_abs_log_err": float(np.mean(np.abs(y - t[ho]))),
+           "holdout_mean_ratio_pred_over_true": float(np.mean(m_pred / m_true)),
+           "holdout_under_predicted": int(np.sum(m_pred < m_true)),
+           "prediction_rule": "m = ceil(1.05 exp(y))"}
+    if a.record:
+        with open(a.record, "w") as f:
+            json.dump(rec, f, indent=1)
+    print(json.dumps(rec))
 
 
 if __name__ == "__main__":
