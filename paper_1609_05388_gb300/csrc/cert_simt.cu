@@ -34,17 +34,30 @@ struct SimtArgs {
     long long dump_stride;  // tile pairs t = q * dump_stride, q < dump_tiles, into slot q
 };
 
-// acc[a][b] += rows(I) . rows(J) over K, for the thread's 8 x 8 block.
-__device__ __forceinline__ void gram_tile(const float *__restrict__ M, int ld, int K, int rowI,
-                                          int rowJ, float (*As)[BK][BM + PADS],
-                                          float (*Bs)[BK][BM + PADS], float acc[8][8]) {
+// Chunk of the FP32 accumulation: FMA chains of kChunk terms, each added into
+// the running sum.  A chain's rounding error is at most kChunk u times its sum
+// of |a_k b_k|, the additions of the K / kChunk chunk sums at most K / kChunk u
+// times the total, so the Gram entry is off by at most
+// (kChunk + K / kChunk + 1) u sum |a_k b_k| <= (kChunk + K / kChunk + 1) u |a| |b|
+// (Cauchy-Schwarz): a worst-case bound (bound_model, FP32).
+constexpr int kChunk = 32;
+
+// acc[a][b] = rows(I) . rows(J) over K for the thread's 8 x 4 block of column
+// half H (the thread's columns tx * 4 + b + 64 H), summed in chunks of kChunk
+// terms.  Two halves per tile keep the chunk sums within the register budget.
+template <int H>
+__device__ __forceinline__ void gram_tile_half(const float *__restrict__ M, int ld, int K, int rowI,
+                                               int rowJ, float (*As)[BK][BM + PADS],
+                                               float (*Bs)[BK][BM + PADS], float acc[8][4]) {
+    static_assert(kChunk % BK == 0, "chunks of whole stages");
     const int tid = threadIdx.x;
     const int ty = tid >> 4, tx = tid & 15;
     const int lr = tid >> 1, lk = (tid & 1) * 4;
+    float tmp[8][4];
 #pragma unroll
     for (int a = 0; a < 8; ++a)
 #pragma unroll
-        for (int b = 0; b < 8; ++b) acc[a][b] = 0.0f;
+        for (int b = 0; b < 4; ++b) acc[a][b] = tmp[a][b] = 0.0f;
     const float *pa = M + (int64_t)(rowI + lr) * ld + lk;
     const float *pb = M + (int64_t)(rowJ + lr) * ld + lk;
     float4 ra = *reinterpret_cast<const float4 *>(pa);
@@ -64,14 +77,22 @@ __device__ __forceinline__ void gram_tile(const float *__restrict__ M, int ld, i
         for (int kk = 0; kk < BK; ++kk) {
             float4 a0 = *reinterpret_cast<const float4 *>(&As[buf][kk][ty * 4]);
             float4 a1 = *reinterpret_cast<const float4 *>(&As[buf][kk][64 + ty * 4]);
-            float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][tx * 4]);
-            float4 b1 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 + tx * 4]);
+            float4 b0 = *reinterpret_cast<const float4 *>(&Bs[buf][kk][64 * H + tx * 4]);
             float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            float bv[4] = {b0.x, b0.y, b0.z, b0.w};
 #pragma unroll
             for (int a = 0; a < 8; ++a)
 #pragma unroll
-                for (int b = 0; b < 8; ++b) acc[a][b] = fmaf(av[a], bv[b], acc[a][b]);
+                for (int b = 0; b < 4; ++b) tmp[a][b] = fmaf(av[a], bv[b], tmp[a][b]);
+        }
+        if ((k0 + BK) % kChunk == 0 || k0 + BK >= K) {
+#pragma unroll
+            for (int a = 0; a < 8; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    acc[a][b] += tmp[a][b];
+                    tmp[a][b] = 0.0f;
+                }
         }
         buf ^= 1;
     }
@@ -92,7 +113,7 @@ __global__ void __launch_bounds__(NT, 1) cert_simt_kernel(SimtArgs p) {
     double sum = 0.0, bsum = 0.0;
     float mx = -1.0f, mxb_all = 0.0f;
     int ai = 0x7fffffff, aj = 0x7fffffff;
-    float gx[8][8], gy[8][8];
+    float gx[8][4], gy[8][4];
 
     __shared__ int s_stop;
     for (long long t = p.t_begin + blockIdx.x; t < p.ntp; t += gridDim.x) {
@@ -111,44 +132,52 @@ __global__ void __launch_bounds__(NT, 1) cert_simt_kernel(SimtArgs p) {
             sJx[tid] = p.rsx[rowJ + tid];
             sJy[tid] = p.rsy[rowJ + tid];
         }
-        gram_tile(p.Yc, p.ldy, p.Ky, rowI, rowJ, As, Bs, gy);
-        gram_tile(p.Xc, p.ldx, p.Kx, rowI, rowJ, As, Bs, gx);
-
         float tsum = 0.0f, tbsum = 0.0f;
         bool stop = false;
 #pragma unroll
-        for (int a = 0; a < 8; ++a) {
-            const int li = ty * 4 + (a & 3) + (a >> 2) * 64;
-            const int i = rowI + li;
-            const RowStat xi = sIx[li], yi = sIy[li];
+        for (int h = 0; h < 2; ++h) {
+            // the tile's Grams for the thread's column half h
+            if (h == 0) {
+                gram_tile_half<0>(p.Yc, p.ldy, p.Ky, rowI, rowJ, As, Bs, gy);
+                gram_tile_half<0>(p.Xc, p.ldx, p.Kx, rowI, rowJ, As, Bs, gx);
+            } else {
+                gram_tile_half<1>(p.Yc, p.ldy, p.Ky, rowI, rowJ, As, Bs, gy);
+                gram_tile_half<1>(p.Xc, p.ldx, p.Kx, rowI, rowJ, As, Bs, gx);
+            }
 #pragma unroll
-            for (int b = 0; b < 8; ++b) {
-                const int lj = tx * 4 + (b & 3) + (b >> 2) * 64;
-                const int j = rowJ + lj;
-                FastPair fp;
-                int cls = PAIR_SKIP;
-                if (i < j && j < p.n) cls = classify_pair(gx[a][b], gy[a][b], xi, sJx[lj], yi, sJy[lj], p.cc, fp);
-                if (p.dump && t % p.dump_stride == 0 && t / p.dump_stride < p.dump_tiles) {
-                    const RowStat xj = sJx[lj], yj = sJy[lj];
-                    float4 v;
-                    v.x = (xi.n2 + xj.n2) - 2.0f * gx[a][b];
-                    v.y = (yi.n2 + yj.n2) - 2.0f * gy[a][b];
-                    v.z = fmaf(xi.q4, xj.q4, fmaf(xi.q1, xj.q1, p.cc.c_r * (xi.n2 + xj.n2)));
-                    v.w = fmaf(yi.q4, yj.q4, fmaf(yi.q1, yj.q1, p.cc.c_r * (yi.n2 + yj.n2)));
-                    p.dump[((t / p.dump_stride) * BM + li) * BM + lj] = v;
-                }
-                queue_push(cls == PAIR_QUEUE, i, j, p.queue, p.qcount, p.qcap);
-                if (cls == PAIR_OK) {
-                    ++npairs;
-                    if (fp.bin >= 0) s_hist[fp.bin * NT + tid] += 1u; else ++nover;
-                    nviol += fp.violation;
-                    tsum += fp.delta;
-                    tbsum += fp.bound;
-                    mxb_all = fmaxf(mxb_all, fp.bound);
-                    if (better_max(fp.delta, i, j, mx, ai, aj)) { mx = fp.delta; ai = i; aj = j; }
-                    stop |= fp.delta > p.cc.eps + fp.bound;
-                } else if (cls == PAIR_QUEUE) {
-                    ++nqueued;
+            for (int a = 0; a < 8; ++a) {
+                const int li = ty * 4 + (a & 3) + (a >> 2) * 64;
+                const int i = rowI + li;
+                const RowStat xi = sIx[li], yi = sIy[li];
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int lj = tx * 4 + b + h * 64;
+                    const int j = rowJ + lj;
+                    FastPair fp;
+                    int cls = PAIR_SKIP;
+                    if (i < j && j < p.n) cls = classify_pair(gx[a][b], gy[a][b], xi, sJx[lj], yi, sJy[lj], p.cc, fp);
+                    if (p.dump && t % p.dump_stride == 0 && t / p.dump_stride < p.dump_tiles) {
+                        const RowStat xj = sJx[lj], yj = sJy[lj];
+                        float4 v;
+                        v.x = (xi.n2 + xj.n2) - 2.0f * gx[a][b];
+                        v.y = (yi.n2 + yj.n2) - 2.0f * gy[a][b];
+                        v.z = fmaf(xi.q4, xj.q4, fmaf(xi.q1, xj.q1, p.cc.c_r * (xi.n2 + xj.n2)));
+                        v.w = fmaf(yi.q4, yj.q4, fmaf(yi.q1, yj.q1, p.cc.c_r * (yi.n2 + yj.n2)));
+                        p.dump[((t / p.dump_stride) * BM + li) * BM + lj] = v;
+                    }
+                    queue_push(cls == PAIR_QUEUE, i, j, p.queue, p.qcount, p.qcap);
+                    if (cls == PAIR_OK) {
+                        ++npairs;
+                        if (fp.bin >= 0) s_hist[fp.bin * NT + tid] += 1u; else ++nover;
+                        nviol += fp.violation;
+                        tsum += fp.delta;
+                        tbsum += fp.bound;
+                        mxb_all = fmaxf(mxb_all, fp.bound);
+                        if (better_max(fp.delta, i, j, mx, ai, aj)) { mx = fp.delta; ai = i; aj = j; }
+                        stop |= fp.delta > p.cc.eps + fp.bound;
+                    } else if (cls == PAIR_QUEUE) {
+                        ++nqueued;
+                    }
                 }
             }
         }

@@ -182,8 +182,9 @@ BoundModel bound_model(int precision, int K) {
     //    (BF16) or 5.4e-8 (FP16, power-of-two scaled) and averages over the K
     //    terms, hence the 4-norm form; eight (BF16) to sixteen (FP16) RMS.
     //  * accumulation (cacc, times ||a||_2 ||b||_2):
-    //      FP32 SIMT: one FMA chain of K round-to-nearest steps, three RMS of
-    //      its random-walk error;
+    //      FP32 SIMT: FMA chains of 32 terms, each added into the running
+    //      sum (cert_simt.cu), a worst-case bound of
+    //      (32 + ceil(K / 32) + 1) u |a| |b| (round-to-nearest IEEE steps);
     //      tensor cores: the FP32 accumulator truncates (up to one unit in the
     //      last place per MMA, observed about half on average); each 64-wide
     //      K chunk ends with 4 full-size MMAs (<= 4 * 2^-23 of the chunk's
@@ -198,17 +199,16 @@ BoundModel bound_model(int precision, int K) {
     //    (16u of the chunk's sum of |a_k b_k|), and the chunk sums are added
     //    with round to nearest (u per chunk), in all at most
     //    (41 + chunks - 13) u |a| |b|, within cacc (n2_a + n2_b) >= 2 cacc |a| |b|.
-    //  * BF16x3 and FP32 rest on statistical terms (the RMS error of the
-    //    products, the random walk of an FMA chain); they are multiplied by a
-    //    safety factor (BF16x3 4.5, FP32 4) chosen so that over a strided 1 %
-    //    of the tiles of the 60 000 x 784 and 200 000 x 2048 launches the
+    //  * BF16x3 rests on a statistical term (the RMS error of the products),
+    //    multiplied by a safety factor of 4.5 chosen so that over a strided
+    //    1 % of the tiles of the 60 000 x 784 and 200 000 x 2048 launches the
     //    largest |error| / bound is at most 1/4: a calibrated bound keeps a
     //    fourfold margin.  tests/test_gpu_bounds.py measures all three.
     BoundModel bm;
     const float u = 5.9604645e-08f;  // 2^-24
     if (precision == ADAGIO_PREC_FP32) {
         bm.c4 = 0.0f;
-        bm.cacc = 4.0f * (3.0f * u * sqrtf(fmaxf((float)K, 1.0f) / 3.0f));
+        bm.cacc = (33.0f + ceilf(fmaxf((float)K, 1.0f) / 32.0f)) * u;
     } else {
         const float safety = precision == ADAGIO_PREC_FP16X3 ? 1.0f : 4.5f;
         bm.c4 = safety * (precision == ADAGIO_PREC_FP16X3 ? 9.0e-7f : 2.6e-5f);

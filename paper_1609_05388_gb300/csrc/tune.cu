@@ -169,7 +169,7 @@ int adagio_tune_load(adagio_ctx *ctx, const char *path) {
         double sc, v, bd, ms;
         if (!read_number_field(obj, "size_class", &sc) || !read_number_field(obj, "variant", &v) ||
             !read_number_field(obj, "band", &bd) || !read_number_field(obj, "tile_ms", &ms) ||
-            !(v == 1 || v == 2) || !(bd >= 1 && bd <= 32) || sc < 0 || sc > 30) {
+            !(v == 1 || v == 2) || !(bd >= 1 && bd <= 64) || sc < 0 || sc > 30) {
             ctx->last_error = "malformed tile table entry: " + obj;
             return ADAGIO_E_INVALID_ARG;
         }
