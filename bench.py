@@ -305,7 +305,7 @@ def prefix_leg(ctx, X, Y, s, m, eps, reps=2):
             "full_max": full.max,
             "prefixes": [{"k": r["k"], "m": s + r["k"], "verdict": r["verdict"],
                           "max_interval": [r["max_lower"], r["max_upper"]],
-                          "certain_violations": r["certain_violations"],
+                          "violations": r["violations"], "recomputed": r["recomputed"],
                           "unsettled_pairs": r["unsettled_pairs"]} for r in res]}
 
 

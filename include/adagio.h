@@ -220,22 +220,25 @@ int adagio_cert_merge(const adagio_cert_part *parts, int count, adagio_cert *out
 /*
  * Verdict of one JL prefix in adagio_distortion_prefixes.
  *  k            JL rows the candidate keeps (kc)
- *  verdict      1: every pair's distortion is certainly <= eps (the candidate
- *               is certified); 0: some pair's distortion certainly exceeds
- *               eps; -1: undecided (no certain violation, but the error bound
- *               of some pair straddles eps: certify the candidate in full)
- *  certain_violations   pairs whose distortion certainly exceeds eps
- *  unsettled_pairs      pairs whose bound interval contains eps
+ *  verdict      1: the candidate is certified (no pair's distortion exceeds
+ *               eps); 0: some pair's distortion exceeds eps; -1: undecided
+ *               (no violation found, but unsettled_pairs > 0)
+ *  violations   pairs whose distortion exceeds eps: the exact count when
+ *               unsettled_pairs = 0, else a lower bound
+ *  recomputed   pairs the per-pair bounds left open (near eps, or possibly
+ *               x_i == x_j), decided by an exact FP64 recompute of their rows
+ *  unsettled_pairs  open pairs beyond the recompute queue's capacity (2^18
+ *               pairs per call, shared by the candidates); 0 in practice
  *  max_lower, max_upper the candidate's largest distortion lies in
- *               [max_lower, max_upper] (lower and upper ends of the pairs'
- *               bound intervals)
- *  Pairs whose distortion the fast tiles cannot bound (x_i == x_j, or too
- *  ill-conditioned) count as unsettled and make max_upper +inf.
+ *               [max_lower, max_upper] (bounds of the pairs' intervals and
+ *               the exact values of the recomputed pairs); max_upper is +inf
+ *               when an unsettled pair may have x_i == x_j
+ *  Pairs with x_i == x_j are excluded, as in the certificate.
  */
 typedef struct {
     int32_t k;
     int32_t verdict;
-    uint64_t certain_violations, unsettled_pairs;
+    uint64_t violations, unsettled_pairs, recomputed;
     double max_lower, max_upper;
 } adagio_prefix_cert;
 
@@ -250,9 +253,9 @@ typedef struct {
  * k - 128, ...: the prefixes below a dimension already fitted);
  * 1 <= kc[c] <= k; 1 <= count <= 4.  The pass computes `full`, the certificate of
  * the whole map (as adagio_distortion with hist [0, 2 eps)), and out[c], the
- * verdict of each candidate against eps from per-pair bounds on its
- * distortion (the pass shares the tensor-core Gram sums; no pair of a
- * candidate is recomputed, so a verdict may stay undecided).
+ * verdict of each candidate against eps: from per-pair bounds on its
+ * distortion on the shared tensor-core Gram sums, and for the few pairs those
+ * bounds leave open, from an exact recompute.
  *  precision    ADAGIO_PREC_FP16X3 or ADAGIO_PREC_BF16X3.
  * X, Y host or device; full and out host.  Synchronises `stream`.
  * Errors: INVALID_ARG (sizes, kc, count, eps in (0, 1), precision),

@@ -71,7 +71,8 @@ class PrefixCertStruct(ctypes.Structure):
     """adagio_prefix_cert: the verdict of one JL prefix."""
     _fields_ = [
         ("k", ctypes.c_int32), ("verdict", ctypes.c_int32),
-        ("certain_violations", ctypes.c_uint64), ("unsettled_pairs", ctypes.c_uint64),
+        ("violations", ctypes.c_uint64), ("unsettled_pairs", ctypes.c_uint64),
+        ("recomputed", ctypes.c_uint64),
         ("max_lower", ctypes.c_double), ("max_upper", ctypes.c_double),
     ]
 
@@ -416,7 +417,7 @@ class Context:
 
         Y = [PCA part (s columns) | k JL columns]; prefix c keeps kc[c] JL
         columns rescaled by sqrt(k / kc[c]).  verdict 1 = certified at eps,
-        0 = certainly violated, -1 = undecided."""
+        0 = violated (violations = the exact count), -1 = undecided."""
         x, y = _Arr(X), _Arr(Y)
         if x.rows != y.rows:
             raise ValueError("X and Y must have the same number of rows")

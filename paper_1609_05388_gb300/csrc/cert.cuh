@@ -23,6 +23,9 @@ struct MultiSpec {
     void *cs = nullptr;        // count x n_pad float4
     void *out = nullptr;       // slots x count verdict records (32 B each)
     int slots = 0;             // records per candidate (CTAs x epilogue warps)
+    void *cq = nullptr;        // device: int4 (i, j, candidate, 0) of the open pairs
+    unsigned long long *cqcount = nullptr;  // device: open pairs offered (zeroed by the caller)
+    unsigned long long cqcap = 0;
 };
 
 struct CertLaunch {

@@ -114,6 +114,8 @@ struct TcMulti {
     // r > uv or r < lv, certainly within when lf <= r <= uf
     float uv, lv, uf, lf;
     long long n_pad;           // rows of each candidate's statistics
+    int4 *cq;                  // open pairs (i, j, candidate) for the exact recompute
+    unsigned long long *cqcount, cqcap;
     // [count][n_pad] interleaved by row pair (2q, 2q+1): element 2q = the two
     // |yP|^2 and the two q4 of the PCA part, element 2q + 1 = the two |yJc|^2
     // and the two q4 of the whole prefix (q4 times sqrt(0.56))
@@ -400,21 +402,32 @@ __device__ __forceinline__ unsigned cand_fast2(f2 xl, f2 xh, f2 yh, f2 nyl, bool
 
 // The full test of one pair: it certainly exceeds eps when yl > uv xh or
 // yh < lv xl, certainly does not when the common-path conditions hold, and is
-// open otherwise; a pair with xl <= 0 (possibly x_i == x_j, which the
-// certificate excludes) stays open and leaves the largest r unbounded.
-__device__ __forceinline__ void cand_slow(float xl, float xh, float yh, float nyl, const TcMulti &m,
-                                          CandRun &a) {
+// open otherwise.  An open pair (i, j) goes to the candidates' queue, where an
+// exact recompute decides it; a pair with xl <= 0 (possibly x_i == x_j, which
+// the certificate excludes) is always open.  Only an open pair the full queue
+// cannot take leaves the largest r unbounded.
+__device__ __forceinline__ void cand_slow(float xl, float xh, float yh, float nyl, int i, int j, int c,
+                                          const TcMulti &m, CandRun &a) {
     const float yl = -nyl;
     const bool pos = xl > 0.0f;
     const bool viol = pos & ((fmaf(-m.uv, xh, yl) > 0.0f) | (fmaf(m.lv, xl, -yh) > 0.0f));
     const bool fine = pos & (fmaf(-m.uf, xl, yh) <= 0.0f) & (fmaf(m.lf, xh, -yl) <= 0.0f);
+    const bool open = !viol & !fine;
     a.certain += viol ? 1u : 0u;
-    a.open += (!viol & !fine) ? 1u : 0u;
+    a.open += open ? 1u : 0u;
+    bool queued = false;
+    if (open) {
+        const unsigned long long q = atomicAdd(m.cqcount, 1ull);
+        if (q < m.cqcap) {
+            m.cq[q] = make_int4(i, j, c, 0);
+            queued = true;
+        }
+    }
     float nrmh, rnl, u;
     upk2(a.nrmh, nrmh, u);
     upk2(a.rnl, rnl, u);
     if (!pos) {
-        nrmh = -INFINITY;
+        if (!queued) nrmh = -INFINITY;
     } else {
         if (fmaf(nrmh, xl, yh) > 0.0f) {  // a new largest upper bound
             nrmh = fminf(nrmh, -__fdiv_ru(yh, xl));
@@ -1104,8 +1117,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                             upk2(xh, h0, h1);
                             upk2(yh, y0, y1);
                             upk2(nyl, n0, n1);
-                            if (flag & (1u << q)) cand_slow(l0, h0, y0, n0, m, a);
-                            if (flag & (2u << q)) cand_slow(l1, h1, y1, n1, m, a);
+                            if (flag & (1u << q)) cand_slow(l0, h0, y0, n0, i, j, c, m, a);
+                            if (flag & (2u << q)) cand_slow(l1, h1, y1, n1, i, j + 1, c, m, a);
                         }
                     }
                 }
@@ -1679,6 +1692,13 @@ bool launch_cert_tc(const CertLaunch &L, int precision, cudaStream_t st) {
         mt.uf = std::nextafter((float)(e1 * (1.0 - sl)), 0.0f);
         mt.lf = up(e0 * (1.0 + sl));
         mt.cs = reinterpret_cast<const ulonglong2 *>(ms.cs);
+        mt.cq = reinterpret_cast<int4 *>(ms.cq);
+        mt.cqcount = ms.cqcount;
+        mt.cqcap = ms.cqcap;
+        // a certificate whose recompute queue overflowed runs the tiles again:
+        // each launch starts the candidates' queue afresh (their records are
+        // written, not added)
+        ADAGIO_CUDA(cudaMemsetAsync(ms.cqcount, 0, sizeof(unsigned long long), st));
         mt.out = reinterpret_cast<CandPartial *>(ms.out);
         mt.n_pad = y.n_pad;
         const int4 kc4 = make_int4(ms.kc[0], ms.kc[1], ms.kc[2], ms.kc[3]);
