@@ -209,3 +209,30 @@ def test_fixed_mode_search_pads_a_fixed_pca_part():
     assert [r for r, mx in res.probes if mx <= 0.3] == [r for r, _ in res.probes if r >= 6]
     for r, mx in res.probes:
         assert (mx < 1e-6) if r >= 6 else (mx > 0.5)
+
+
+def test_jl_prefix_maps_are_rescaled_prefixes():
+    """The reading behind the multi-candidate certificate: the map with kc JL
+    rows (entries +-1/sqrt(kc), Algorithm 1) is the k-row map's first kc JL
+    rows times sqrt(k / kc), with the same PCA part, so its embedding is
+    [Y_P | sqrt(k / kc) Y_J[:, :kc]] and its squared distances are
+    |dP|^2 + (k / kc) |dJ[:kc]|^2 (checked on the certificate, which recomputes
+    every distance from the embedded coordinates)."""
+    X = synth.small(seed=2, n=300).X.astype(np.float64)
+    s, k = 6, 128
+    f = O.fit(X, s + k, 9, s=s)
+    Y = O.embed(f.A, X)
+    for kc in (64, 100, 128):
+        Sk = O.jl_matrix(9, kc, X.shape[1])
+        np.testing.assert_allclose(Sk, np.sqrt(k / kc) * f.S[:kc], rtol=1e-15, atol=0)
+        fc = O.fit(X, s + kc, 9, s=s, pca_result=f.pca)
+        Yc = O.embed(fc.A, X)
+        cand = np.hstack([Y[:, :s], np.sqrt(k / kc) * Y[:, s:s + kc]])
+        np.testing.assert_allclose(Yc, cand, rtol=1e-12, atol=1e-12)
+        a = certificate(X, Yc, 0.3)
+        b = certificate(X, cand, 0.3)
+        assert a.violations == b.violations and abs(a.max - b.max) <= 1e-12
+        # and the prefix map is not the unscaled prefix: that one shrinks the JL part
+        unscaled = np.hstack([Y[:, :s], Y[:, s:s + kc]])
+        if kc < k:
+            assert certificate(X, unscaled, 0.3).mean > a.mean
