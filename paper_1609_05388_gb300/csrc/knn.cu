@@ -8,10 +8,11 @@
 // ties (equal distances) broken by the smaller base index, query i's own index
 // left out when `exclude_self` (the graph of one point set).
 //
-// Steps, per block of 1024 query rows:
+// Steps, per block of query rows (1024 to 8192 of them, as many as a 2 GiB
+// Gram block holds):
 //   1. Gram block G = Q_blk B^T on tcgen05 tensor cores (the split-precision
 //      GEMM of tcgemm.cu: per-row power-of-two FP16 hi + lo planes, three
-//      products per term, FP32 accumulation), 1024 x nb floats;
+//      products per term, FP32 accumulation), rows x nb floats;
 //   2. one warp per query row scans its Gram row (each lane loading kUnroll
 //      columns ahead of filtering them), forms the approximate squared
 //      distances d~ = |q|^2 + |b|^2 - 2 q.b and keeps the 64 smallest (d~, j)
@@ -38,7 +39,9 @@ namespace {
 
 constexpr int kMaxK = 48;                 // largest k served
 constexpr int kCand = 64;                 // candidates kept per query (two per lane)
-constexpr int kBlockQ = 1024;             // query rows per Gram block
+constexpr int kBlockQMin = 1024;          // query rows per Gram block: at least
+constexpr int kBlockQMax = 8192;          // and at most (one warp per row in the scan)
+constexpr size_t kGramBudget = size_t(2) << 30;  // bytes of one FP32 Gram block, at most
 constexpr int kUnroll = 8;                // columns a lane loads before filtering them
 constexpr int kSelWarps = 8;              // warps (query rows) per selection CTA
 constexpr float kDistErr = 128.0f * 5.9604645e-08f;  // c: 128 u
@@ -297,7 +300,11 @@ extern "C" int adagio_knn(adagio_ctx *ctx, const float *Q, int64_t nq, int64_t l
         const bool same = Q == B && ldq == ldb && nq == nb;
         const int Kp = pad64(m);
         const bool out_dev = is_device_ptr(idx, ctx->device) && is_device_ptr(d2, ctx->device);
-        const int64_t qrows_max = std::min<int64_t>(nq, kBlockQ);
+        // as many query rows per block as 2 GiB of Gram values hold (whole
+        // multiples of 1024, up to 8192): more rows keep more scan warps in flight
+        const int64_t fit_rows = (int64_t)(kGramBudget / ((size_t)nb * 4)) / kBlockQMin * kBlockQMin;
+        const int64_t block_q = std::max<int64_t>(kBlockQMin, std::min<int64_t>(kBlockQMax, fit_rows));
+        const int64_t qrows_max = std::min<int64_t>(nq, block_q);
         const size_t part_floats =
             (size_t)std::max<int64_t>(1, tc_gemm_workspace(ctx, (int)qrows_max, (int)nb, Kp, false));
         size_t need = align_up((size_t)nb * ldb * 4, 256) + (same ? 0 : align_up((size_t)nq * ldq * 4, 256));
@@ -369,8 +376,8 @@ extern "C" int adagio_knn(adagio_ctx *ctx, const float *Q, int64_t nq, int64_t l
         a.d2 = dd2;
         a.redo = redo;
         a.nredo = nredo;
-        for (int64_t q0 = 0; q0 < nq; q0 += kBlockQ) {
-            const int64_t rows = std::min<int64_t>(kBlockQ, nq - q0);
+        for (int64_t q0 = 0; q0 < nq; q0 += block_q) {
+            const int64_t rows = std::min<int64_t>(block_q, nq - q0);
             SplitPlanes blk = pq;
             blk.hi = pq.hi + q0 * Kp;
             blk.lo = pq.lo + q0 * Kp;

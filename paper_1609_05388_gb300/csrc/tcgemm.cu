@@ -2,7 +2,10 @@
 // Sec. 2 / Sec. 4.5 and the projection of Algorithm 1): C = A B^T from the
 // 2-term 16-bit planes of A and B.
 //
-// One CTA per (128 x 128 output tile, K split).  Roles (320 threads):
+// Persistent: one CTA per SM walks the work items (128 x 128 output tile, K
+// split), the barrier phases and TMEM slots running on from item to item, so
+// that a CTA's setup is paid once and an item's epilogue overlaps the next
+// item's loads and MMAs.  Roles (320 threads):
 //   warp 0      TMA producer: A hi/lo and B hi/lo, 64 K-elements per stage,
 //               3 stages of 64 KB, 128-byte swizzle
 //   warp 1      TMEM owner (2 chunk slots of 128 columns) and MMA issuer:
@@ -41,7 +44,8 @@ constexpr size_t kSmem = kTmemPtr + 16 + 1024;      // + alignment slack
 static_assert(kSmem <= 232448, "GEMM tile exceeds the shared-memory limit");
 
 struct GemmArgs {
-    int M, N, tiles_n;
+    int M, N, tiles_n, tiles;  // tiles = tiles_m * tiles_n
+    long long items;           // tiles x K splits
     int ksteps, ksplit;        // K steps in total / per split
     int sym;
     const float *sa, *sb;      // power-of-two scales
@@ -57,12 +61,22 @@ __global__ void __launch_bounds__(kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap map_ah, const __grid_constant__ CUtensorMap map_al,
                    const __grid_constant__ CUtensorMap map_bh, const __grid_constant__ CUtensorMap map_bl,
                    GemmArgs p) {
-    const int tm = blockIdx.x / p.tiles_n, tn = blockIdx.x % p.tiles_n;
-    if (p.sym && tn < tm) return;  // the mirror of a computed tile
-    const int k0 = blockIdx.y * p.ksplit;
-    const int k1 = min(p.ksteps, k0 + p.ksplit);
-    const int nsteps = k1 - k0;
-    const int nchunks = (nsteps + kChunkSteps - 1) / kChunkSteps;
+    // work item w: tile w % tiles, K split w / tiles; the mirror of a
+    // computed tile (sym, tn < tm) is skipped by every role alike
+    struct Item {
+        int tm, tn, split, k0, k1, nsteps, nchunks;
+    };
+    auto item = [&](long long w, Item &it) {
+        const int tile = (int)(w % p.tiles);
+        it.split = (int)(w / p.tiles);
+        it.tm = tile / p.tiles_n;
+        it.tn = tile % p.tiles_n;
+        it.k0 = it.split * p.ksplit;
+        it.k1 = min(p.ksteps, it.k0 + p.ksplit);
+        it.nsteps = it.k1 - it.k0;
+        it.nchunks = (it.nsteps + kChunkSteps - 1) / kChunkSteps;
+        return !(p.sym && it.tn < it.tm);
+    };
 
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t *smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
@@ -99,7 +113,6 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *s_tmem;
-    auto chunk_steps = [&](int c) { return min(kChunkSteps, nsteps - c * kChunkSteps); };
 
     if (warp == 0) {
         // ------------------------------------------------------ TMA producer
@@ -108,23 +121,31 @@ __global__ void __launch_bounds__(kThreads, 1)
         bool issued[kStages];
         uint32_t issued_parity[kStages];
         for (int s = 0; s < kStages; ++s) issued[s] = false, issued_parity[s] = 0;
-        for (int ks = k0; ks < k1; ++ks) {
-            if (!warp_wait(bar_empty + 8 * stage, phase ^ 1, p.status, 1)) break;
-            if (lane == 0) {
-                const uint32_t bar = bar_full + 8 * stage;
-                const uint32_t dst = sbase + stage * kStageBytes;
-                mbar_arrive_expect_tx(bar, kStageBytes);
-                tma_load_2d<false>(dst, &map_ah, ks * kKStep, tm * kTile, bar);
-                tma_load_2d<false>(dst + kPlane, &map_al, ks * kKStep, tm * kTile, bar);
-                tma_load_2d<false>(dst + 2 * kPlane, &map_bh, ks * kKStep, tn * kTile, bar);
-                tma_load_2d<false>(dst + 3 * kPlane, &map_bl, ks * kKStep, tn * kTile, bar);
-            }
-            __syncwarp();
-            issued[stage] = true;
-            issued_parity[stage] = phase;
-            if (++stage == kStages) {
-                stage = 0;
-                phase ^= 1;
+        bool ok = true;
+        for (long long w = blockIdx.x; ok && w < p.items; w += gridDim.x) {
+            Item it;
+            if (!item(w, it)) continue;
+            for (int ks = it.k0; ks < it.k1; ++ks) {
+                if (!warp_wait(bar_empty + 8 * stage, phase ^ 1, p.status, 1)) {
+                    ok = false;
+                    break;
+                }
+                if (lane == 0) {
+                    const uint32_t bar = bar_full + 8 * stage;
+                    const uint32_t dst = sbase + stage * kStageBytes;
+                    mbar_arrive_expect_tx(bar, kStageBytes);
+                    tma_load_2d<false>(dst, &map_ah, ks * kKStep, it.tm * kTile, bar);
+                    tma_load_2d<false>(dst + kPlane, &map_al, ks * kKStep, it.tm * kTile, bar);
+                    tma_load_2d<false>(dst + 2 * kPlane, &map_bh, ks * kKStep, it.tn * kTile, bar);
+                    tma_load_2d<false>(dst + 3 * kPlane, &map_bl, ks * kKStep, it.tn * kTile, bar);
+                }
+                __syncwarp();
+                issued[stage] = true;
+                issued_parity[stage] = phase;
+                if (++stage == kStages) {
+                    stage = 0;
+                    phase ^= 1;
+                }
             }
         }
         if (lane == 0)
@@ -156,48 +177,59 @@ __global__ void __launch_bounds__(kThreads, 1)
                 tc_mma<false>(d, ah + off, bh + off, p.idesc, 1u);
             }
         };
-        for (int c = 0; c < nchunks; ++c) {
-            const int nst = chunk_steps(c);
-            if (!warp_wait(bar_full + 8 * stage, phase, p.status, 2)) break;
-            if (!warp_wait(bar_sempty + 8 * slot, sphase ^ 1, p.status, 2)) break;
-            tc_fence_after();
-            const uint32_t d = tmem_base + (uint32_t)(slot * kTile);
-            const int st0 = stage;
-            int st1 = stage + 1;
-            uint32_t ph1 = phase;
-            if (st1 == kStages) {
-                st1 = 0;
-                ph1 ^= 1;
-            }
-            if (lane == 0) {
-                cross(st0, d, 0u);
-                any = true;
-            }
-            __syncwarp();
-            if (nst == 2) {
-                if (!warp_wait(bar_full + 8 * st1, ph1, p.status, 2)) break;
+        bool ok = true;
+        for (long long w = blockIdx.x; ok && w < p.items; w += gridDim.x) {
+            Item it;
+            if (!item(w, it)) continue;
+            for (int c = 0; c < it.nchunks; ++c) {
+                const int nst = min(kChunkSteps, it.nsteps - c * kChunkSteps);
+                if (!warp_wait(bar_full + 8 * stage, phase, p.status, 2) ||
+                    !warp_wait(bar_sempty + 8 * slot, sphase ^ 1, p.status, 2)) {
+                    ok = false;
+                    break;
+                }
                 tc_fence_after();
-                if (lane == 0) cross(st1, d, 1u);
+                const uint32_t d = tmem_base + (uint32_t)(slot * kTile);
+                const int st0 = stage;
+                int st1 = stage + 1;
+                uint32_t ph1 = phase;
+                if (st1 == kStages) {
+                    st1 = 0;
+                    ph1 ^= 1;
+                }
+                if (lane == 0) {
+                    cross(st0, d, 0u);
+                    any = true;
+                }
                 __syncwarp();
-            }
-            if (lane == 0) {
-                full_size(st0, d);
-                tc_commit<false>(bar_empty + 8 * st0);
                 if (nst == 2) {
-                    full_size(st1, d);
-                    tc_commit<false>(bar_empty + 8 * st1);
+                    if (!warp_wait(bar_full + 8 * st1, ph1, p.status, 2)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    if (lane == 0) cross(st1, d, 1u);
+                    __syncwarp();
                 }
-                tc_commit<false>(bar_sfull + 8 * slot);
-            }
-            __syncwarp();
-            for (int q = 0; q < nst; ++q)
-                if (++stage == kStages) {
-                    stage = 0;
-                    phase ^= 1;
+                if (lane == 0) {
+                    full_size(st0, d);
+                    tc_commit<false>(bar_empty + 8 * st0);
+                    if (nst == 2) {
+                        full_size(st1, d);
+                        tc_commit<false>(bar_empty + 8 * st1);
+                    }
+                    tc_commit<false>(bar_sfull + 8 * slot);
                 }
-            if (++slot == 2) {
-                slot = 0;
-                sphase ^= 1;
+                __syncwarp();
+                for (int q = 0; q < nst; ++q)
+                    if (++stage == kStages) {
+                        stage = 0;
+                        phase ^= 1;
+                    }
+                if (++slot == 2) {
+                    slot = 0;
+                    sphase ^= 1;
+                }
             }
         }
         any = __shfl_sync(0xffffffffu, any ? 1 : 0, 0) != 0;
@@ -212,40 +244,62 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int quarter = warp & 3;
         const int h = ew >> 2;
         const uint32_t lane_addr = (uint32_t)(quarter * 32) << 16;
-        float acc[kEpiCols];
-#pragma unroll
-        for (int c = 0; c < kEpiCols; ++c) acc[c] = 0.0f;
         int slot = 0;
         uint32_t sphase = 0;
         bool ok = true;
-        for (int c = 0; c < nchunks; ++c) {
-            ok = warp_wait(bar_sfull + 8 * slot, sphase, p.status, 3);
-            if (!ok) break;
-            tc_fence_after();
-            uint32_t v[64];
-            tmem_ld64_wait(tmem_base + lane_addr + (uint32_t)(slot * kTile + h * kEpiCols), v);
+        for (long long w = blockIdx.x; ok && w < p.items; w += gridDim.x) {
+            Item it;
+            if (!item(w, it)) continue;
+            float acc[kEpiCols];
 #pragma unroll
-            for (int q = 0; q < kEpiCols; ++q) acc[q] += __uint_as_float(v[q]);
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(bar_sempty + 8 * slot);
-            if (++slot == 2) {
-                slot = 0;
-                sphase ^= 1;
+            for (int c = 0; c < kEpiCols; ++c) acc[c] = 0.0f;
+            for (int c = 0; c < it.nchunks; ++c) {
+                ok = warp_wait(bar_sfull + 8 * slot, sphase, p.status, 3);
+                if (!ok) break;
+                tc_fence_after();
+                uint32_t v[64];
+                tmem_ld64_wait(tmem_base + lane_addr + (uint32_t)(slot * kTile + h * kEpiCols), v);
+#pragma unroll
+                for (int q = 0; q < kEpiCols; ++q) acc[q] += __uint_as_float(v[q]);
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_sempty + 8 * slot);
+                if (++slot == 2) {
+                    slot = 0;
+                    sphase ^= 1;
+                }
             }
-        }
-        const int row = tm * kTile + quarter * 32 + lane;
-        if (ok && row < p.M) {
-            const float ia = 1.0f / p.sa[(int64_t)row * p.sa_stride];  // powers of two: exact
-            float *dst = p.out + (int64_t)blockIdx.y * p.split_stride + (int64_t)row * p.ldo;
-            const int c0 = tn * kTile + h * kEpiCols;
+            // the item's tile, written while the next item's chunks run
+            const int row = it.tm * kTile + quarter * 32 + lane;
+            if (ok && row < p.M) {
+                const float ia = 1.0f / p.sa[(int64_t)row * p.sa_stride];  // powers of two: exact
+                float *dst = p.out + (int64_t)it.split * p.split_stride + (int64_t)row * p.ldo;
+                const int c0 = it.tn * kTile + h * kEpiCols;
+                // 16-byte stores where the row allows them: a lane writes its own
+                // row, so each store instruction touches 32 rows
+                const bool vec = c0 + kEpiCols <= p.N && ((reinterpret_cast<uintptr_t>(dst + c0) & 15u) == 0);
+                if (vec) {
 #pragma unroll
-            for (int q = 0; q < kEpiCols; ++q) {
-                const int col = c0 + q;
-                if (col < p.N) {
-                    float v = acc[q] * ia * (1.0f / p.sb[(int64_t)col * p.sb_stride]);
-                    if (p.bias) v += p.bias[col];
-                    dst[col] = v;
+                    for (int q = 0; q < kEpiCols; q += 4) {
+                        float v[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            const int col = c0 + q + e;
+                            v[e] = acc[q + e] * ia * (1.0f / p.sb[(int64_t)col * p.sb_stride]);
+                            if (p.bias) v[e] += p.bias[col];
+                        }
+                        *reinterpret_cast<float4 *>(dst + c0 + q) = make_float4(v[0], v[1], v[2], v[3]);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < kEpiCols; ++q) {
+                        const int col = c0 + q;
+                        if (col < p.N) {
+                            float v = acc[q] * ia * (1.0f / p.sb[(int64_t)col * p.sb_stride]);
+                            if (p.bias) v += p.bias[col];
+                            dst[col] = v;
+                        }
+                    }
                 }
             }
         }
@@ -419,6 +473,8 @@ void tc_gemm(adagio_ctx *ctx, const SplitPlanes &A, const SplitPlanes &B, int M,
     a.M = M;
     a.N = N;
     a.tiles_n = q.tiles_n;
+    a.tiles = q.tiles_m * q.tiles_n;
+    a.items = (long long)a.tiles * q.splits;
     a.ksteps = q.ksteps;
     a.ksplit = q.ksplit;
     a.sym = sym ? 1 : 0;
@@ -440,7 +496,8 @@ void tc_gemm(adagio_ctx *ctx, const SplitPlanes &A, const SplitPlanes &B, int M,
     const CUtensorMap mbh = plane_map(B.hi, B.rows, B.Kp, kKStep, kTile, B.bf16);
     const CUtensorMap mbl = plane_map(B.lo, B.rows, B.Kp, kKStep, kTile, B.bf16);
     tc_gemm_init();
-    dim3 grid((unsigned)(q.tiles_m * q.tiles_n), (unsigned)q.splits);
+    // persistent: at most one CTA per SM (the shared memory holds one)
+    const unsigned grid = (unsigned)std::min<long long>(a.items, ctx->num_sms);
     tc_gemm_kernel<<<grid, kThreads, kSmem, st>>>(mah, mal, mbh, mbl, a);
     ADAGIO_CHECK_LAUNCH();
     if (!direct) {
